@@ -1,0 +1,153 @@
+/*
+ * skim.h -- C ABI of libskim: combined bottom-k reachability sketches, SKIM
+ * greedy seed selection and the sketch-based influence oracle on one GB300
+ * GPU (sm_103a).
+ *
+ * Method: Cohen, Delling, Pajor, Werneck, "Sketch-based Influence
+ * Maximization and Computation: Scaling up with Guarantees" (arXiv 1408.6282).
+ *
+ * Conventions for every call:
+ *   - Return value: SKIM_OK (0) on success, a negative SKIM_E* code otherwise;
+ *     skim_strerror() names it.  After SKIM_ECUDA or SKIM_ETIMEOUT the
+ *     context is unusable and must be destroyed.
+ *   - Ownership: inputs are borrowed for the duration of the call and copied;
+ *     outputs are written to caller-owned buffers.  All device memory used by
+ *     a context is allocated by the library and released by skim_destroy().
+ *   - Pointers marked (host) must be host memory; pointers marked
+ *     (host|device) may be either, as stated by the accompanying flag.
+ *   - Calls on one context are not thread-safe; use one context per thread.
+ *   - All work runs on the stream given at creation (NULL: the legacy default
+ *     stream); calls that return results on the host synchronise that stream.
+ */
+#ifndef SKIM_H
+#define SKIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SKIM_OK 0
+#define SKIM_EINVAL -1    /* bad argument: null pointer, node id >= n, k < 2, l == 0 or l > 64, ... */
+#define SKIM_ENOMEM -2    /* device or host allocation failed */
+#define SKIM_ENOTBUILT -3 /* query before skim_build_sketches() */
+#define SKIM_ETIMEOUT -4  /* a device-side wait hit its iteration cap; context unusable */
+#define SKIM_ECUDA -5     /* a CUDA runtime call failed; context unusable */
+#define SKIM_EGRAPH -6    /* edge list not canonical (unsorted, duplicate or self-loop) */
+#define SKIM_ERANGE -7    /* a size exceeds a stated limit */
+
+/* Probability models of the binary IC model (Section 6, "uniform" and
+ * "weighted cascade"; trivalency assigns p in {0.1, 0.01, 0.001} per edge). */
+#define SKIM_PROB_UNIFORM 0
+#define SKIM_PROB_WC 1
+#define SKIM_PROB_TRIVALENCY 2
+
+/* Directed graph as a canonical edge list: m pairs (src[e], dst[e]) sorted by
+ * (src, dst), no duplicates, no self-loops, ids < n.  An edge (u,v) means u
+ * can infect v (Section 2).  on_device = 0: src/dst are host pointers;
+ * 1: device pointers on the current device. */
+typedef struct {
+    uint32_t n;
+    uint64_t m;
+    const uint32_t *src;
+    const uint32_t *dst;
+    int on_device;
+} skim_graph;
+
+/* Parameters (Sections 3-4):
+ *   l          number of IC instances, 1..64 (one 64-bit word per node holds a
+ *              node's instances);
+ *   k          sketch size, 2..255;
+ *   prob_model SKIM_PROB_*; p is the uniform edge probability, 0 < p <= 1;
+ *   coin_key   key of the live-edge coins: edge (u,v) is live in instance i
+ *              iff fmix(fmix(coin_key ^ (u<<32|v)) + (i+1)*G) <= floor(p*2^64)-1,
+ *              fmix the SplitMix64 output function, G = 0x9E3779B97F4A7C15;
+ *              for weighted cascade the bound is floor((2^64-1)/indeg(v));
+ *   rank_key   rank of pair (v,i) is fmix(rank_key + (v*l+i)*G), read as
+ *              a real in [0,1) after scaling by 2^-64 (ranks never tie);
+ *   prob_key   trivalency class of edge (u,v): fmix(prob_key ^ (u<<32|v)) % 3;
+ *   batch_lanes  ranks per batched search, 0 = automatic. */
+typedef struct {
+    uint32_t l;
+    uint32_t k;
+    int prob_model;
+    double p;
+    uint64_t coin_key;
+    uint64_t rank_key;
+    uint64_t prob_key;
+    uint32_t batch_lanes;
+} skim_params;
+
+typedef struct skim_ctx skim_ctx;
+
+/* Create a context on the current CUDA device: copies the graph, builds both
+ * CSR directions in device memory and the rank order of all n*l pairs
+ * (Section 3; "shuffle the nl node-instance pairs" of Algorithms 1 and 2 is
+ * read as increasing rank order).  stream: a cudaStream_t, or NULL.
+ * Errors: SKIM_EINVAL, SKIM_EGRAPH, SKIM_ENOMEM, SKIM_ECUDA. */
+int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_ctx **out);
+
+/* Algorithm 2 (Section 5.2): combined bottom-k reachability sketches X_v of
+ * all nodes (Eq. combinedrs), computed by rank-batched pruned reverse
+ * searches; the result equals the definition exactly.  Sketches stay in
+ * device memory.  May be called again (recomputes). */
+int skim_build_sketches(skim_ctx *ctx);
+
+/* Copy sketches out: x_out[v*k + j] = j-th smallest rank of X_v (row-major,
+ * n*k uint64), len_out[v] = |X_v| (n uint32).  out_on_device selects the
+ * memory kind of both outputs.  SKIM_ENOTBUILT before skim_build_sketches(). */
+int skim_get_sketches(skim_ctx *ctx, uint64_t *x_out, uint32_t *len_out, int out_on_device);
+
+/* Device pointers to the resident sketches (valid until the next build or
+ * destroy), for callers that keep them on the GPU. */
+int skim_sketch_pointers(skim_ctx *ctx, const uint64_t **x_dev, const uint32_t **len_dev);
+
+/* SKIM, Algorithm 1 (Section 4): select n_seeds more seeds.  Continues the
+ * sequence on repeated calls (resume after tau_v, Section 4).  Outputs (host):
+ * seeds_out[j] the j-th new seed, cov_out[j] its marginal coverage in
+ * node-instance pairs, i.e. l * I_j (integer).  Tie rules: the seed is the
+ * smallest node id among nodes whose partial sketch reaches k on the same
+ * rank; when ranks run out, argmax size with ties to the smallest id, and the
+ * smallest unchosen id once everything is covered.
+ * Errors: SKIM_EINVAL if the total would exceed n. */
+int skim_greedy(skim_ctx *ctx, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out);
+
+/* Restart SKIM from the empty seed set (drops covered pairs and the index). */
+int skim_greedy_reset(skim_ctx *ctx);
+
+/* Influence oracle query (Section 5.1, Eq. unionest, Cohen-Kaplan union
+ * estimator): estimate of Inf(S) = |union of R_u, u in S| / l from the
+ * sketches of S.  seeds (host), n_seeds >= 0; duplicates allowed; the empty
+ * set gives 0.  The sum is formed exactly in fixed point and rounded once, so
+ * the result does not depend on summation order.  est_out (host). */
+int skim_oracle_query(skim_ctx *ctx, const uint32_t *seeds, uint32_t n_seeds, double *est_out);
+
+/* Batched form of skim_oracle_query: q queries given in CSR form.
+ * offsets[q+1] (host), seeds[offsets[q]] (host|device per on_device),
+ * est_out[q] (host|device per on_device).  Each result is bitwise identical
+ * to the single-query call. */
+int skim_oracle_query_batch(skim_ctx *ctx, const uint64_t *offsets, uint32_t q,
+                            const uint32_t *seeds, double *est_out, int on_device);
+
+/* Counters of the last build / greedy call (see SKIM_STAT_* indices). */
+#define SKIM_STAT_REV_VISITS 0      /* (node, rank) visits of reverse searches */
+#define SKIM_STAT_REV_COINS 1       /* coins evaluated by reverse searches */
+#define SKIM_STAT_INSERTIONS 2      /* sketch insertions (build) or commits (greedy) */
+#define SKIM_STAT_FWD_VISITS 3      /* (node, instance) pairs covered by residual searches */
+#define SKIM_STAT_FWD_COINS 4       /* coins evaluated by residual searches */
+#define SKIM_STAT_BATCHES 5         /* rank batches */
+#define SKIM_STAT_RANKS 6           /* ranks consumed */
+#define SKIM_STAT_RETRIES 7         /* batches re-run with fewer lanes after a table overflow */
+#define SKIM_STAT_COUNT 8
+int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
+
+int skim_destroy(skim_ctx *ctx);
+
+const char *skim_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKIM_H */
