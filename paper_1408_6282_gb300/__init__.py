@@ -1,0 +1,214 @@
+"""Python binding of libskim (SKIM and the sketch-based influence oracle on a
+GB300 GPU).  Argument marshalling only: every step of the computation runs in
+the CUDA library.  There is no CPU fallback -- if ``libskim.so`` is missing
+or fails to load, every call raises.
+
+The module-level functions carry the names of the C ABI (``include/skim.h``);
+:class:`Skim` wraps them for numpy / torch callers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libskim.so")
+
+SKIM_OK = 0
+_ERR = {-1: "SKIM_EINVAL", -2: "SKIM_ENOMEM", -3: "SKIM_ENOTBUILT", -4: "SKIM_ETIMEOUT", -5: "SKIM_ECUDA",
+        -6: "SKIM_EGRAPH", -7: "SKIM_ERANGE"}
+PROB_UNIFORM, PROB_WC, PROB_TRIVALENCY = 0, 1, 2
+STAT_NAMES = ("rev_visits", "rev_coins", "insertions", "fwd_visits", "fwd_coins", "batches", "ranks", "retries")
+
+
+class SkimError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_ERR.get(code, code)} ({code})")
+        self.code = code
+
+
+class skim_graph(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("m", C.c_uint64), ("src", C.c_void_p), ("dst", C.c_void_p),
+                ("on_device", C.c_int)]
+
+
+class skim_params(C.Structure):
+    _fields_ = [("l", C.c_uint32), ("k", C.c_uint32), ("prob_model", C.c_int), ("p", C.c_double),
+                ("coin_key", C.c_uint64), ("rank_key", C.c_uint64), ("prob_key", C.c_uint64),
+                ("batch_lanes", C.c_uint32)]
+
+
+_lib = None
+
+
+def load():
+    """Load libskim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libskim.so not found at {LIB_PATH}; build it with "
+                           "`python -m paper_1408_6282_gb300.build` (needs nvcc)")
+    lib = C.CDLL(LIB_PATH)
+    vp, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
+    lib.skim_create.argtypes = [C.POINTER(skim_graph), C.POINTER(skim_params), vp, C.POINTER(vp)]
+    lib.skim_build_sketches.argtypes = [vp]
+    lib.skim_get_sketches.argtypes = [vp, vp, vp, C.c_int]
+    lib.skim_sketch_pointers.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
+    lib.skim_greedy.argtypes = [vp, u32, vp, vp]
+    lib.skim_greedy_reset.argtypes = [vp]
+    lib.skim_oracle_query.argtypes = [vp, vp, u32, vp]
+    lib.skim_oracle_query_batch.argtypes = [vp, vp, u32, vp, vp, C.c_int]
+    lib.skim_get_stats.argtypes = [vp, vp, u32]
+    lib.skim_destroy.argtypes = [vp]
+    lib.skim_strerror.argtypes = [C.c_int]
+    lib.skim_strerror.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != SKIM_OK:
+        raise SkimError(rc, what)
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+# ---- C ABI names -------------------------------------------------------------
+
+def skim_create(graph: skim_graph, params: skim_params, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load().skim_create(C.byref(graph), C.byref(params), C.c_void_p(stream or None), C.byref(h)),
+           "skim_create")
+    return h.value
+
+
+def skim_build_sketches(ctx: int):
+    _check(load().skim_build_sketches(ctx), "skim_build_sketches")
+
+
+def skim_get_sketches(ctx: int, x_out, len_out, out_on_device: int = 0):
+    _check(load().skim_get_sketches(ctx, _ptr(x_out), _ptr(len_out), out_on_device), "skim_get_sketches")
+
+
+def skim_sketch_pointers(ctx: int) -> tuple[int, int]:
+    x, ln = C.c_void_p(), C.c_void_p()
+    _check(load().skim_sketch_pointers(ctx, C.byref(x), C.byref(ln)), "skim_sketch_pointers")
+    return x.value, ln.value
+
+
+def skim_greedy(ctx: int, n_seeds: int, seeds_out: np.ndarray, cov_out: np.ndarray):
+    _check(load().skim_greedy(ctx, n_seeds, _ptr(seeds_out), _ptr(cov_out)), "skim_greedy")
+
+
+def skim_greedy_reset(ctx: int):
+    _check(load().skim_greedy_reset(ctx), "skim_greedy_reset")
+
+
+def skim_oracle_query(ctx: int, seeds: np.ndarray, n_seeds: int, est_out: np.ndarray):
+    _check(load().skim_oracle_query(ctx, _ptr(seeds) if n_seeds else None, n_seeds, _ptr(est_out)),
+           "skim_oracle_query")
+
+
+def skim_oracle_query_batch(ctx: int, offsets: np.ndarray, q: int, seeds, est_out, on_device: int = 0):
+    _check(load().skim_oracle_query_batch(ctx, _ptr(offsets), q, _ptr(seeds), _ptr(est_out), on_device),
+           "skim_oracle_query_batch")
+
+
+def skim_get_stats(ctx: int, out: np.ndarray, count: int):
+    _check(load().skim_get_stats(ctx, _ptr(out), count), "skim_get_stats")
+
+
+def skim_destroy(ctx: int):
+    _check(load().skim_destroy(ctx), "skim_destroy")
+
+
+def skim_strerror(code: int) -> str:
+    return load().skim_strerror(code).decode()
+
+
+# ---- convenience wrapper -------------------------------------------------------
+
+class Skim:
+    """One graph, its IC parameters and the device state built from them.
+
+    src/dst: canonical edge list (sorted by (src, dst), no duplicates, no
+    self-loops) as uint32 numpy arrays (host) or int32/uint32 CUDA tensors.
+    """
+
+    def __init__(self, n: int, src, dst, l: int, k: int, prob_model: int = PROB_UNIFORM, p: float = 0.1,
+                 coin_key: int = 0, rank_key: int = 0, prob_key: int = 0, batch_lanes: int = 0, stream: int = 0):
+        on_device = not isinstance(src, np.ndarray)
+        if not on_device:
+            src = np.ascontiguousarray(src, dtype=np.uint32)
+            dst = np.ascontiguousarray(dst, dtype=np.uint32)
+        self._keep = (src, dst)
+        m = int(src.shape[0])
+        g = skim_graph(n, m, _ptr(src) if m else None, _ptr(dst) if m else None, 1 if on_device else 0)
+        prm = skim_params(l, k, prob_model, p, coin_key & (2**64 - 1), rank_key & (2**64 - 1),
+                          prob_key & (2**64 - 1), batch_lanes)
+        self.n, self.m, self.l, self.k = n, m, l, k
+        self.ctx = skim_create(g, prm, stream)
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            skim_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def build_sketches(self):
+        skim_build_sketches(self.ctx)
+
+    def sketches(self) -> tuple[np.ndarray, np.ndarray]:
+        x = np.zeros((self.n, self.k), np.uint64)
+        ln = np.zeros(self.n, np.uint32)
+        skim_get_sketches(self.ctx, x, ln, 0)
+        return x, ln
+
+    def greedy(self, n_seeds: int) -> tuple[np.ndarray, np.ndarray]:
+        seeds = np.zeros(max(1, n_seeds), np.uint32)
+        cov = np.zeros(max(1, n_seeds), np.uint64)
+        skim_greedy(self.ctx, n_seeds, seeds, cov)
+        return seeds[:n_seeds], cov[:n_seeds]
+
+    def greedy_reset(self):
+        skim_greedy_reset(self.ctx)
+
+    def query(self, seeds) -> float:
+        s = np.ascontiguousarray(seeds, dtype=np.uint32)
+        out = np.zeros(1, np.float64)
+        skim_oracle_query(self.ctx, s, int(s.shape[0]), out)
+        return float(out[0])
+
+    def query_batch(self, seed_sets) -> np.ndarray:
+        sets = [np.ascontiguousarray(s, dtype=np.uint32) for s in seed_sets]
+        off = np.zeros(len(sets) + 1, np.uint64)
+        off[1:] = np.cumsum([s.shape[0] for s in sets])
+        flat = np.concatenate(sets) if sets and off[-1] else np.zeros(1, np.uint32)
+        out = np.zeros(max(1, len(sets)), np.float64)
+        skim_oracle_query_batch(self.ctx, off, len(sets), flat, out, 0)
+        return out[: len(sets)]
+
+    def stats(self) -> dict:
+        out = np.zeros(len(STAT_NAMES), np.uint64)
+        skim_get_stats(self.ctx, out, len(STAT_NAMES))
+        return dict(zip(STAT_NAMES, (int(v) for v in out)))

@@ -1,0 +1,277 @@
+// batch.cu -- per-batch steps after a reverse search has marked, for every
+// visited (node, lane word), the lanes that reached the node.  Visit records
+// (node << tbits | word, table slot) arrive sorted by key, so each node's
+// words form one run in increasing rank order.
+//
+// Algorithm 2 acceptance (Section 5.2): for node v and instance i the first
+// k - lcnt[v][i] lanes of instance i (in rank order) join v's local sketch;
+// the ranks that join also enter the global sketch X_v while it holds fewer
+// than k ranks.  Batches advance in increasing rank order, so X_v is filled
+// in increasing order and needs no merge: appending is the bottom-k merge of
+// Algorithm 2.  Pruning in the search used the counts at the start of the
+// batch, so every lane whose rank belongs in a local sketch did reach it.
+//
+// SKIM (Algorithm 1): size[v] counts the processed, uncovered ranks that reach
+// v.  The batch's stop lane is the earliest lane at which some node's size
+// reaches k (smallest node id on ties); lanes up to it are committed (sizes
+// and the inverted index), the rest stay valid for the next step because a
+// search from an uncovered pair never meets a covered node.
+#include "internal.cuh"
+
+namespace skim {
+
+namespace {
+
+inline unsigned grid_for(size_t n, int threads, unsigned cap = 152 * 32) {
+    size_t g = (n + threads - 1) / threads;
+    if (g > cap) g = cap;
+    return static_cast<unsigned>(g ? g : 1);
+}
+
+__global__ void k_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < B; j += gridDim.x * blockDim.x)
+        lane_inst[j] = static_cast<uint8_t>(lane_pair[j] % l);
+    // pad the last word so that reads of absent lanes stay in bounds and harmless
+}
+
+SKIM_DEV bool run_start(const uint64_t *rec_key, uint64_t r, uint32_t tbits) {
+    return r == 0 || (rec_key[r] >> tbits) != (rec_key[r - 1] >> tbits);
+}
+
+__global__ void k_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                         const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
+                         uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl) {
+    unsigned long long ins = 0;
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        if (!run_start(rec_key, r, tbits)) continue;
+        const uint64_t v = rec_key[r] >> tbits;
+        uint8_t *lc = lcnt + v * l;
+        uint64_t *xv = X + v * k;
+        uint32_t len = xlen[v];
+        uint64_t newfull = 0;
+        const uint64_t tmask = (1ull << tbits) - 1;
+        for (uint64_t rr = r; rr < R && (rec_key[rr] >> tbits) == v; rr++) {
+            const uint64_t t = rec_key[rr] & tmask;
+            uint64_t m = hvals[rec_val[rr]];
+            while (m) {
+                int j = __ffsll(m) - 1;
+                m &= m - 1;
+                const uint64_t lane = t * 64 + j;
+                const uint32_t i = lane_inst[lane];
+                const uint32_t c = lc[i];
+                if (c < k) {
+                    lc[i] = static_cast<uint8_t>(c + 1);
+                    ins++;
+                    if (c + 1 == k) newfull |= 1ull << i;
+                    if (len < k) xv[len++] = lane_rank[lane];
+                }
+            }
+        }
+        xlen[v] = len;
+        if (newfull) full[v] |= newfull;
+    }
+    warp_add(&ctl->stats[kStInsert], ins);
+}
+
+__global__ void k_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hkeys, uint64_t *hvals) {
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        uint32_t s = rec_val[r];
+        hkeys[s] = kEmptyKey;
+        hvals[s] = 0;
+    }
+}
+
+// lanes of word t inside [lo, hi] (inclusive), lo <= hi
+SKIM_DEV uint64_t range_mask(uint64_t t, uint32_t lo, uint32_t hi) {
+    const uint64_t w0 = t * 64, w1 = w0 + 63;
+    if (w1 < lo || w0 > hi) return 0;
+    uint64_t m = ~0ull;
+    if (lo > w0) m &= ~0ull << (lo - w0);
+    if (hi < w1) m &= ~0ull >> (w1 - hi);
+    return m;
+}
+
+__global__ void k_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                             const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
+                             uint32_t k, DevCtl *ctl) {
+    const uint64_t tmask = (1ull << tbits) - 1;
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        if (!run_start(rec_key, r, tbits)) continue;
+        const uint64_t v = rec_key[r] >> tbits;
+        const uint32_t need = k - size[v];
+        uint32_t cum = 0;
+        for (uint64_t rr = r; rr < R && (rec_key[rr] >> tbits) == v; rr++) {
+            const uint64_t t = rec_key[rr] & tmask;
+            uint64_t m = hvals[rec_val[rr]] & alive[t] & range_mask(t, lo, 0xffffffffu);
+            uint32_t c = __popcll(m);
+            if (cum + c >= need) {
+                uint64_t p = t * 64 + nth_set_bit(m, static_cast<int>(need - cum - 1));
+                atomicMin(&ctl->best, (p << 32) | v);
+                break;
+            }
+            cum += c;
+        }
+    }
+}
+
+__global__ void k_commit_count(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                               const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size,
+                               unsigned long long *lane_cnt, DevCtl *ctl) {
+    const uint64_t tmask = (1ull << tbits) - 1;
+    unsigned long long ins = 0;
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        if (!run_start(rec_key, r, tbits)) continue;
+        const uint64_t v = rec_key[r] >> tbits;
+        uint32_t add = 0;
+        for (uint64_t rr = r; rr < R && (rec_key[rr] >> tbits) == v; rr++) {
+            const uint64_t t = rec_key[rr] & tmask;
+            uint64_t m = hvals[rec_val[rr]] & alive[t] & range_mask(t, lo, hi);
+            add += __popcll(m);
+            while (m) {
+                int j = __ffsll(m) - 1;
+                m &= m - 1;
+                atomicAdd(&lane_cnt[t * 64 + j], 1ull);
+            }
+        }
+        if (add) size[v] += add;
+        ins += add;
+    }
+    warp_add(&ctl->stats[kStInsert], ins);
+}
+
+__global__ void k_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                                 const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi,
+                                 const uint64_t *lane_off, uint32_t *lane_fill, uint64_t idx_base,
+                                 uint32_t *idx_nodes) {
+    const uint64_t tmask = (1ull << tbits) - 1;
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t v = rec_key[r] >> tbits;
+        const uint64_t t = rec_key[r] & tmask;
+        uint64_t m = hvals[rec_val[r]] & alive[t] & range_mask(t, lo, hi);
+        while (m) {
+            int j = __ffsll(m) - 1;
+            m &= m - 1;
+            const uint64_t lane = t * 64 + j;
+            uint32_t pos = atomicAdd(&lane_fill[lane], 1u);
+            idx_nodes[idx_base + lane_off[lane] + pos] = static_cast<uint32_t>(v);
+        }
+    }
+}
+
+__global__ void k_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32_t hi, const uint64_t *lane_cnt,
+                                  const uint64_t *lane_off, uint64_t idx_base, uint64_t *seg_start,
+                                  uint32_t *seg_len) {
+    for (uint64_t j = lo + blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; j <= hi;
+         j += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        uint64_t c = lane_cnt[j];
+        if (c) {
+            uint32_t pr = lane_pair[j];
+            seg_start[pr] = idx_base + lane_off[j];
+            seg_len[pr] = static_cast<uint32_t>(c);
+        }
+    }
+}
+
+__global__ void k_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, uint32_t l, const uint64_t *covered,
+                           uint64_t *alive) {
+    for (uint32_t j = lo + blockIdx.x * blockDim.x + threadIdx.x; j < B; j += gridDim.x * blockDim.x) {
+        const uint64_t bit = 1ull << (j & 63);
+        if (!(alive[j >> 6] & bit)) continue;
+        uint32_t pr = lane_pair[j];
+        uint32_t u = pr / l, i = pr % l;
+        if ((covered[u] >> i) & 1ull) atomicAnd(reinterpret_cast<unsigned long long *>(&alive[j >> 6]), ~bit);
+    }
+}
+
+__global__ void k_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl) {
+    unsigned long long best = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        unsigned long long key = (static_cast<unsigned long long>(size[v]) << 32) | (0xffffffffu - v);
+        best = max(best, key);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_down_sync(kFull, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&ctl->argmax, best);
+}
+
+__global__ void k_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl) {
+    unsigned long long best = ~0ull;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (!chosen[v]) best = min(best, static_cast<unsigned long long>(v));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(kFull, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(&ctl->best, best);
+}
+
+}  // namespace
+
+cudaError_t launch_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, cudaStream_t s) {
+    k_lane_inst<<<grid_for(B, 256), 256, 0, s>>>(lane_pair, B, l, lane_inst);
+    return cudaGetLastError();
+}
+cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                          const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
+                          uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
+                          cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    k_accept<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, lane_inst, lane_rank, l, k, lcnt,
+                                              full, X, xlen, ctl);
+    return cudaGetLastError();
+}
+cudaError_t launch_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hkeys, uint64_t *hvals, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    k_clear_slots<<<grid_for(R, 256), 256, 0, s>>>(rec_val, R, hkeys, hvals);
+    return cudaGetLastError();
+}
+cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                              const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
+                              uint32_t k, DevCtl *ctl, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    k_candidates<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, size, k, ctl);
+    return cudaGetLastError();
+}
+cudaError_t launch_commit_count(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                                const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size,
+                                uint64_t *lane_cnt, DevCtl *ctl, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    k_commit_count<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, hi, size,
+                                                    reinterpret_cast<unsigned long long *>(lane_cnt), ctl);
+    return cudaGetLastError();
+}
+cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                                  const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi,
+                                  const uint64_t *lane_off, uint32_t *lane_fill, uint64_t idx_base,
+                                  uint32_t *idx_nodes, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    k_commit_scatter<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, hi, lane_off,
+                                                      lane_fill, idx_base, idx_nodes);
+    return cudaGetLastError();
+}
+cudaError_t launch_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32_t hi, const uint64_t *lane_cnt,
+                                   const uint64_t *lane_off, uint64_t idx_base, uint64_t *seg_start,
+                                   uint32_t *seg_len, cudaStream_t s) {
+    k_commit_segments<<<grid_for(hi - lo + 1, 256), 256, 0, s>>>(lane_pair, lo, hi, lane_cnt, lane_off, idx_base,
+                                                                 seg_start, seg_len);
+    return cudaGetLastError();
+}
+cudaError_t launch_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, uint32_t l, const uint64_t *covered,
+                            uint64_t *alive, cudaStream_t s) {
+    if (lo >= B) return cudaSuccess;
+    k_refilter<<<grid_for(B - lo, 256), 256, 0, s>>>(lane_pair, lo, B, l, covered, alive);
+    return cudaGetLastError();
+}
+cudaError_t launch_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl, cudaStream_t s) {
+    k_argmax_size<<<grid_for(n, 256), 256, 0, s>>>(size, n, ctl);
+    return cudaGetLastError();
+}
+cudaError_t launch_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl, cudaStream_t s) {
+    k_min_unchosen<<<grid_for(n, 256), 256, 0, s>>>(chosen, n, ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace skim

@@ -1,0 +1,798 @@
+// capi.cu -- libskim C ABI: context, graph and rank setup, the rank-batched
+// sketch build (Algorithm 2), SKIM (Algorithm 1) and influence queries
+// (Eq. unionest).  Host code orchestrates; all per-element work runs in the
+// kernels of graph.cu, traverse.cu, batch.cu and query.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "prims.cuh"
+#include "skim.h"
+
+using namespace skim;
+
+struct skim_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool broken = false;
+    uint32_t n = 0;
+    uint64_t m = 0;
+    uint32_t l = 0, k = 0;
+    uint64_t nl = 0;
+    CoinModel cm{};
+    uint32_t batch_cfg = 0;
+    // graph
+    uint32_t *fptr = nullptr, *fcol = nullptr, *rptr = nullptr, *rcol = nullptr;
+    uint64_t *thr_wc = nullptr;
+    // rank order
+    uint64_t *srank = nullptr;
+    uint32_t *spair = nullptr;
+    // control
+    DevCtl *ctl = nullptr;
+    DevCtl *hctl = nullptr;  // pinned mirror
+    unsigned *dflag = nullptr;
+    // traversal scratch
+    Item *q = nullptr;
+    uint64_t qcap = 0;
+    uint64_t *hkeys = nullptr, *hvals = nullptr, *pend = nullptr;
+    uint64_t hcap = 0;
+    uint64_t *rkey = nullptr, *rkey2 = nullptr;
+    uint32_t *rval = nullptr, *rval2 = nullptr;
+    uint64_t rcap = 0;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    uint8_t *lane_inst = nullptr;
+    uint64_t *alive = nullptr, *lane_cnt = nullptr, *lane_off = nullptr;
+    uint32_t *lane_fill = nullptr;
+    uint32_t lane_cap = 0;
+    int grid_rev = 0, grid_fwd = 0;
+    uint64_t timeout_ns = 2000000000ull;
+    // sketches
+    uint8_t *lcnt = nullptr;
+    uint64_t *full = nullptr, *X = nullptr;
+    uint32_t *xlen = nullptr;
+    bool built = false;
+    // SKIM
+    bool sk_init = false;
+    uint64_t *covered = nullptr, *seg_start = nullptr, *pend_trav = nullptr, *pend_erase = nullptr;
+    uint32_t *size = nullptr, *seg_len = nullptr, *idx = nullptr;
+    uint8_t *chosen = nullptr;
+    uint64_t idx_cap = 0, idx_used = 0;
+    uint64_t cursor = 0;
+    uint32_t nseeds = 0;
+    bool batch_active = false;
+    uint64_t bp0 = 0;
+    uint32_t bB = 0, btbits = 0, blo = 0;
+    uint64_t bR = 0;
+    uint32_t skim_B = 0;
+    // queries
+    uint64_t *qk = nullptr, *qv = nullptr;
+    uint64_t qtcap = 0;
+    uint32_t *qseeds = nullptr;
+    uint64_t qseeds_cap = 0;
+    uint64_t *qoff = nullptr, *qtoff = nullptr;
+    double *qout = nullptr;
+    uint64_t qmeta_cap = 0;
+    // counters of the last build/greedy call
+    uint64_t hstats[SKIM_STAT_COUNT] = {0};
+};
+
+namespace {
+
+int fail_cuda(skim_ctx *c, cudaError_t e) {
+    if (c) c->broken = true;
+    if (getenv("SKIM_DEBUG")) fprintf(stderr, "libskim: CUDA error %s\n", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SKIM_ENOMEM : SKIM_ECUDA;
+}
+
+#define CK(c, x)                                       \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return fail_cuda(c, e_); \
+    } while (0)
+
+#define RC(x)                 \
+    do {                      \
+        int r_ = (x);         \
+        if (r_ != SKIM_OK) return r_; \
+    } while (0)
+
+template <class T>
+int dalloc(skim_ctx *c, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? SKIM_ENOMEM : fail_cuda(c, e);
+    }
+    return SKIM_OK;
+}
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+int bitlen(uint64_t x) {  // bits needed to hold values 0..x
+    int b = 0;
+    while (b < 64 && (x >> b)) b++;
+    return b;
+}
+
+uint64_t pow2_at_least(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+uint64_t tm1_of(double p) {
+    if (p >= 1.0) return ~0ull;
+    return static_cast<uint64_t>(std::ldexp(p, 64)) - 1ull;
+}
+
+int sync_ctl(skim_ctx *c) {
+    CK(c, cudaMemcpyAsync(c->hctl, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    return SKIM_OK;
+}
+
+// zero the queue/control fields of DevCtl, keep the statistics
+int reset_ctl(skim_ctx *c) {
+    CK(c, cudaMemsetAsync(c->ctl, 0, offsetof(DevCtl, stats), c->st));
+    CK(c, cudaMemsetAsync(&c->ctl->err, 0, sizeof(unsigned) * 4, c->st));
+    return SKIM_OK;
+}
+
+int reset_queue(skim_ctx *c, uint64_t used) {
+    uint64_t u = std::min(used, c->qcap);
+    if (u) CK(c, cudaMemsetAsync(c->q, 0, u * sizeof(Item), c->st));
+    CK(c, cudaMemsetAsync(c->ctl, 0, 3 * sizeof(unsigned long long), c->st));
+    CK(c, cudaMemsetAsync(&c->ctl->spill, 0, sizeof(unsigned), c->st));
+    return SKIM_OK;
+}
+
+TravArgs base_args(skim_ctx *c, bool forward) {
+    TravArgs a{};
+    a.ptr = forward ? c->fptr : c->rptr;
+    a.col = forward ? c->fcol : c->rcol;
+    a.cm = c->cm;
+    a.q = c->q;
+    a.qcap = c->qcap;
+    a.ctl = c->ctl;
+    a.timeout_ns = c->timeout_ns;
+    a.hkeys = c->hkeys;
+    a.hvals = c->hvals;
+    a.hmask = c->hcap - 1;
+    a.rec_key = c->rkey;
+    a.rec_val = c->rval;
+    a.rcap = c->rcap;
+    a.lane_inst = c->lane_inst;
+    a.full = c->full;
+    a.pend = c->pend;
+    a.covered = c->covered;
+    a.seg_start = c->seg_start;
+    a.seg_len = c->seg_len;
+    a.size = c->size;
+    a.idx_nodes = c->idx;
+    a.l = c->l;
+    a.pend_trav = c->pend_trav;
+    a.pend_erase = c->pend_erase;
+    return a;
+}
+
+// Run traversal rounds until the queue drains with nothing spilled.
+int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out) {
+    for (;;) {
+        CK(c, launch_traverse(a, forward, forward ? c->grid_fwd : c->grid_rev, c->st));
+        RC(sync_ctl(c));
+        const DevCtl &h = *c->hctl;
+        if (h.err & kErrTimeout) {
+            c->broken = true;
+            return SKIM_ETIMEOUT;
+        }
+        if (R_out) *R_out = h.rec_count;
+        if (h.err & kErrRetryable) return SKIM_OK;  // caller re-runs the batch
+        if (!h.spill) return SKIM_OK;
+        RC(reset_queue(c, h.q_tail));
+        if (forward)
+            CK(c, launch_respill_fwd(a, c->n, c->st));
+        else
+            CK(c, launch_respill_rev(a, h.rec_count, c->st));
+    }
+}
+
+// Reverse search of the batch of ranks [p0, p0+B).  mode_build: Algorithm 2
+// (pruned by local counts); otherwise SKIM (covered sources skipped).
+// Returns SKIM_OK with *retry set if the batch overflowed its tables.
+int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry) {
+    *retry = false;
+    const uint32_t T = (B + 63) / 64;
+    const uint32_t tbits = bitlen(T - 1);
+    RC(reset_ctl(c));
+    CK(c, launch_lane_inst(c->spair + p0, B, c->l, c->lane_inst, c->st));
+    if (!mode_build) CK(c, cudaMemsetAsync(c->alive, 0, T * sizeof(uint64_t), c->st));
+    TravArgs a = base_args(c, false);
+    a.tbits = tbits;
+    a.prune = mode_build ? 1 : 0;
+    CK(c, launch_rev_sources(a, c->spair + p0, B, c->l, mode_build ? nullptr : c->covered,
+                             mode_build ? nullptr : c->alive, c->st));
+    uint64_t R = 0;
+    RC(run_traversal(c, a, false, &R));
+    const DevCtl &h = *c->hctl;
+    if (h.err & kErrRetryable) {
+        *retry = true;
+        RC(reset_queue(c, h.q_tail));
+        CK(c, cudaMemsetAsync(c->hkeys, 0xff, c->hcap * sizeof(uint64_t), c->st));
+        CK(c, cudaMemsetAsync(c->hvals, 0, c->hcap * sizeof(uint64_t), c->st));
+        CK(c, cudaMemsetAsync(c->pend, 0, c->hcap * sizeof(uint64_t), c->st));
+        c->hstats[SKIM_STAT_RETRIES]++;
+        return SKIM_OK;
+    }
+    RC(reset_queue(c, h.q_tail));
+    const int bits = bitlen(c->n - 1) + static_cast<int>(tbits);
+    CK(c, radix_sort_pairs(c->rkey, c->rval, c->rkey2, c->rval2, R, bits, c->ws, c->st));
+    c->bR = R;
+    c->btbits = tbits;
+    c->hstats[SKIM_STAT_BATCHES]++;
+    return SKIM_OK;
+}
+
+int clear_batch(skim_ctx *c) {
+    CK(c, launch_clear_slots(c->rval, c->bR, c->hkeys, c->hvals, c->st));
+    c->bR = 0;
+    return SKIM_OK;
+}
+
+int pull_stats(skim_ctx *c) {
+    RC(sync_ctl(c));
+    c->hstats[SKIM_STAT_REV_VISITS] = c->hctl->stats[kStRevVisits];
+    c->hstats[SKIM_STAT_REV_COINS] = c->hctl->stats[kStRevCoins];
+    c->hstats[SKIM_STAT_INSERTIONS] = c->hctl->stats[kStInsert];
+    c->hstats[SKIM_STAT_FWD_VISITS] = c->hctl->stats[kStFwdVisits];
+    c->hstats[SKIM_STAT_FWD_COINS] = c->hctl->stats[kStFwdCoins];
+    return SKIM_OK;
+}
+
+int reset_stats(skim_ctx *c) {
+    CK(c, cudaMemsetAsync(c->ctl->stats, 0, sizeof(c->ctl->stats), c->st));
+    std::fill(c->hstats, c->hstats + SKIM_STAT_COUNT, 0);
+    return SKIM_OK;
+}
+
+uint32_t default_lanes(skim_ctx *c) {
+    uint64_t b = c->batch_cfg ? c->batch_cfg : (1u << 18);
+    b = std::min<uint64_t>(b, static_cast<uint64_t>(kMaxWords) * 64);
+    b = std::min<uint64_t>(b, c->lane_cap);
+    return static_cast<uint32_t>(std::max<uint64_t>(64, b));
+}
+
+// ---- SKIM steps ------------------------------------------------------------
+
+int skim_state_init(skim_ctx *c) {
+    if (!c->covered) {
+        RC(dalloc(c, &c->covered, c->n));
+        RC(dalloc(c, &c->size, c->n));
+        RC(dalloc(c, &c->seg_start, c->nl));
+        RC(dalloc(c, &c->seg_len, c->nl));
+        RC(dalloc(c, &c->chosen, c->n));
+        RC(dalloc(c, &c->pend_trav, c->n));
+        RC(dalloc(c, &c->pend_erase, c->n));
+    }
+    CK(c, cudaMemsetAsync(c->covered, 0, c->n * sizeof(uint64_t), c->st));
+    CK(c, cudaMemsetAsync(c->size, 0, c->n * sizeof(uint32_t), c->st));
+    CK(c, cudaMemsetAsync(c->seg_len, 0, c->nl * sizeof(uint32_t), c->st));
+    CK(c, cudaMemsetAsync(c->chosen, 0, c->n, c->st));
+    CK(c, cudaMemsetAsync(c->pend_trav, 0, c->n * sizeof(uint64_t), c->st));
+    CK(c, cudaMemsetAsync(c->pend_erase, 0, c->n * sizeof(uint64_t), c->st));
+    if (c->batch_active) RC(clear_batch(c));
+    c->idx_used = 0;
+    c->cursor = 0;
+    c->nseeds = 0;
+    c->batch_active = false;
+    c->skim_B = 0;
+    c->sk_init = true;
+    return SKIM_OK;
+}
+
+int ensure_idx(skim_ctx *c, uint64_t need) {
+    if (need <= c->idx_cap) return SKIM_OK;
+    uint64_t cap = std::max<uint64_t>(need + need / 2, 1ull << 22);
+    uint32_t *nb = nullptr;
+    RC(dalloc(c, &nb, cap));
+    if (c->idx_used) CK(c, cudaMemcpyAsync(nb, c->idx, c->idx_used * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    dfree(c->idx);
+    c->idx = nb;
+    c->idx_cap = cap;
+    return SKIM_OK;
+}
+
+// Commit lanes [lo, hi] of the active batch: sizes and the inverted index.
+int commit_lanes(skim_ctx *c, uint32_t lo, uint32_t hi) {
+    if (lo > hi) return SKIM_OK;
+    const uint32_t cnt = hi - lo + 1;
+    CK(c, cudaMemsetAsync(c->lane_cnt + lo, 0, cnt * sizeof(uint64_t), c->st));
+    CK(c, cudaMemsetAsync(c->lane_fill + lo, 0, cnt * sizeof(uint32_t), c->st));
+    CK(c, launch_commit_count(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, lo, hi, c->size, c->lane_cnt,
+                              c->ctl, c->st));
+    CK(c, exclusive_scan_u64(c->lane_cnt + lo, c->lane_off + lo, cnt, reinterpret_cast<uint64_t *>(&c->ctl->total), c->ws, c->st));
+    RC(sync_ctl(c));
+    const uint64_t tot = c->hctl->total;
+    RC(ensure_idx(c, c->idx_used + tot));
+    CK(c, launch_commit_scatter(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, lo, hi, c->lane_off,
+                                c->lane_fill, c->idx_used, c->idx, c->st));
+    CK(c, launch_commit_segments(c->spair + c->bp0, lo, hi, c->lane_cnt, c->lane_off, c->idx_used, c->seg_start,
+                                 c->seg_len, c->st));
+    c->idx_used += tot;
+    return SKIM_OK;
+}
+
+// Residual problem for seed x: forward search in every instance.
+int residual(skim_ctx *c, uint32_t x, uint64_t *cov) {
+    RC(reset_ctl(c));
+    TravArgs a = base_args(c, true);
+    CK(c, launch_fwd_source(a, x, c->st));
+    RC(run_traversal(c, a, true, nullptr));
+    *cov = c->hctl->ix_cov;
+    RC(reset_queue(c, c->hctl->q_tail));
+    CK(c, cudaMemsetAsync(c->chosen + x, 1, 1, c->st));
+    return SKIM_OK;
+}
+
+int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
+    for (;;) {
+        if (c->batch_active) {
+            CK(c, cudaMemsetAsync(&c->ctl->best, 0xff, sizeof(unsigned long long), c->st));
+            CK(c, launch_candidates(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, c->blo, c->size, c->k,
+                                    c->ctl, c->st));
+            RC(sync_ctl(c));
+            const uint64_t best = c->hctl->best;
+            if (best != ~0ull) {
+                const uint32_t p = static_cast<uint32_t>(best >> 32);
+                const uint32_t x = static_cast<uint32_t>(best & 0xffffffffu);
+                RC(commit_lanes(c, c->blo, p));
+                RC(residual(c, x, cov_out));
+                c->blo = p + 1;
+                CK(c, launch_refilter(c->spair + c->bp0, c->blo, c->bB, c->l, c->covered, c->alive, c->st));
+                *x_out = x;
+                return SKIM_OK;
+            }
+            RC(commit_lanes(c, c->blo, c->bB - 1));
+            RC(clear_batch(c));
+            c->batch_active = false;
+            continue;
+        }
+        if (c->cursor < c->nl) {
+            if (!c->skim_B) c->skim_B = std::min<uint32_t>(default_lanes(c), 1u << 14);
+            uint32_t B = static_cast<uint32_t>(std::min<uint64_t>(c->skim_B, c->nl - c->cursor));
+            bool retry = false;
+            RC(rev_batch(c, c->cursor, B, false, &retry));
+            if (retry) {
+                c->skim_B = std::max<uint32_t>(64, B / 2);
+                continue;
+            }
+            c->batch_active = true;
+            c->bp0 = c->cursor;
+            c->bB = B;
+            c->blo = 0;
+            c->cursor += B;
+            c->hstats[SKIM_STAT_RANKS] += B;
+            c->skim_B = std::min<uint32_t>(default_lanes(c), c->skim_B * 2);
+            continue;
+        }
+        // ranks exhausted: the largest partial sketch (ties to the smallest id)
+        CK(c, cudaMemsetAsync(&c->ctl->argmax, 0, sizeof(unsigned long long), c->st));
+        CK(c, launch_argmax_size(c->size, c->n, c->ctl, c->st));
+        RC(sync_ctl(c));
+        uint64_t am = c->hctl->argmax;
+        uint32_t x = 0xffffffffu - static_cast<uint32_t>(am & 0xffffffffu);
+        if ((am >> 32) == 0) {
+            CK(c, cudaMemsetAsync(&c->ctl->best, 0xff, sizeof(unsigned long long), c->st));
+            CK(c, launch_min_unchosen(c->chosen, c->n, c->ctl, c->st));
+            RC(sync_ctl(c));
+            x = static_cast<uint32_t>(c->hctl->best);
+        }
+        RC(residual(c, x, cov_out));
+        *x_out = x;
+        return SKIM_OK;
+    }
+}
+
+int ensure_query_space(skim_ctx *c, uint64_t seeds, uint64_t q, uint64_t table) {
+    if (seeds > c->qseeds_cap) {
+        dfree(c->qseeds);
+        c->qseeds_cap = std::max<uint64_t>(seeds, 4096);
+        RC(dalloc(c, &c->qseeds, c->qseeds_cap));
+    }
+    if (q + 1 > c->qmeta_cap) {
+        dfree(c->qoff);
+        dfree(c->qtoff);
+        dfree(c->qout);
+        c->qmeta_cap = std::max<uint64_t>(q + 1, 1024);
+        RC(dalloc(c, &c->qoff, c->qmeta_cap));
+        RC(dalloc(c, &c->qtoff, c->qmeta_cap));
+        RC(dalloc(c, &c->qout, c->qmeta_cap));
+    }
+    if (table > c->qtcap) {
+        dfree(c->qk);
+        dfree(c->qv);
+        c->qtcap = std::max<uint64_t>(table, 1ull << 16);
+        RC(dalloc(c, &c->qk, c->qtcap));
+        RC(dalloc(c, &c->qv, c->qtcap));
+    }
+    return SKIM_OK;
+}
+
+uint64_t query_table(uint64_t s, uint32_t k) { return pow2_at_least(std::max<uint64_t>(64, 2 * s * (k - 1) + 2)); }
+
+}  // namespace
+
+extern "C" {
+
+const char *skim_strerror(int code) {
+    switch (code) {
+        case SKIM_OK: return "ok";
+        case SKIM_EINVAL: return "invalid argument";
+        case SKIM_ENOMEM: return "out of memory";
+        case SKIM_ENOTBUILT: return "sketches not built";
+        case SKIM_ETIMEOUT: return "device wait timed out";
+        case SKIM_ECUDA: return "CUDA error";
+        case SKIM_EGRAPH: return "edge list not canonical";
+        case SKIM_ERANGE: return "size out of range";
+        default: return "unknown error";
+    }
+}
+
+int skim_destroy(skim_ctx *c) {
+    if (!c) return SKIM_EINVAL;
+    cudaStreamSynchronize(c->st);
+    dfree(c->fptr); dfree(c->fcol); dfree(c->rptr); dfree(c->rcol); dfree(c->thr_wc);
+    dfree(c->srank); dfree(c->spair);
+    dfree(c->ctl); dfree(c->dflag);
+    if (c->hctl) cudaFreeHost(c->hctl);
+    dfree(c->q); dfree(c->hkeys); dfree(c->hvals); dfree(c->pend);
+    dfree(c->rkey); dfree(c->rkey2); dfree(c->rval); dfree(c->rval2);
+    if (c->ws) cudaFree(c->ws);
+    dfree(c->lane_inst); dfree(c->alive); dfree(c->lane_cnt); dfree(c->lane_off); dfree(c->lane_fill);
+    dfree(c->lcnt); dfree(c->full); dfree(c->X); dfree(c->xlen);
+    dfree(c->covered); dfree(c->seg_start); dfree(c->pend_trav); dfree(c->pend_erase);
+    dfree(c->size); dfree(c->seg_len); dfree(c->idx); dfree(c->chosen);
+    dfree(c->qk); dfree(c->qv); dfree(c->qseeds); dfree(c->qoff); dfree(c->qtoff); dfree(c->qout);
+    delete c;
+    return SKIM_OK;
+}
+
+int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_ctx **out) {
+    if (!g || !prm || !out) return SKIM_EINVAL;
+    *out = nullptr;
+    if (g->n == 0 || prm->l == 0 || prm->l > 64 || prm->k < 2 || prm->k > 255) return SKIM_EINVAL;
+    if (prm->prob_model < 0 || prm->prob_model > 2) return SKIM_EINVAL;
+    if (prm->prob_model == 0 && !(prm->p > 0.0 && prm->p <= 1.0)) return SKIM_EINVAL;
+    if (prm->prob_model == 0 && prm->p < 1.0 && static_cast<uint64_t>(std::ldexp(prm->p, 64)) == 0) return SKIM_EINVAL;
+    if (g->m && (!g->src || !g->dst)) return SKIM_EINVAL;
+    if (g->m >= (1ull << 32)) return SKIM_ERANGE;
+    const uint64_t nl = static_cast<uint64_t>(g->n) * prm->l;
+    if (nl > 0xffffffffull) return SKIM_ERANGE;
+
+    skim_ctx *c = new (std::nothrow) skim_ctx();
+    if (!c) return SKIM_ENOMEM;
+    cudaGetDevice(&c->device);
+    c->st = static_cast<cudaStream_t>(stream);
+    c->n = g->n;
+    c->m = g->m;
+    c->l = prm->l;
+    c->k = prm->k;
+    c->nl = nl;
+    c->batch_cfg = prm->batch_lanes;
+    c->cm.model = prm->prob_model;
+    c->cm.tm1_uniform = prm->prob_model == 0 ? tm1_of(prm->p) : 0;
+    c->cm.tm1_class[0] = tm1_of(0.1);
+    c->cm.tm1_class[1] = tm1_of(0.01);
+    c->cm.tm1_class[2] = tm1_of(0.001);
+    c->cm.coin_key = prm->coin_key;
+    c->cm.prob_key = prm->prob_key;
+    const uint32_t n = g->n;
+    const uint64_t m = g->m;
+    int rc = SKIM_OK;
+#define TRY(x)                       \
+    do {                             \
+        rc = (x);                    \
+        if (rc != SKIM_OK) goto fail; \
+    } while (0)
+#define TRYC(x)                                  \
+    do {                                         \
+        cudaError_t e_ = (x);                    \
+        if (e_ != cudaSuccess) {                 \
+            rc = fail_cuda(c, e_);               \
+            goto fail;                           \
+        }                                        \
+    } while (0)
+    {
+        TRY(dalloc(c, &c->ctl, 1));
+        TRYC(cudaMallocHost(reinterpret_cast<void **>(&c->hctl), sizeof(DevCtl)));
+        TRYC(cudaMemsetAsync(c->ctl, 0, sizeof(DevCtl), c->st));
+        TRY(dalloc(c, &c->dflag, 1));
+        // edges on the device
+        uint32_t *dsrc = nullptr, *ddst = nullptr;
+        bool own_edges = !g->on_device;
+        if (own_edges) {
+            TRY(dalloc(c, &dsrc, m));
+            TRY(dalloc(c, &ddst, m));
+            if (m) {
+                TRYC(cudaMemcpyAsync(dsrc, g->src, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->st));
+                TRYC(cudaMemcpyAsync(ddst, g->dst, m * sizeof(uint32_t), cudaMemcpyHostToDevice, c->st));
+            }
+        } else {
+            dsrc = const_cast<uint32_t *>(g->src);
+            ddst = const_cast<uint32_t *>(g->dst);
+        }
+        TRYC(cudaMemsetAsync(c->dflag, 0, sizeof(unsigned), c->st));
+        TRYC(launch_check_edges(dsrc, ddst, m, n, c->dflag, c->st));
+        unsigned bad = 0;
+        TRYC(cudaMemcpyAsync(&bad, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+        TRYC(cudaStreamSynchronize(c->st));
+        if (bad) {
+            if (own_edges) { dfree(dsrc); dfree(ddst); }
+            rc = SKIM_EGRAPH;
+            goto fail;
+        }
+        // workspace for scans and sorts
+        const uint64_t rcap = std::min<uint64_t>(std::max<uint64_t>(4ull * std::min<uint64_t>(nl, 1u << 18), 1u << 20),
+                                                 1ull << 25);
+        size_t ws = std::max({scan_workspace_bytes(static_cast<size_t>(n) + 1), radix_workspace_bytes(m),
+                              radix_workspace_bytes(rcap), scan_workspace_bytes(static_cast<size_t>(kMaxWords) * 64)});
+        c->ws_bytes = ws;
+        TRYC(cudaMalloc(&c->ws, ws));
+        // forward CSR: rows of the (src,dst)-sorted list
+        uint64_t *deg = nullptr;
+        TRY(dalloc(c, &deg, static_cast<size_t>(n) + 1));
+        TRY(dalloc(c, &c->fptr, static_cast<size_t>(n) + 1));
+        TRY(dalloc(c, &c->rptr, static_cast<size_t>(n) + 1));
+        TRY(dalloc(c, &c->fcol, m));
+        TRY(dalloc(c, &c->rcol, m));
+        TRYC(cudaMemsetAsync(deg, 0, (static_cast<size_t>(n) + 1) * sizeof(uint64_t), c->st));
+        TRYC(launch_degree_count(dsrc, m, deg, c->st));
+        TRYC(exclusive_scan_u64(deg, deg, static_cast<size_t>(n) + 1, nullptr, c->ws, c->st));
+        TRYC(launch_u64_to_u32(deg, c->fptr, static_cast<size_t>(n) + 1, c->st));
+        if (m) TRYC(cudaMemcpyAsync(c->fcol, ddst, m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->st));
+        // reverse CSR: sort by (dst, src)
+        TRYC(cudaMemsetAsync(deg, 0, (static_cast<size_t>(n) + 1) * sizeof(uint64_t), c->st));
+        TRYC(launch_degree_count(ddst, m, deg, c->st));
+        TRYC(exclusive_scan_u64(deg, deg, static_cast<size_t>(n) + 1, nullptr, c->ws, c->st));
+        TRYC(launch_u64_to_u32(deg, c->rptr, static_cast<size_t>(n) + 1, c->st));
+        if (m) {
+            uint64_t *k1 = nullptr, *k2 = nullptr;
+            uint32_t *v1 = nullptr, *v2 = nullptr;
+            TRY(dalloc(c, &k1, m));
+            TRY(dalloc(c, &k2, m));
+            TRY(dalloc(c, &v1, m));
+            TRY(dalloc(c, &v2, m));
+            TRYC(launch_make_rev_keys(dsrc, ddst, m, k1, v1, c->st));
+            TRYC(radix_sort_pairs(k1, v1, k2, v2, m, 32 + bitlen(n - 1), c->ws, c->st));
+            TRYC(launch_split_rev(k1, m, c->rcol, c->st));
+            TRYC(cudaStreamSynchronize(c->st));
+            dfree(k1); dfree(k2); dfree(v1); dfree(v2);
+        }
+        TRYC(cudaStreamSynchronize(c->st));
+        dfree(deg);
+        if (own_edges) { dfree(dsrc); dfree(ddst); }
+        // degree limits of the chunked work items
+        unsigned long long *md = reinterpret_cast<unsigned long long *>(c->ctl);
+        TRYC(cudaMemsetAsync(md, 0, sizeof(unsigned long long), c->st));
+        TRYC(launch_max_degree(c->rptr, n, md, c->st));
+        TRYC(launch_max_degree(c->fptr, n, md, c->st));
+        unsigned long long maxdeg = 0;
+        TRYC(cudaMemcpyAsync(&maxdeg, md, sizeof(maxdeg), cudaMemcpyDeviceToHost, c->st));
+        TRYC(cudaStreamSynchronize(c->st));
+        TRYC(cudaMemsetAsync(c->ctl, 0, sizeof(DevCtl), c->st));
+        if (maxdeg > kMaxDegree) { rc = SKIM_ERANGE; goto fail; }
+        if (prm->prob_model == 1) {
+            TRY(dalloc(c, &c->thr_wc, n));
+            TRYC(launch_wc_thresholds(c->rptr, n, c->thr_wc, c->st));
+        }
+        c->cm.thr_wc = c->thr_wc;
+        // rank order of the n*l pairs
+        TRY(dalloc(c, &c->srank, nl));
+        TRY(dalloc(c, &c->spair, nl));
+        {
+            void *rws = nullptr;
+            TRYC(cudaMalloc(&rws, rank_sort_workspace_bytes(nl)));
+            cudaError_t e = rank_sort(prm->rank_key, nl, c->srank, c->spair, rws, c->st);
+            cudaError_t e2 = cudaStreamSynchronize(c->st);
+            cudaFree(rws);
+            TRYC(e);
+            TRYC(e2);
+        }
+        // traversal scratch
+        c->lane_cap = static_cast<uint32_t>(std::min<uint64_t>(pow2_at_least(std::min<uint64_t>(nl, kMaxWords * 64ull)),
+                                                               kMaxWords * 64ull));
+        if (c->lane_cap < 64) c->lane_cap = 64;
+        c->rcap = rcap;
+        c->hcap = pow2_at_least(2 * rcap);
+        c->qcap = std::max<uint64_t>(rcap, 1u << 22);
+        TRY(dalloc(c, &c->q, c->qcap));
+        TRYC(cudaMemsetAsync(c->q, 0, c->qcap * sizeof(Item), c->st));
+        TRY(dalloc(c, &c->hkeys, c->hcap));
+        TRY(dalloc(c, &c->hvals, c->hcap));
+        TRY(dalloc(c, &c->pend, c->hcap));
+        TRYC(cudaMemsetAsync(c->hkeys, 0xff, c->hcap * sizeof(uint64_t), c->st));
+        TRYC(cudaMemsetAsync(c->hvals, 0, c->hcap * sizeof(uint64_t), c->st));
+        TRYC(cudaMemsetAsync(c->pend, 0, c->hcap * sizeof(uint64_t), c->st));
+        TRY(dalloc(c, &c->rkey, c->rcap));
+        TRY(dalloc(c, &c->rkey2, c->rcap));
+        TRY(dalloc(c, &c->rval, c->rcap));
+        TRY(dalloc(c, &c->rval2, c->rcap));
+        TRY(dalloc(c, &c->lane_inst, c->lane_cap));
+        TRYC(cudaMemsetAsync(c->lane_inst, 0, c->lane_cap, c->st));
+        TRY(dalloc(c, &c->alive, c->lane_cap / 64 + 1));
+        TRY(dalloc(c, &c->lane_cnt, c->lane_cap));
+        TRY(dalloc(c, &c->lane_off, c->lane_cap));
+        TRY(dalloc(c, &c->lane_fill, c->lane_cap));
+        c->grid_rev = traverse_grid(false);
+        c->grid_fwd = traverse_grid(true);
+        TRYC(cudaStreamSynchronize(c->st));
+    }
+#undef TRY
+#undef TRYC
+    *out = c;
+    return SKIM_OK;
+fail:
+    skim_destroy(c);
+    return rc;
+}
+
+int skim_build_sketches(skim_ctx *c) {
+    if (!c) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    if (!c->X) {
+        RC(dalloc(c, &c->lcnt, c->nl));
+        RC(dalloc(c, &c->full, c->n));
+        RC(dalloc(c, &c->X, static_cast<size_t>(c->n) * c->k));
+        RC(dalloc(c, &c->xlen, c->n));
+    }
+    if (c->batch_active) {  // a SKIM batch holds the visited table: release it
+        RC(commit_lanes(c, c->blo, c->bB - 1));
+        RC(clear_batch(c));
+        c->batch_active = false;
+    }
+    CK(c, cudaMemsetAsync(c->lcnt, 0, c->nl, c->st));
+    CK(c, cudaMemsetAsync(c->full, 0, c->n * sizeof(uint64_t), c->st));
+    CK(c, cudaMemsetAsync(c->X, 0, static_cast<size_t>(c->n) * c->k * sizeof(uint64_t), c->st));
+    CK(c, cudaMemsetAsync(c->xlen, 0, c->n * sizeof(uint32_t), c->st));
+    RC(reset_stats(c));
+    c->built = false;
+    const uint32_t Bmax = default_lanes(c);
+    uint32_t B = std::min<uint32_t>(Bmax, 1u << 12);
+    uint64_t p0 = 0;
+    while (p0 < c->nl) {
+        uint32_t b = static_cast<uint32_t>(std::min<uint64_t>(B, c->nl - p0));
+        bool retry = false;
+        RC(rev_batch(c, p0, b, true, &retry));
+        if (retry) {
+            B = std::max<uint32_t>(64, b / 2);
+            continue;
+        }
+        CK(c, launch_accept(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->lane_inst, c->srank + p0, c->l, c->k,
+                            c->lcnt, c->full, c->X, c->xlen, c->ctl, c->st));
+        RC(clear_batch(c));
+        p0 += b;
+        c->hstats[SKIM_STAT_RANKS] += b;
+        B = std::min<uint32_t>(Bmax, B * 2);
+    }
+    uint64_t batches = c->hstats[SKIM_STAT_BATCHES], ranks = c->hstats[SKIM_STAT_RANKS],
+             retries = c->hstats[SKIM_STAT_RETRIES];
+    RC(pull_stats(c));
+    c->hstats[SKIM_STAT_BATCHES] = batches;
+    c->hstats[SKIM_STAT_RANKS] = ranks;
+    c->hstats[SKIM_STAT_RETRIES] = retries;
+    c->built = true;
+    return SKIM_OK;
+}
+
+int skim_get_sketches(skim_ctx *c, uint64_t *x_out, uint32_t *len_out, int out_on_device) {
+    if (!c || !x_out || !len_out) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    if (!c->built) return SKIM_ENOTBUILT;
+    cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(c, cudaMemcpyAsync(x_out, c->X, static_cast<size_t>(c->n) * c->k * sizeof(uint64_t), kind, c->st));
+    CK(c, cudaMemcpyAsync(len_out, c->xlen, c->n * sizeof(uint32_t), kind, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    return SKIM_OK;
+}
+
+int skim_sketch_pointers(skim_ctx *c, const uint64_t **x_dev, const uint32_t **len_dev) {
+    if (!c || !x_dev || !len_dev) return SKIM_EINVAL;
+    if (!c->built) return SKIM_ENOTBUILT;
+    *x_dev = c->X;
+    *len_dev = c->xlen;
+    return SKIM_OK;
+}
+
+int skim_greedy_reset(skim_ctx *c) {
+    if (!c) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    return skim_state_init(c);
+}
+
+int skim_greedy(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out) {
+    if (!c || (n_seeds && (!seeds_out || !cov_out))) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    if (!c->sk_init) RC(skim_state_init(c));
+    if (static_cast<uint64_t>(c->nseeds) + n_seeds > c->n) return SKIM_EINVAL;
+    RC(reset_stats(c));
+    for (uint32_t j = 0; j < n_seeds; j++) {
+        uint32_t x = 0;
+        uint64_t cov = 0;
+        RC(next_seed(c, &x, &cov));
+        seeds_out[j] = x;
+        cov_out[j] = cov;
+        c->nseeds++;
+    }
+    uint64_t keep[3] = {c->hstats[SKIM_STAT_BATCHES], c->hstats[SKIM_STAT_RANKS], c->hstats[SKIM_STAT_RETRIES]};
+    RC(pull_stats(c));
+    c->hstats[SKIM_STAT_BATCHES] = keep[0];
+    c->hstats[SKIM_STAT_RANKS] = keep[1];
+    c->hstats[SKIM_STAT_RETRIES] = keep[2];
+    return SKIM_OK;
+}
+
+int skim_oracle_query_batch(skim_ctx *c, const uint64_t *offsets, uint32_t q, const uint32_t *seeds, double *est_out,
+                            int on_device) {
+    if (!c || !offsets || (q && !est_out)) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    if (!c->built) return SKIM_ENOTBUILT;
+    if (q == 0) return SKIM_OK;
+    if (offsets[0] != 0) return SKIM_EINVAL;
+    std::vector<uint64_t> toff(static_cast<size_t>(q) + 1, 0);
+    for (uint32_t i = 0; i < q; i++) {
+        if (offsets[i + 1] < offsets[i]) return SKIM_EINVAL;
+        toff[i + 1] = toff[i] + query_table(offsets[i + 1] - offsets[i], c->k);
+    }
+    const uint64_t total = offsets[q];
+    if (total && !seeds) return SKIM_EINVAL;
+    if (!on_device) {
+        for (uint64_t i = 0; i < total; i++)
+            if (seeds[i] >= c->n) return SKIM_EINVAL;
+    }
+    RC(ensure_query_space(c, total, q, toff[q]));
+    const uint32_t *dseeds = seeds;
+    if (!on_device && total) {
+        CK(c, cudaMemcpyAsync(c->qseeds, seeds, total * sizeof(uint32_t), cudaMemcpyHostToDevice, c->st));
+        dseeds = c->qseeds;
+    }
+    CK(c, cudaMemcpyAsync(c->qoff, offsets, (static_cast<size_t>(q) + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                          c->st));
+    CK(c, cudaMemcpyAsync(c->qtoff, toff.data(), toff.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaMemsetAsync(c->dflag, 0, sizeof(unsigned), c->st));
+    double *dout = on_device ? est_out : c->qout;
+    CK(c, launch_query(c->X, c->xlen, c->n, c->k, c->l, dseeds, c->qoff, c->qtoff, q, c->qk, c->qv, dout, c->dflag,
+                       c->st));
+    unsigned bad = 0;
+    CK(c, cudaMemcpyAsync(&bad, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+    if (!on_device)
+        CK(c, cudaMemcpyAsync(est_out, c->qout, q * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    return bad ? SKIM_EINVAL : SKIM_OK;
+}
+
+int skim_oracle_query(skim_ctx *c, const uint32_t *seeds, uint32_t n_seeds, double *est_out) {
+    if (!c || !est_out || (n_seeds && !seeds)) return SKIM_EINVAL;
+    uint64_t off[2] = {0, n_seeds};
+    return skim_oracle_query_batch(c, off, 1, seeds, est_out, 0);
+}
+
+int skim_get_stats(skim_ctx *c, uint64_t *out, uint32_t count) {
+    if (!c || !out) return SKIM_EINVAL;
+    for (uint32_t i = 0; i < count && i < SKIM_STAT_COUNT; i++) out[i] = c->hstats[i];
+    return SKIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// internal.cuh -- launchers and argument blocks shared by the libskim
+// translation units (host-visible declarations; kernels live in the .cu files).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace skim {
+
+// Live-edge threshold model (Section 6: uniform p, weighted cascade 1/indeg,
+// trivalency classes).
+struct CoinModel {
+    int model;            // 0 uniform, 1 weighted cascade, 2 trivalency
+    uint64_t tm1_uniform;  // floor(p * 2^64) - 1
+    uint64_t tm1_class[3];
+    const uint64_t *thr_wc;  // per node: floor((2^64-1) / indeg(node))
+    uint64_t coin_key;
+    uint64_t prob_key;
+};
+
+// Arguments of the asynchronous traversal kernels.
+struct TravArgs {
+    const uint32_t *ptr;  // CSR row pointers in the search direction
+    const uint32_t *col;
+    CoinModel cm;
+    Item *q;
+    uint64_t qcap;
+    DevCtl *ctl;
+    uint64_t timeout_ns;
+    // reverse searches (lanes = ranks of a batch)
+    uint64_t *hkeys;
+    uint64_t *hvals;
+    uint64_t hmask;
+    uint64_t *rec_key;
+    uint32_t *rec_val;
+    uint64_t rcap;
+    uint32_t tbits;             // record key = (node << tbits) | word
+    const uint8_t *lane_inst;   // instance of every lane of the batch
+    const uint64_t *full;       // Algorithm 2 pruning: instances whose local sketch holds k ranks
+    int prune;
+    uint64_t *pend;             // per table slot: lane bits whose expansion was spilled
+    // residual (forward) searches (lanes = instances)
+    uint64_t *covered;
+    const uint64_t *seg_start;
+    uint32_t *seg_len;
+    uint32_t *size;
+    const uint32_t *idx_nodes;
+    uint32_t l;
+    uint64_t *pend_trav;        // per node: instances whose expansion was spilled
+    uint64_t *pend_erase;       // per node: instances whose index erasure was spilled
+};
+
+// graph.cu
+cudaError_t launch_check_edges(const uint32_t *src, const uint32_t *dst, uint64_t m, uint32_t n, unsigned *bad,
+                               cudaStream_t s);
+cudaError_t launch_degree_count(const uint32_t *idx, uint64_t m, uint64_t *deg, cudaStream_t s);
+cudaError_t launch_u64_to_u32(const uint64_t *in, uint32_t *out, size_t n, cudaStream_t s);
+cudaError_t launch_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint64_t m, uint64_t *key, uint32_t *val,
+                                 cudaStream_t s);
+cudaError_t launch_split_rev(const uint64_t *key, uint64_t m, uint32_t *rcol, cudaStream_t s);
+cudaError_t launch_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr, cudaStream_t s);
+cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out, cudaStream_t s);
+
+// Rank order of all pairs: bucket by the top bits, then sort each bucket.
+size_t rank_sort_workspace_bytes(uint64_t nl);
+cudaError_t rank_sort(uint64_t rank_key, uint64_t nl, uint64_t *sorted_rank, uint32_t *sorted_pair, void *ws,
+                      cudaStream_t s);
+
+// traverse.cu
+cudaError_t launch_rev_sources(const TravArgs &a, const uint32_t *lane_pair, uint32_t B, uint32_t l,
+                               const uint64_t *covered, uint64_t *alive, cudaStream_t s);
+cudaError_t launch_fwd_source(const TravArgs &a, uint32_t x, cudaStream_t s);
+cudaError_t launch_traverse(const TravArgs &a, bool forward, int grid, cudaStream_t s);
+// Re-queue spilled work (after a drained traversal that set DevCtl::spill).
+cudaError_t launch_respill_rev(const TravArgs &a, uint64_t R, cudaStream_t s);
+cudaError_t launch_respill_fwd(const TravArgs &a, uint32_t n, cudaStream_t s);
+int traverse_grid(bool forward);  // resident blocks for the persistent traversal
+
+// batch.cu
+cudaError_t launch_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, cudaStream_t s);
+cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                          const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
+                          uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
+                          cudaStream_t s);
+cudaError_t launch_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hkeys, uint64_t *hvals, cudaStream_t s);
+cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                              const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
+                              uint32_t k, DevCtl *ctl, cudaStream_t s);
+cudaError_t launch_commit_count(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                                const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size,
+                                uint64_t *lane_cnt, DevCtl *ctl, cudaStream_t s);
+cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                                  const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi,
+                                  const uint64_t *lane_off, uint32_t *lane_fill, uint64_t idx_base,
+                                  uint32_t *idx_nodes, cudaStream_t s);
+cudaError_t launch_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32_t hi, const uint64_t *lane_cnt,
+                                   const uint64_t *lane_off, uint64_t idx_base, uint64_t *seg_start,
+                                   uint32_t *seg_len, cudaStream_t s);
+cudaError_t launch_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, uint32_t l, const uint64_t *covered,
+                            uint64_t *alive, cudaStream_t s);
+cudaError_t launch_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl, cudaStream_t s);
+cudaError_t launch_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl, cudaStream_t s);
+
+// query.cu
+cudaError_t launch_query(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
+                         const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off, uint32_t q,
+                         uint64_t *hkeys, uint64_t *hvals, double *out, unsigned *err, cudaStream_t s);
+
+}  // namespace skim

@@ -1,0 +1,180 @@
+// query.cu -- influence oracle queries (Section 5.1, Eq. unionest).
+//
+// For a seed set S, every rank z of X_u minus {tau_u} (u in S) is charged
+// 1/max{tau_u : z in X_u minus {tau_u}}; the sum estimates |union of R_u| and
+// is divided by l.  tau_u is the k-th smallest rank of a full sketch and 1 for
+// a sketch with fewer than k ranks (Eq. combinedthresh).
+//
+// One block per query: a hash table in global scratch keeps, per distinct z,
+// the largest tau (as a 64-bit integer; the integer order equals the order of
+// the reals h/2^64 and the rounding to double is monotone).  Each term 1/tau is
+// formed in double exactly as h -> double -> scale by 2^-64 -> 1/x, then added
+// exactly in 192-bit fixed point (64 fraction bits suffice: every term is >= 1
+// with a 53-bit significand) and the total is rounded to double once, to
+// nearest-even.  The result therefore does not depend on the order in which
+// ranks are visited, and a query gives the same bits alone or in a batch.
+#include "internal.cuh"
+
+namespace skim {
+
+namespace {
+
+constexpr int kQThreads = 512;
+
+struct U192 {
+    uint64_t w[3];
+};
+
+SKIM_DEV void add192(U192 &a, const U192 &b) {
+    uint64_t s0 = a.w[0] + b.w[0];
+    uint64_t c0 = s0 < a.w[0];
+    uint64_t s1 = a.w[1] + b.w[1];
+    uint64_t c1 = s1 < a.w[1];
+    s1 += c0;
+    c1 |= (s1 < c0);
+    a.w[0] = s0;
+    a.w[1] = s1;
+    a.w[2] = a.w[2] + b.w[2] + c1;
+}
+
+// term 1/tau for the integer threshold h (h = ~0 stands for tau = 1)
+SKIM_DEV double inv_tau(uint64_t h) {
+    double tau = ldexp(__ull2double_rn(h), -64);
+    return 1.0 / tau;
+}
+
+// exact fixed-point image (value * 2^64) of a double in [1, 2^64]
+SKIM_DEV U192 to_fixed(double v) {
+    uint64_t bits = static_cast<uint64_t>(__double_as_longlong(v));
+    int e = static_cast<int>((bits >> 52) & 0x7ff) - 1023;
+    uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    int sh = e + 12;  // value * 2^64 = mant * 2^(e - 52 + 64)
+    U192 r{{0, 0, 0}};
+    int q = sh >> 6, rb = sh & 63;
+    r.w[q] = mant << rb;
+    if (rb && q + 1 < 3) r.w[q + 1] = mant >> (64 - rb);
+    return r;
+}
+
+SKIM_DEV int top_bit(const U192 &a) {
+    for (int i = 2; i >= 0; i--)
+        if (a.w[i]) return i * 64 + 63 - __clzll(static_cast<long long>(a.w[i]));
+    return -1;
+}
+
+SKIM_DEV uint64_t bit_at(const U192 &a, int p) { return (a.w[p >> 6] >> (p & 63)) & 1ull; }
+
+SKIM_DEV bool any_below(const U192 &a, int p) {  // any bit set strictly below position p
+    for (int i = 0; i < 3; i++) {
+        int lo = i * 64;
+        if (p <= lo) break;
+        uint64_t m = (p - lo >= 64) ? ~0ull : ((1ull << (p - lo)) - 1);
+        if (a.w[i] & m) return true;
+    }
+    return false;
+}
+
+// round (a * 2^-64) to the nearest double, ties to even
+SKIM_DEV double fixed_to_double(const U192 &a) {
+    int p = top_bit(a);
+    if (p < 0) return 0.0;
+    if (p <= 52) return ldexp(static_cast<double>(a.w[0]), -64);
+    int sh = p - 52;
+    uint64_t mant = 0;
+    for (int b = 0; b < 53; b++) mant |= bit_at(a, sh + b) << b;
+    bool rnd = bit_at(a, sh - 1);
+    bool sticky = any_below(a, sh - 1);
+    if (rnd && (sticky || (mant & 1ull))) {
+        mant++;
+        if (mant == (1ull << 53)) {
+            mant >>= 1;
+            sh++;
+        }
+    }
+    return ldexp(static_cast<double>(mant), sh - 64);
+}
+
+__global__ void __launch_bounds__(kQThreads) k_query(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k,
+                                                     uint32_t l, const uint32_t *seeds, const uint64_t *offsets,
+                                                     const uint64_t *table_off, uint64_t *hkeys, uint64_t *hvals,
+                                                     double *out, unsigned *err) {
+    __shared__ unsigned long long top_tau;  // rank value ~0 has no table key: kept here
+    __shared__ int top_used;
+    __shared__ U192 wsum[kQThreads / 32];
+    const uint64_t q = blockIdx.x;
+    const uint64_t s0 = offsets[q], s1 = offsets[q + 1];
+    const uint64_t H = table_off[q + 1] - table_off[q];
+    uint64_t *tk = hkeys + table_off[q];
+    uint64_t *tv = hvals + table_off[q];
+    if (threadIdx.x == 0) {
+        top_tau = 0;
+        top_used = 0;
+    }
+    for (uint64_t i = threadIdx.x; i < H; i += blockDim.x) {
+        tk[i] = kEmptyKey;
+        tv[i] = 0;
+    }
+    __syncthreads();
+    const uint64_t hmask = H - 1;
+    const uint64_t work = (s1 - s0) * k;
+    for (uint64_t e = threadIdx.x; e < work; e += blockDim.x) {
+        const uint32_t u = seeds[s0 + e / k];
+        const uint32_t pos = static_cast<uint32_t>(e % k);
+        if (u >= n) {
+            atomicOr(err, 1u);
+            continue;
+        }
+        const uint32_t ln = xlen[u];
+        const uint32_t body = ln == k ? k - 1 : ln;
+        if (pos >= body) continue;
+        const uint64_t z = X[static_cast<uint64_t>(u) * k + pos];
+        const uint64_t tau = ln == k ? X[static_cast<uint64_t>(u) * k + k - 1] : ~0ull;
+        if (z == kEmptyKey) {
+            atomicMax(&top_tau, static_cast<unsigned long long>(tau));
+            top_used = 1;
+            continue;
+        }
+        uint64_t h = fmix(z) & hmask;
+        for (uint64_t p = 0; p < H; p++) {
+            unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long *>(&tk[h]),
+                                                static_cast<unsigned long long>(kEmptyKey),
+                                                static_cast<unsigned long long>(z));
+            if (prev == kEmptyKey || prev == z) {
+                atomicMax(reinterpret_cast<unsigned long long *>(&tv[h]), static_cast<unsigned long long>(tau));
+                break;
+            }
+            h = (h + 1) & hmask;
+        }
+    }
+    __syncthreads();
+    U192 acc{{0, 0, 0}};
+    for (uint64_t i = threadIdx.x; i < H; i += blockDim.x) {
+        if (tk[i] != kEmptyKey) add192(acc, to_fixed(inv_tau(tv[i])));
+    }
+    if (threadIdx.x == 0 && top_used) add192(acc, to_fixed(inv_tau(top_tau)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        U192 other;
+        for (int w = 0; w < 3; w++) other.w[w] = __shfl_down_sync(kFull, acc.w[w], o);
+        add192(acc, other);
+    }
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        U192 tot{{0, 0, 0}};
+        for (int w = 0; w < kQThreads / 32; w++) add192(tot, wsum[w]);
+        out[q] = fixed_to_double(tot) / static_cast<double>(l);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_query(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
+                         const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off, uint32_t q,
+                         uint64_t *hkeys, uint64_t *hvals, double *out, unsigned *err, cudaStream_t s) {
+    if (q == 0) return cudaSuccess;
+    k_query<<<q, kQThreads, 0, s>>>(X, xlen, n, k, l, seeds, offsets, table_off, hkeys, hvals, out, err);
+    return cudaGetLastError();
+}
+
+}  // namespace skim

@@ -1,0 +1,501 @@
+// traverse.cu -- asynchronous, worklist-driven graph searches.
+//
+// Reverse searches (Algorithm 2 sketch building, Section 5.2; Algorithm 1
+// sketch building, Section 4): a batch of B consecutive ranks is searched at
+// once.  Lane j of the batch is the j-th rank; lanes are packed 64 to a word
+// and a visit is a (node, word, lane mask) triple.  Every (node, lane) pair is
+// expanded at most once: a lane bit enters a node through an atomicOr on the
+// node's visited word, and only newly set bits are pushed.  The live-edge coin
+// of a lane is drawn in that lane's instance (Section 2, binary IC model).
+// Algorithm 2's pruning -- skip a node whose local sketch of the lane's
+// instance already holds k ranks -- is tested against the state at the start
+// of the batch, which keeps the result exact (see the acceptance step).
+//
+// Residual searches (Algorithm 1, "Residual problem"): a forward search from
+// the new seed with lanes = instances, pruned at covered pairs; each newly
+// covered pair with an index entry queues the decrements of the sizes listed
+// in that entry (the entry is erased).
+//
+// There are no BFS levels: warps claim items from one global queue, process
+// them, and push new items; the search ends when every pushed item is done.
+// Every wait is bounded by a timeout that sets an error flag.
+#include "internal.cuh"
+
+namespace skim {
+
+namespace {
+
+constexpr int kTravThreads = 256;
+constexpr int kMaxProbe = 4096;
+
+SKIM_DEV uint64_t edge_tm1_rev(const CoinModel &cm, uint32_t u, uint32_t v, uint64_t tm1_head) {
+    if (cm.model == 2) return cm.tm1_class[fmix(cm.prob_key ^ ((static_cast<uint64_t>(u) << 32) | v)) % 3u];
+    return tm1_head;
+}
+
+SKIM_DEV uint64_t edge_tm1_fwd(const CoinModel &cm, uint32_t u, uint32_t w) {
+    if (cm.model == 0) return cm.tm1_uniform;
+    if (cm.model == 1) return cm.thr_wc[w];
+    return cm.tm1_class[fmix(cm.prob_key ^ ((static_cast<uint64_t>(u) << 32) | w)) % 3u];
+}
+
+// Insert-or-merge of (key, bits) into the visited table.  Returns false if the
+// probe limit is hit.  *old = bits present before, *slot = table slot,
+// *first = this call created the entry.
+SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t key, uint64_t bits, uint64_t *old,
+                      uint64_t *slot, bool *first) {
+    uint64_t h = fmix(key) & hmask;
+    for (int p = 0; p < kMaxProbe; p++) {
+        uint64_t k = *reinterpret_cast<volatile uint64_t *>(&hkeys[h]);
+        if (k == kEmptyKey) {
+            unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long *>(&hkeys[h]),
+                                                static_cast<unsigned long long>(kEmptyKey),
+                                                static_cast<unsigned long long>(key));
+            if (prev == kEmptyKey) {
+                *first = true;
+                *slot = h;
+                *old = atomicOr(reinterpret_cast<unsigned long long *>(&hvals[h]), bits);
+                return true;
+            }
+            k = prev;
+        }
+        if (k == key) {
+            *first = false;
+            *slot = h;
+            *old = atomicOr(reinterpret_cast<unsigned long long *>(&hvals[h]), bits);
+            return true;
+        }
+        h = (h + 1) & hmask;
+    }
+    return false;
+}
+
+SKIM_DEV uint32_t n_chunks(uint32_t deg) { return (deg + kChunk - 1) / kChunk; }
+
+// Reserve `cnt` queue slots per lane (warp-aggregated); returns the lane's
+// first slot.  Slots at or beyond capacity never receive an item: they are
+// counted as done at once, and the caller parks that work in a pending mask.
+SKIM_DEV unsigned long long reserve_slots(const TravArgs &A, uint32_t cnt) {
+    unsigned long long tot;
+    unsigned long long ex = warp_excl_scan(cnt, &tot);
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 0 && tot) base = atomicAdd(&A.ctl->q_tail, tot);
+    base = __shfl_sync(kFull, base, 0);
+    if ((threadIdx.x & 31) == 0 && tot && base + tot > A.qcap) {
+        unsigned long long lost = base + tot - (base >= A.qcap ? base : A.qcap);
+        atomicAdd(&A.ctl->q_done, lost);
+    }
+    return base + ex;
+}
+
+SKIM_DEV void write_item(const TravArgs &A, unsigned long long slot, uint32_t v, uint32_t w, uint64_t mask) {
+    if (slot >= A.qcap) return;
+    Item *it = &A.q[slot];
+    it->v = v;
+    it->w = w;
+    st_release(&it->mask, mask);
+}
+
+// A lane whose reservation does not fit fills its in-capacity slots with
+// placeholders; returns true if the lane must park its work.
+SKIM_DEV bool spill_if_full(const TravArgs &A, unsigned long long s, uint32_t ni) {
+    if (s + ni <= A.qcap) return false;
+    for (uint32_t c = 0; c < ni; c++) write_item(A, s + c, 0, kNopTag, 1);
+    atomicOr(&A.ctl->spill, 1u);
+    return true;
+}
+
+// Warp-collective: queue the expansion of lane bits `nb` of entry (u, t)
+// (table slot `slot`).
+SKIM_DEV void push_rev(const TravArgs &A, uint32_t u, uint32_t t, uint64_t nb, uint64_t slot) {
+    uint32_t ni = 0;
+    if (nb) ni = n_chunks(A.ptr[u + 1] - A.ptr[u]);
+    if (!__any_sync(kFull, ni != 0)) return;
+    unsigned long long s = reserve_slots(A, ni);
+    if (ni && spill_if_full(A, s, ni)) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&A.pend[slot]), nb);
+        return;
+    }
+    for (uint32_t c = 0; c < ni; c++) write_item(A, s + c, u, (t << kChunkBits) | c, nb);
+}
+
+// Warp-collective: lanes with `act` visit node u with lane bits `bits` in word t.
+SKIM_DEV void emit_rev(const TravArgs &A, bool act, uint32_t u, uint32_t t, uint64_t bits) {
+    uint64_t nb = 0;
+    bool first = false;
+    uint64_t slot = 0;
+    if (act && bits) {
+        uint64_t old;
+        uint64_t key = (static_cast<uint64_t>(u) << A.tbits) | t;
+        if (hash_or(A.hkeys, A.hvals, A.hmask, key, bits, &old, &slot, &first)) {
+            nb = bits & ~old;
+        } else {
+            atomicOr(&A.ctl->err, kErrHash);
+        }
+    }
+    // record of the (node, word) entry, written once by its creator
+    {
+        unsigned ball = __ballot_sync(kFull, first);
+        if (ball) {
+            unsigned long long base = 0;
+            if ((threadIdx.x & 31) == 0) base = atomicAdd(&A.ctl->rec_count, static_cast<unsigned long long>(__popc(ball)));
+            base = __shfl_sync(kFull, base, 0);
+            if (first) {
+                unsigned long long r = base + __popc(ball & lanemask_lt());
+                if (r < A.rcap) {
+                    A.rec_key[r] = (static_cast<uint64_t>(u) << A.tbits) | t;
+                    A.rec_val[r] = static_cast<uint32_t>(slot);
+                } else {
+                    atomicOr(&A.ctl->err, kErrRecords);
+                }
+            }
+        }
+    }
+    warp_add(&A.ctl->stats[kStRevVisits], __popcll(nb));
+    push_rev(A, u, t, nb, slot);
+}
+
+// Warp-collective: queue the expansion of node w in instances `trav` and the
+// erasure of the index entries of pairs (w, i), i in `erase`.
+SKIM_DEV void push_fwd(const TravArgs &A, uint32_t w, uint64_t trav, uint64_t erase) {
+    uint32_t ni = 0;
+    if (trav) ni = n_chunks(A.ptr[w + 1] - A.ptr[w]);
+    for (uint64_t m = erase; m; m &= m - 1) {
+        int i = __ffsll(m) - 1;
+        ni += n_chunks(A.seg_len[static_cast<uint64_t>(w) * A.l + i]);
+    }
+    if (!__any_sync(kFull, ni != 0)) return;
+    unsigned long long s = reserve_slots(A, ni);
+    if (ni && spill_if_full(A, s, ni)) {
+        if (trav) atomicOr(reinterpret_cast<unsigned long long *>(&A.pend_trav[w]), trav);
+        if (erase) atomicOr(reinterpret_cast<unsigned long long *>(&A.pend_erase[w]), erase);
+        return;
+    }
+    uint32_t c = 0;
+    if (trav) {
+        uint32_t nc = n_chunks(A.ptr[w + 1] - A.ptr[w]);
+        for (; c < nc; c++) write_item(A, s + c, w, c, trav);
+    }
+    for (uint64_t m = erase; m; m &= m - 1) {
+        int i = __ffsll(m) - 1;
+        uint64_t pair = static_cast<uint64_t>(w) * A.l + i;
+        uint32_t len = A.seg_len[pair];
+        if (!len) continue;
+        A.seg_len[pair] = 0;  // erase index[w,i]
+        uint64_t st = A.seg_start[pair];
+        uint32_t ne = n_chunks(len);
+        for (uint32_t e = 0; e < ne; e++, c++) write_item(A, s + c, len, kEraseTag | e, st + 1);
+    }
+}
+
+// Warp-collective: lanes with `act` reach node w in the instances of `live`
+// during a residual search.
+SKIM_DEV void emit_fwd(const TravArgs &A, bool act, uint32_t w, uint64_t live) {
+    uint64_t nb = 0;
+    if (act && live) {
+        uint64_t cov = *reinterpret_cast<volatile uint64_t *>(&A.covered[w]);
+        nb = live & ~cov;
+        if (nb) {
+            uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(&A.covered[w]), nb);
+            nb &= ~old;
+        }
+    }
+    warp_add(&A.ctl->ix_cov, __popcll(nb));
+    warp_add(&A.ctl->stats[kStFwdVisits], __popcll(nb));
+    uint64_t erase = 0;
+    for (uint64_t m = nb; m; m &= m - 1) {
+        int i = __ffsll(m) - 1;
+        if (A.seg_len[static_cast<uint64_t>(w) * A.l + i]) erase |= 1ull << i;
+    }
+    push_fwd(A, w, nb, erase);
+}
+
+// Process the items held by the lanes with `have`, edges (or index entries)
+// of all items flattened over the warp.
+template <bool FWD>
+SKIM_DEV void process_items(const TravArgs &A, bool have, const Item &it) {
+    const int lane = threadIdx.x & 31;
+    uint32_t begin = 0, cnt = 0;
+    uint64_t tm1 = 0;
+    bool erase = false;
+    if (have) {
+        if (it.w == kNopTag) {
+            cnt = 0;
+        } else if (FWD && (it.w & kEraseTag)) {
+            erase = true;
+            begin = (it.w & ~kEraseTag) * kChunk;
+            cnt = min(kChunk, it.v - begin);
+        } else {
+            uint32_t chunk = it.w & ((1u << kChunkBits) - 1);
+            uint32_t e0 = A.ptr[it.v], e1 = A.ptr[it.v + 1];
+            begin = e0 + chunk * kChunk;
+            cnt = min(kChunk, e1 - begin);
+            if (!FWD) tm1 = A.cm.model == 1 ? A.cm.thr_wc[it.v] : A.cm.tm1_uniform;
+        }
+    }
+    unsigned long long tot;
+    unsigned long long excl = warp_excl_scan(cnt, &tot);
+    unsigned long long incl = excl + cnt;
+    unsigned long long coins = 0;
+    for (unsigned long long b0 = 0; b0 < tot; b0 += 32) {
+        unsigned long long f = b0 + lane;
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            unsigned long long iv = __shfl_sync(kFull, incl, lo + step - 1);
+            if (iv <= f) lo += step;
+        }
+        const int owner = lo;
+        const uint32_t ov = __shfl_sync(kFull, it.v, owner);
+        const uint32_t ow = __shfl_sync(kFull, it.w, owner);
+        const uint64_t om = __shfl_sync(kFull, it.mask, owner);
+        const uint32_t ob = __shfl_sync(kFull, begin, owner);
+        const unsigned long long oex = __shfl_sync(kFull, excl, owner);
+        const bool oerase = __shfl_sync(kFull, erase, owner);
+        const uint64_t otm1 = __shfl_sync(kFull, tm1, owner);
+        const bool valid = f < tot;
+        const uint32_t idx = ob + static_cast<uint32_t>(f - oex);
+        if (FWD) {
+            bool act = false;
+            uint32_t w = 0;
+            uint64_t live = 0;
+            if (valid) {
+                if (oerase) {
+                    uint32_t node = A.idx_nodes[(om - 1) + idx];
+                    atomicSub(&A.size[node], 1u);
+                } else {
+                    w = A.col[idx];
+                    uint64_t he = edge_state(A.cm.coin_key, ov, w);
+                    uint64_t t1 = edge_tm1_fwd(A.cm, ov, w);
+                    uint64_t m = om;
+                    coins += __popcll(m);
+                    while (m) {
+                        int i = __ffsll(m) - 1;
+                        m &= m - 1;
+                        if (coin_live(he, static_cast<uint32_t>(i), t1)) live |= 1ull << i;
+                    }
+                    act = live != 0;
+                }
+            }
+            emit_fwd(A, act, w, live);
+        } else {
+            bool act = false;
+            uint32_t u = 0;
+            uint64_t live = 0;
+            const uint32_t t = ow >> kChunkBits;
+            if (valid) {
+                u = A.col[idx];
+                uint64_t he = edge_state(A.cm.coin_key, u, ov);
+                uint64_t t1 = edge_tm1_rev(A.cm, u, ov, otm1);
+                const uint8_t *li = A.lane_inst + static_cast<size_t>(t) * 64;
+                uint64_t m = om;
+                coins += __popcll(m);
+                while (m) {
+                    int j = __ffsll(m) - 1;
+                    m &= m - 1;
+                    if (coin_live(he, li[j], t1)) live |= 1ull << j;
+                }
+                if (live && A.prune) {
+                    uint64_t fu = A.full[u];
+                    if (fu) {
+                        uint64_t mm = live;
+                        while (mm) {
+                            int j = __ffsll(mm) - 1;
+                            mm &= mm - 1;
+                            if ((fu >> li[j]) & 1ull) live &= ~(1ull << j);
+                        }
+                    }
+                }
+                act = live != 0;
+            }
+            emit_rev(A, act, u, t, live);
+        }
+    }
+    warp_add(&A.ctl->stats[FWD ? kStFwdCoins : kStRevCoins], coins);
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs A) {
+    const int lane = threadIdx.x & 31;
+    DevCtl *C = A.ctl;
+    uint64_t t_progress = globaltimer();
+    unsigned long long seen_done = ld_volatile(&C->q_done);
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&C->q_head, 32ull);
+        base = __shfl_sync(kFull, base, 0);
+        const unsigned long long slot = base + lane;
+        bool pending = slot < A.qcap;
+        bool empty = !pending;  // resolved without an item
+        for (;;) {
+            Item it{0, 0, 0};
+            bool have = false;
+            if (pending) {
+                uint64_t m = ld_acquire(&A.q[slot].mask);
+                if (m) {
+                    it.v = *reinterpret_cast<volatile uint32_t *>(&A.q[slot].v);
+                    it.w = *reinterpret_cast<volatile uint32_t *>(&A.q[slot].w);
+                    it.mask = m;
+                    have = true;
+                    pending = false;
+                }
+            }
+            const unsigned hb = __ballot_sync(kFull, have);
+            if (hb) {
+                process_items<FWD>(A, have, it);
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    atomicAdd(&C->q_done, static_cast<unsigned long long>(__popc(hb)));
+                }
+                t_progress = globaltimer();
+            } else if (__any_sync(kFull, pending)) {
+                // nothing ready: either items are still being written, or more
+                // may be pushed, or the queue has drained
+                unsigned long long d = ld_volatile(&C->q_done);
+                __threadfence();
+                unsigned long long tl = ld_volatile(&C->q_tail);
+                if (d == tl && pending && slot >= tl) {
+                    pending = false;
+                    empty = true;
+                }
+                if (d != seen_done) {
+                    seen_done = d;
+                    t_progress = globaltimer();
+                }
+                if (*reinterpret_cast<volatile unsigned *>(&C->err) & kErrTimeout) return;
+                if (globaltimer() - t_progress > A.timeout_ns) {
+                    if (lane == 0) atomicOr(&C->err, kErrTimeout);
+                    return;
+                }
+                __nanosleep(128);
+            }
+            if (!__any_sync(kFull, pending)) break;
+        }
+        if (__any_sync(kFull, empty)) return;
+    }
+}
+
+}  // namespace
+
+int traverse_grid(bool forward) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (forward)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_traverse<true>, kTravThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_traverse<false>, kTravThreads, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_traverse(const TravArgs &a, bool forward, int grid, cudaStream_t s) {
+    if (forward)
+        k_traverse<true><<<grid, kTravThreads, 0, s>>>(a);
+    else
+        k_traverse<false><<<grid, kTravThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Sources of a batch: lane j starts at the node of its pair.  Algorithm 2
+// prunes a source whose local sketch in its instance is full; SKIM skips a
+// covered source pair (its rank is consumed without a search).
+__global__ void k_rev_sources(TravArgs A, const uint32_t *lane_pair, uint32_t B, uint32_t l, const uint64_t *covered,
+                              uint64_t *alive) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x / 32);
+    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w * 32 < B; w += warps) {
+        const uint32_t j = w * 32 + lane;
+        bool act = j < B;
+        uint32_t u = 0, i = 0;
+        if (act) {
+            uint32_t pr = lane_pair[j];
+            u = pr / l;
+            i = pr % l;
+            if (A.prune && ((A.full[u] >> i) & 1ull)) act = false;
+            if (covered && ((covered[u] >> i) & 1ull)) act = false;
+        }
+        if (alive) {
+            unsigned b = __ballot_sync(kFull, act);
+            if (lane == 0 && b) {
+                uint64_t bits = static_cast<uint64_t>(b) << ((w & 1) * 32);
+                atomicOr(reinterpret_cast<unsigned long long *>(&alive[w >> 1]), bits);
+            }
+        }
+        emit_rev(A, act, u, j >> 6, 1ull << (j & 63));
+    }
+}
+
+__global__ void k_respill_rev(TravArgs A, uint64_t R) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x / 32);
+    const uint64_t tmask = (1ull << A.tbits) - 1;
+    for (uint64_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w * 32 < R; w += warps) {
+        const uint64_t r = w * 32 + lane;
+        uint64_t p = 0, slot = 0, key = 0;
+        if (r < R) {
+            slot = A.rec_val[r];
+            key = A.rec_key[r];
+            p = atomicExch(reinterpret_cast<unsigned long long *>(&A.pend[slot]), 0ull);
+        }
+        push_rev(A, static_cast<uint32_t>(key >> A.tbits), static_cast<uint32_t>(key & tmask), p, slot);
+    }
+}
+
+__global__ void k_respill_fwd(TravArgs A, uint32_t n) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x / 32);
+    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w * 32 < n; w += warps) {
+        const uint32_t v = w * 32 + lane;
+        uint64_t pt = 0, pe = 0;
+        if (v < n) {
+            pt = atomicExch(reinterpret_cast<unsigned long long *>(&A.pend_trav[v]), 0ull);
+            pe = atomicExch(reinterpret_cast<unsigned long long *>(&A.pend_erase[v]), 0ull);
+        }
+        push_fwd(A, v < n ? v : 0, pt, pe);
+    }
+}
+
+__global__ void k_fwd_source(TravArgs A, uint32_t x) {
+    const uint64_t lmask = A.l == 64 ? ~0ull : ((1ull << A.l) - 1);
+    emit_fwd(A, threadIdx.x == 0, x, lmask);
+}
+
+}  // namespace
+
+cudaError_t launch_rev_sources(const TravArgs &a, const uint32_t *lane_pair, uint32_t B, uint32_t l,
+                               const uint64_t *covered, uint64_t *alive, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    unsigned warps = (B + 31) / 32;
+    unsigned blocks = (warps + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_rev_sources<<<blocks, 256, 0, s>>>(a, lane_pair, B, l, covered, alive);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_respill_rev(const TravArgs &a, uint64_t R, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    uint64_t warps = (R + 31) / 32;
+    uint64_t blocks = (warps + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_respill_rev<<<static_cast<unsigned>(blocks), 256, 0, s>>>(a, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_respill_fwd(const TravArgs &a, uint32_t n, cudaStream_t s) {
+    uint64_t warps = (n + 31) / 32;
+    uint64_t blocks = (warps + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_respill_fwd<<<static_cast<unsigned>(blocks), 256, 0, s>>>(a, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_source(const TravArgs &a, uint32_t x, cudaStream_t s) {
+    k_fwd_source<<<1, 32, 0, s>>>(a, x);
+    return cudaGetLastError();
+}
+
+}  // namespace skim

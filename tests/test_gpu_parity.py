@@ -1,0 +1,262 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Sketches, seed sequences and coverage counts must match bit for bit;
+influence estimates within 1e-12 relative (the GPU sums exactly and rounds
+once, the oracle sums in double in its own order).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1408_6282_gb300 as p
+    from paper_1408_6282_gb300 import build as b
+    b.build()
+    p.load()
+    return p
+
+
+def _both(pkg, g, l, k, model, p, seed, batch_lanes=0):
+    ks = synth.Keys.from_seed(seed)
+    pb = oracle.Problem(g.n, g.src, g.dst, l, k, model, p, ks.coin, ks.rank, ks.prob)
+    sk = pkg.Skim(g.n, g.src, g.dst, l, k, model, p, ks.coin, ks.rank, ks.prob, batch_lanes=batch_lanes)
+    return pb, sk
+
+
+def _close(a, b):
+    return abs(a - b) <= REL * max(abs(a), abs(b)) or (a == 0 and b == 0)
+
+
+SMALL = [
+    ("chain", lambda: synth.chain(40)),
+    ("star", lambda: synth.star_out(50)),
+    ("cycle", lambda: synth.cycle(33)),
+    ("clique", lambda: synth.clique(9)),
+    ("empty", lambda: synth.empty_graph(17)),
+    ("single", lambda: synth.empty_graph(1)),
+    ("er_sparse", lambda: synth.random_small_graph(300, 900, 3)),
+    ("er_dense", lambda: synth.random_small_graph(120, 3000, 4)),
+    ("rmat10", lambda: synth.rmat(10, 8, 99)),
+]
+CONF = [  # l, k, model, p, batch_lanes
+    (1, 2, 0, 0.5, 0),
+    (3, 4, 0, 0.3, 64),
+    (16, 16, 0, 0.1, 0),
+    (64, 8, 1, 0.0, 0),
+    (64, 64, 1, 0.0, 128),
+    (7, 5, 2, 0.0, 0),
+    (64, 3, 0, 1.0, 256),
+]
+
+
+@pytest.mark.parametrize("name,mk", SMALL)
+@pytest.mark.parametrize("l,k,model,p,bl", CONF)
+def test_small_graphs_sketches_skim_queries(pkg, name, mk, l, k, model, p, bl):
+    g = mk()
+    pb, sk = _both(pkg, g, l, k, model, p, 11, bl)
+    with sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        ox, oln, _ = oracle.build_sketches(pb)
+        assert np.array_equal(ln, oln)
+        assert np.array_equal(x, ox)
+        s = min(g.n, 25)
+        seeds, cov = sk.greedy(s)
+        os_, oc, _, _ = oracle.skim(pb, s)
+        assert np.array_equal(seeds, os_), (seeds, os_)
+        assert np.array_equal(cov, oc)
+        rng = np.random.default_rng(5)
+        sets = [[], [0], list(seeds[:3]), rng.integers(0, g.n, 10).tolist(), list(range(g.n))]
+        single = [sk.query(q) for q in sets]
+        batch = sk.query_batch(sets)
+        for q, a, b in zip(sets, single, batch):
+            assert a == b  # bitwise: same result alone and in a batch
+            assert _close(a, oracle.union_estimate(ox, oln, l, q))
+
+
+@pytest.mark.parametrize("bl", [0, 64, 1024])
+def test_skim_full_permutation_and_resume(pkg, bl):
+    g = synth.random_small_graph(200, 1200, 8)
+    pb, sk = _both(pkg, g, 8, 6, 1, 0.0, 21, bl)
+    with sk:
+        a, ca = sk.greedy(7)
+        b, cb = sk.greedy(g.n - 7)  # continues the sequence to exhaustion
+        seeds = np.concatenate([a, b])
+        cov = np.concatenate([ca, cb])
+        os_, oc, _, _ = oracle.skim(pb, g.n)
+        assert np.array_equal(seeds, os_)
+        assert np.array_equal(cov, oc)
+        assert sorted(seeds.tolist()) == list(range(g.n))
+        sk.greedy_reset()
+        c, cc = sk.greedy(10)
+        assert np.array_equal(c, os_[:10]) and np.array_equal(cc, oc[:10])
+
+
+def test_er4096_workload(pkg):
+    w = synth.WORKLOADS["er4096"]
+    g = w.graph()
+    pb, sk = _both(pkg, g, w.l, w.k, w.prob_model, w.p, w.seed)
+    gold = json.load(open(os.path.join(GOLDEN, "er4096.json")))
+    assert g.digest() == gold["graph_sha256"]
+    with sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        assert _digest(x, ln) == gold["sketches"]["sha256"]
+        seeds, cov = sk.greedy(w.seeds)
+        assert seeds.tolist() == gold["skim"]["seeds"]
+        assert [int(c) for c in cov] == gold["skim"]["cov"]
+        for q in gold["queries"]:
+            assert _close(sk.query(q["seeds"]), q["estimate"])
+
+
+@pytest.mark.parametrize("scale,model,p", [(12, 1, 0.0), (13, 0, 0.02), (12, 2, 0.0)])
+def test_rmat_midsize(pkg, scale, model, p):
+    ks = synth.Keys.from_seed(40 + scale)
+    g = synth.rmat(scale, 16, ks.graph)
+    pb, sk = _both(pkg, g, 64, 32, model, p, 40 + scale)
+    with sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        ox, oln, _ = oracle.build_sketches(pb)
+        assert np.array_equal(ln, oln) and np.array_equal(x, ox)
+        seeds, cov = sk.greedy(40)
+        os_, oc, _, _ = oracle.skim(pb, 40)
+        assert np.array_equal(seeds, os_) and np.array_equal(cov, oc)
+        pre = oracle.exact_coverage(pb, seeds)
+        assert np.array_equal(np.cumsum(cov), pre)
+
+
+def _digest(x, ln):
+    x = np.array(x, dtype=np.uint64, copy=True)
+    k = x.shape[1]
+    x[np.arange(k)[None, :] >= ln[:, None].astype(np.int64)] = 0
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(ln, dtype="<u4").tobytes())
+    h.update(np.ascontiguousarray(x, dtype="<u8").tobytes())
+    return h.hexdigest()
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, f"{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"no stored oracle values for {name}")
+    return json.load(open(path))
+
+
+def test_rmat20_wc_full_size(pkg):
+    """R-MAT scale 20, weighted cascade, l = k = 64: every sketch, 50 SKIM seeds
+    and the query set against stored oracle values."""
+    gold = _golden("rmat20_wc")
+    w = synth.WORKLOADS["rmat20_wc"]
+    g = w.graph(device="cuda")
+    assert g.digest() == gold["graph_sha256"]
+    ks = w.keys()
+    with pkg.Skim(g.n, g.src, g.dst, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob) as sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        for v, row in gold["sketches"]["sample_rows"].items():
+            assert [str(int(r)) for r in x[int(v), : ln[int(v)]]] == row
+        assert _digest(x, ln) == gold["sketches"]["sha256"]
+        est = sk.query_batch([q["seeds"] for q in gold["queries"]])
+        for q, e in zip(gold["queries"], est):
+            assert _close(float(e), q["estimate"])
+        seeds, cov = sk.greedy(w.seeds)
+        assert seeds.tolist() == gold["skim"]["seeds"]
+        assert [int(c) for c in cov] == gold["skim"]["cov"]
+
+
+def test_rmat22_wc_sketches_full_size(pkg):
+    gold = _golden("rmat22_wc")
+    if "sketches" not in gold:
+        pytest.skip("no stored sketches")
+    w = synth.WORKLOADS["rmat22_wc"]
+    g = w.graph(device="cuda")
+    assert g.digest() == gold["graph_sha256"]
+    ks = w.keys()
+    with pkg.Skim(g.n, g.src, g.dst, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob) as sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        assert _digest(x, ln) == gold["sketches"]["sha256"]
+        est = sk.query_batch([q["seeds"] for q in gold["queries"]])
+        for q, e in zip(gold["queries"], est):
+            assert _close(float(e), q["estimate"])
+
+
+def test_rmat24_p01_skim_full_size(pkg):
+    """R-MAT scale 24, uniform p = 0.01, l = k = 64: 200 SKIM seeds against
+    stored oracle values."""
+    gold = _golden("rmat24_p01")
+    if "skim" not in gold:
+        pytest.skip("no stored seeds")
+    w = synth.WORKLOADS["rmat24_p01"]
+    g = w.graph(device="cuda")
+    assert g.digest() == gold["graph_sha256"]
+    ks = w.keys()
+    with pkg.Skim(g.n, g.src, g.dst, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob) as sk:
+        seeds, cov = sk.greedy(w.seeds)
+        assert seeds.tolist() == gold["skim"]["seeds"]
+        assert [int(c) for c in cov] == gold["skim"]["cov"]
+
+
+def test_query_sum_is_correctly_rounded(pkg):
+    """The estimate equals the exact sum of the per-rank terms 1/tau, rounded
+    once to double, then divided by l."""
+    g = synth.random_small_graph(3000, 20000, 17)
+    ks = synth.Keys.from_seed(17)
+    l, k = 16, 8
+    with pkg.Skim(g.n, g.src, g.dst, l, k, 0, 0.2, ks.coin, ks.rank, ks.prob) as sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        rng = np.random.default_rng(3)
+        for size in (1, 2, 17, 200, 1000):
+            S = rng.choice(g.n, size=size, replace=False)
+            best = {}
+            for u in S:
+                m = int(ln[u])
+                tau = int(x[u, k - 1]) if m == k else (1 << 64) - 1
+                body = x[u, : k - 1] if m == k else x[u, :m]
+                for z in body:
+                    z = int(z)
+                    best[z] = max(best.get(z, 0), tau)
+            exact = sum((Fraction(1.0 / math.ldexp(float(t), -64)) for t in best.values()), Fraction(0))
+            ref = float(exact) / l
+            assert sk.query(S) == ref
+
+
+def test_error_codes(pkg):
+    g = synth.random_small_graph(50, 200, 2)
+    with pkg.Skim(g.n, g.src, g.dst, 4, 4, 0, 0.2, 1, 2, 3) as sk:
+        with pytest.raises(pkg.SkimError) as e:
+            sk.query([1, 2])
+        assert e.value.code == -3  # not built
+        sk.build_sketches()
+        with pytest.raises(pkg.SkimError) as e:
+            sk.query([1, 50])
+        assert e.value.code == -1
+        with pytest.raises(pkg.SkimError) as e:
+            sk.greedy(51)
+        assert e.value.code == -1
+    src = np.array([1, 0], np.uint32)
+    dst = np.array([2, 1], np.uint32)  # not sorted
+    with pytest.raises(pkg.SkimError) as e:
+        pkg.Skim(3, src, dst, 4, 4)
+    assert e.value.code == -6
+    with pytest.raises(pkg.SkimError) as e:
+        pkg.Skim(3, np.array([1], np.uint32), np.array([1], np.uint32), 4, 4)  # self-loop
+    assert e.value.code == -6
