@@ -89,6 +89,11 @@ typedef struct skim_ctx skim_ctx;
  * Errors: SKIM_EINVAL, SKIM_EGRAPH, SKIM_ENOMEM, SKIM_ECUDA. */
 int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_ctx **out);
 
+/* Recompute the rank order of the n*l pairs (done by skim_create; exposed so
+ * that a caller can time it).  Restarts SKIM (as skim_greedy_reset); the
+ * sketches are unaffected (the ranks themselves do not change). */
+int skim_rank_order(skim_ctx *ctx);
+
 /* Algorithm 2 (Section 5.2): combined bottom-k reachability sketches X_v of
  * all nodes (Eq. combinedrs), computed by rank-batched pruned reverse
  * searches; the result equals the definition exactly.  Sketches stay in
@@ -142,6 +147,33 @@ int skim_oracle_query_batch(skim_ctx *ctx, const uint64_t *offsets, uint32_t q,
 #define SKIM_STAT_RETRIES 7         /* batches re-run with fewer lanes after a table overflow */
 #define SKIM_STAT_COUNT 8
 int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
+
+/* Kernel timing with CUDA events on the context's stream (off by default).
+ * When on, the device time of each launch group below is accumulated until
+ * the next call with reset != 0.  Kinds (index into ms_out / launches_out):
+ *   SKIM_K_REV   reverse searches (Algorithms 1 and 2, the batched BFS)
+ *   SKIM_K_FWD   residual forward searches (Algorithm 1)
+ *   SKIM_K_ACCEPT Algorithm 2 acceptance into the sketches
+ *   SKIM_K_SORT  grouping of visit records by node (radix sort)
+ *   SKIM_K_STEP  SKIM per-node steps (first-to-k candidates, commits)
+ *   SKIM_K_RANKS rank order of the n*l pairs
+ *   SKIM_K_QUERY union-estimator queries
+ *   SKIM_K_SETUP CSR construction and validation */
+#define SKIM_K_REV 0
+#define SKIM_K_FWD 1
+#define SKIM_K_ACCEPT 2
+#define SKIM_K_SORT 3
+#define SKIM_K_STEP 4
+#define SKIM_K_RANKS 5
+#define SKIM_K_QUERY 6
+#define SKIM_K_SETUP 7
+#define SKIM_K_COUNT 8
+int skim_set_timing(skim_ctx *ctx, int on);
+
+/* Number of kernels this library has launched in the calling process since it
+ * was loaded (all contexts).  out (host). */
+int skim_kernel_launches(uint64_t *out);
+int skim_kernel_times(skim_ctx *ctx, double *ms_out, uint64_t *launches_out, uint32_t count, int reset);
 
 int skim_destroy(skim_ctx *ctx);
 

@@ -20,6 +20,7 @@ SKIM_OK = 0
 _ERR = {-1: "SKIM_EINVAL", -2: "SKIM_ENOMEM", -3: "SKIM_ENOTBUILT", -4: "SKIM_ETIMEOUT", -5: "SKIM_ECUDA",
         -6: "SKIM_EGRAPH", -7: "SKIM_ERANGE"}
 PROB_UNIFORM, PROB_WC, PROB_TRIVALENCY = 0, 1, 2
+KERNEL_NAMES = ("rev_search", "fwd_search", "accept", "record_sort", "skim_step", "rank_order", "query", "setup")
 STAT_NAMES = ("rev_visits", "rev_coins", "insertions", "fwd_visits", "fwd_coins", "batches", "ranks", "retries")
 
 
@@ -63,6 +64,10 @@ def load():
     lib.skim_oracle_query_batch.argtypes = [vp, vp, u32, vp, vp, C.c_int]
     lib.skim_get_stats.argtypes = [vp, vp, u32]
     lib.skim_destroy.argtypes = [vp]
+    lib.skim_rank_order.argtypes = [vp]
+    lib.skim_set_timing.argtypes = [vp, C.c_int]
+    lib.skim_kernel_times.argtypes = [vp, vp, vp, u32, C.c_int]
+    lib.skim_kernel_launches.argtypes = [vp]
     lib.skim_strerror.argtypes = [C.c_int]
     lib.skim_strerror.restype = C.c_char_p
     _lib = lib
@@ -88,6 +93,18 @@ def skim_create(graph: skim_graph, params: skim_params, stream: int = 0) -> int:
     _check(load().skim_create(C.byref(graph), C.byref(params), C.c_void_p(stream or None), C.byref(h)),
            "skim_create")
     return h.value
+
+
+def skim_rank_order(ctx: int):
+    _check(load().skim_rank_order(ctx), "skim_rank_order")
+
+
+def skim_set_timing(ctx: int, on: int):
+    _check(load().skim_set_timing(ctx, on), "skim_set_timing")
+
+
+def skim_kernel_times(ctx: int, ms_out: np.ndarray, launches_out: np.ndarray, count: int, reset: int):
+    _check(load().skim_kernel_times(ctx, _ptr(ms_out), _ptr(launches_out), count, reset), "skim_kernel_times")
 
 
 def skim_build_sketches(ctx: int):
@@ -124,6 +141,12 @@ def skim_oracle_query_batch(ctx: int, offsets: np.ndarray, q: int, seeds, est_ou
 
 def skim_get_stats(ctx: int, out: np.ndarray, count: int):
     _check(load().skim_get_stats(ctx, _ptr(out), count), "skim_get_stats")
+
+
+def skim_kernel_launches() -> int:
+    out = np.zeros(1, np.uint64)
+    _check(load().skim_kernel_launches(_ptr(out)), "skim_kernel_launches")
+    return int(out[0])
 
 
 def skim_destroy(ctx: int):
@@ -207,6 +230,18 @@ class Skim:
         out = np.zeros(max(1, len(sets)), np.float64)
         skim_oracle_query_batch(self.ctx, off, len(sets), flat, out, 0)
         return out[: len(sets)]
+
+    def rank_order(self):
+        skim_rank_order(self.ctx)
+
+    def set_timing(self, on: bool = True):
+        skim_set_timing(self.ctx, 1 if on else 0)
+
+    def kernel_times(self, reset: bool = False) -> dict:
+        ms = np.zeros(len(KERNEL_NAMES), np.float64)
+        cnt = np.zeros(len(KERNEL_NAMES), np.uint64)
+        skim_kernel_times(self.ctx, ms, cnt, len(KERNEL_NAMES), 1 if reset else 0)
+        return {n: (float(a), int(b)) for n, a, b in zip(KERNEL_NAMES, ms, cnt)}
 
     def stats(self) -> dict:
         out = np.zeros(len(STAT_NAMES), np.uint64)

@@ -211,6 +211,7 @@ __global__ void k_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl) {
 }  // namespace
 
 cudaError_t launch_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, cudaStream_t s) {
+    note_launch();
     k_lane_inst<<<grid_for(B, 256), 256, 0, s>>>(lane_pair, B, l, lane_inst);
     return cudaGetLastError();
 }
@@ -219,12 +220,14 @@ cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint
                           uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
                           cudaStream_t s) {
     if (R == 0) return cudaSuccess;
+    note_launch();
     k_accept<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, lane_inst, lane_rank, l, k, lcnt,
                                               full, X, xlen, ctl);
     return cudaGetLastError();
 }
 cudaError_t launch_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hkeys, uint64_t *hvals, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
+    note_launch();
     k_clear_slots<<<grid_for(R, 256), 256, 0, s>>>(rec_val, R, hkeys, hvals);
     return cudaGetLastError();
 }
@@ -232,6 +235,7 @@ cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, 
                               const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
                               uint32_t k, DevCtl *ctl, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
+    note_launch();
     k_candidates<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, size, k, ctl);
     return cudaGetLastError();
 }
@@ -239,6 +243,7 @@ cudaError_t launch_commit_count(const uint64_t *rec_key, const uint32_t *rec_val
                                 const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size,
                                 uint64_t *lane_cnt, DevCtl *ctl, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
+    note_launch();
     k_commit_count<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, hi, size,
                                                     reinterpret_cast<unsigned long long *>(lane_cnt), ctl);
     return cudaGetLastError();
@@ -248,6 +253,7 @@ cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_v
                                   const uint64_t *lane_off, uint32_t *lane_fill, uint64_t idx_base,
                                   uint32_t *idx_nodes, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
+    note_launch();
     k_commit_scatter<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, hi, lane_off,
                                                       lane_fill, idx_base, idx_nodes);
     return cudaGetLastError();
@@ -255,6 +261,7 @@ cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_v
 cudaError_t launch_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32_t hi, const uint64_t *lane_cnt,
                                    const uint64_t *lane_off, uint64_t idx_base, uint64_t *seg_start,
                                    uint32_t *seg_len, cudaStream_t s) {
+    note_launch();
     k_commit_segments<<<grid_for(hi - lo + 1, 256), 256, 0, s>>>(lane_pair, lo, hi, lane_cnt, lane_off, idx_base,
                                                                  seg_start, seg_len);
     return cudaGetLastError();
@@ -262,14 +269,17 @@ cudaError_t launch_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint3
 cudaError_t launch_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, uint32_t l, const uint64_t *covered,
                             uint64_t *alive, cudaStream_t s) {
     if (lo >= B) return cudaSuccess;
+    note_launch();
     k_refilter<<<grid_for(B - lo, 256), 256, 0, s>>>(lane_pair, lo, B, l, covered, alive);
     return cudaGetLastError();
 }
 cudaError_t launch_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl, cudaStream_t s) {
+    note_launch();
     k_argmax_size<<<grid_for(n, 256), 256, 0, s>>>(size, n, ctl);
     return cudaGetLastError();
 }
 cudaError_t launch_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl, cudaStream_t s) {
+    note_launch();
     k_min_unchosen<<<grid_for(n, 256), 256, 0, s>>>(chosen, n, ctl);
     return cudaGetLastError();
 }

@@ -32,6 +32,8 @@ struct skim_ctx {
     // rank order
     uint64_t *srank = nullptr;
     uint32_t *spair = nullptr;
+    void *rank_ws = nullptr;
+    uint64_t rank_key = 0;
     // control
     DevCtl *ctl = nullptr;
     DevCtl *hctl = nullptr;  // pinned mirror
@@ -80,6 +82,13 @@ struct skim_ctx {
     uint64_t qmeta_cap = 0;
     // counters of the last build/greedy call
     uint64_t hstats[SKIM_STAT_COUNT] = {0};
+    // kernel timing (CUDA events on the context stream)
+    bool timing = false;
+    double kms[SKIM_K_COUNT] = {0};
+    uint64_t klaunch[SKIM_K_COUNT] = {0};
+    struct Pend { cudaEvent_t a, b; int kind; };
+    std::vector<Pend> kpend;
+    std::vector<cudaEvent_t> kpool;
 };
 
 namespace {
@@ -138,9 +147,52 @@ uint64_t tm1_of(double p) {
     return static_cast<uint64_t>(std::ldexp(p, 64)) - 1ull;
 }
 
+cudaEvent_t ev_get(skim_ctx *c) {
+    if (!c->kpool.empty()) {
+        cudaEvent_t e = c->kpool.back();
+        c->kpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket a launch group with events; resolved at the next synchronisation.
+struct KTimer {
+    skim_ctx *c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    KTimer(skim_ctx *cc, int k) : c(cc), kind(k) {
+        if (c->timing) {
+            a = ev_get(c);
+            cudaEventRecord(a, c->st);
+        }
+    }
+    ~KTimer() {
+        if (c->timing && a) {
+            cudaEvent_t b = ev_get(c);
+            cudaEventRecord(b, c->st);
+            c->kpend.push_back({a, b, kind});
+            c->klaunch[kind]++;
+        }
+    }
+};
+
+void resolve_timers(skim_ctx *c) {
+    for (auto &p : c->kpend) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->kms[p.kind] += ms;
+        c->kpool.push_back(p.a);
+        c->kpool.push_back(p.b);
+    }
+    c->kpend.clear();
+}
+
 int sync_ctl(skim_ctx *c) {
     CK(c, cudaMemcpyAsync(c->hctl, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaStreamSynchronize(c->st));
+    resolve_timers(c);
     return SKIM_OK;
 }
 
@@ -151,10 +203,11 @@ int reset_ctl(skim_ctx *c) {
     return SKIM_OK;
 }
 
+// empty the work queue (cursors and slots) before another traversal round
 int reset_queue(skim_ctx *c, uint64_t used) {
     uint64_t u = std::min(used, c->qcap);
     if (u) CK(c, cudaMemsetAsync(c->q, 0, u * sizeof(Item), c->st));
-    CK(c, cudaMemsetAsync(c->ctl, 0, 3 * sizeof(unsigned long long), c->st));
+    CK(c, cudaMemsetAsync(&c->ctl->q_head, 0, 3 * sizeof(HotCounter), c->st));
     CK(c, cudaMemsetAsync(&c->ctl->spill, 0, sizeof(unsigned), c->st));
     return SKIM_OK;
 }
@@ -191,21 +244,24 @@ TravArgs base_args(skim_ctx *c, bool forward) {
 // Run traversal rounds until the queue drains with nothing spilled.
 int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out) {
     for (;;) {
-        CK(c, launch_traverse(a, forward, forward ? c->grid_fwd : c->grid_rev, c->st));
+        {
+            KTimer kt(c, forward ? SKIM_K_FWD : SKIM_K_REV);
+            CK(c, launch_traverse(a, forward, forward ? c->grid_fwd : c->grid_rev, c->st));
+        }
         RC(sync_ctl(c));
         const DevCtl &h = *c->hctl;
         if (h.err & kErrTimeout) {
             c->broken = true;
             return SKIM_ETIMEOUT;
         }
-        if (R_out) *R_out = h.rec_count;
+        if (R_out) *R_out = h.rec_count.v;
         if (h.err & kErrRetryable) return SKIM_OK;  // caller re-runs the batch
         if (!h.spill) return SKIM_OK;
-        RC(reset_queue(c, h.q_tail));
+        RC(reset_queue(c, h.q_tail.v));
         if (forward)
             CK(c, launch_respill_fwd(a, c->n, c->st));
         else
-            CK(c, launch_respill_rev(a, h.rec_count, c->st));
+            CK(c, launch_respill_rev(a, h.rec_count.v, c->st));
     }
 }
 
@@ -229,16 +285,19 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     const DevCtl &h = *c->hctl;
     if (h.err & kErrRetryable) {
         *retry = true;
-        RC(reset_queue(c, h.q_tail));
+        RC(reset_queue(c, h.q_tail.v));
         CK(c, cudaMemsetAsync(c->hkeys, 0xff, c->hcap * sizeof(uint64_t), c->st));
         CK(c, cudaMemsetAsync(c->hvals, 0, c->hcap * sizeof(uint64_t), c->st));
         CK(c, cudaMemsetAsync(c->pend, 0, c->hcap * sizeof(uint64_t), c->st));
         c->hstats[SKIM_STAT_RETRIES]++;
         return SKIM_OK;
     }
-    RC(reset_queue(c, h.q_tail));
+    RC(reset_queue(c, h.q_tail.v));
     const int bits = bitlen(c->n - 1) + static_cast<int>(tbits);
-    CK(c, radix_sort_pairs(c->rkey, c->rval, c->rkey2, c->rval2, R, bits, c->ws, c->st));
+    {
+        KTimer kt(c, SKIM_K_SORT);
+        CK(c, radix_sort_pairs(c->rkey, c->rval, c->rkey2, c->rval2, R, bits, c->ws, c->st));
+    }
     c->bR = R;
     c->btbits = tbits;
     c->hstats[SKIM_STAT_BATCHES]++;
@@ -321,6 +380,7 @@ int commit_lanes(skim_ctx *c, uint32_t lo, uint32_t hi) {
     const uint32_t cnt = hi - lo + 1;
     CK(c, cudaMemsetAsync(c->lane_cnt + lo, 0, cnt * sizeof(uint64_t), c->st));
     CK(c, cudaMemsetAsync(c->lane_fill + lo, 0, cnt * sizeof(uint32_t), c->st));
+    KTimer kt(c, SKIM_K_STEP);
     CK(c, launch_commit_count(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, lo, hi, c->size, c->lane_cnt,
                               c->ctl, c->st));
     CK(c, exclusive_scan_u64(c->lane_cnt + lo, c->lane_off + lo, cnt, reinterpret_cast<uint64_t *>(&c->ctl->total), c->ws, c->st));
@@ -342,7 +402,7 @@ int residual(skim_ctx *c, uint32_t x, uint64_t *cov) {
     CK(c, launch_fwd_source(a, x, c->st));
     RC(run_traversal(c, a, true, nullptr));
     *cov = c->hctl->ix_cov;
-    RC(reset_queue(c, c->hctl->q_tail));
+    RC(reset_queue(c, c->hctl->q_tail.v));
     CK(c, cudaMemsetAsync(c->chosen + x, 1, 1, c->st));
     return SKIM_OK;
 }
@@ -351,8 +411,11 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
     for (;;) {
         if (c->batch_active) {
             CK(c, cudaMemsetAsync(&c->ctl->best, 0xff, sizeof(unsigned long long), c->st));
-            CK(c, launch_candidates(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, c->blo, c->size, c->k,
-                                    c->ctl, c->st));
+            {
+                KTimer kt(c, SKIM_K_STEP);
+                CK(c, launch_candidates(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, c->blo, c->size,
+                                        c->k, c->ctl, c->st));
+            }
             RC(sync_ctl(c));
             const uint64_t best = c->hctl->best;
             if (best != ~0ull) {
@@ -406,6 +469,16 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
     }
 }
 
+int rank_order(skim_ctx *c) {
+    {
+        KTimer kt(c, SKIM_K_RANKS);
+        CK(c, rank_sort(c->rank_key, c->nl, c->srank, c->spair, c->rank_ws, c->st));
+    }
+    CK(c, cudaStreamSynchronize(c->st));
+    resolve_timers(c);
+    return SKIM_OK;
+}
+
 int ensure_query_space(skim_ctx *c, uint64_t seeds, uint64_t q, uint64_t table) {
     if (seeds > c->qseeds_cap) {
         dfree(c->qseeds);
@@ -456,6 +529,7 @@ int skim_destroy(skim_ctx *c) {
     cudaStreamSynchronize(c->st);
     dfree(c->fptr); dfree(c->fcol); dfree(c->rptr); dfree(c->rcol); dfree(c->thr_wc);
     dfree(c->srank); dfree(c->spair);
+    if (c->rank_ws) cudaFree(c->rank_ws);
     dfree(c->ctl); dfree(c->dflag);
     if (c->hctl) cudaFreeHost(c->hctl);
     dfree(c->q); dfree(c->hkeys); dfree(c->hvals); dfree(c->pend);
@@ -466,6 +540,8 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->covered); dfree(c->seg_start); dfree(c->pend_trav); dfree(c->pend_erase);
     dfree(c->size); dfree(c->seg_len); dfree(c->idx); dfree(c->chosen);
     dfree(c->qk); dfree(c->qv); dfree(c->qseeds); dfree(c->qoff); dfree(c->qtoff); dfree(c->qout);
+    for (auto &p : c->kpend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : c->kpool) cudaEventDestroy(e);
     delete c;
     return SKIM_OK;
 }
@@ -545,8 +621,10 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
             goto fail;
         }
         // workspace for scans and sorts
-        const uint64_t rcap = std::min<uint64_t>(std::max<uint64_t>(4ull * std::min<uint64_t>(nl, 1u << 18), 1u << 20),
-                                                 1ull << 25);
+        // visit records per batch: a few per lane; sized generously so that
+        // re-running a batch with fewer lanes stays rare
+        const uint64_t lanes_max = std::min<uint64_t>(nl, prm->batch_lanes ? prm->batch_lanes : (1u << 18));
+        const uint64_t rcap = std::min<uint64_t>(std::max<uint64_t>(16ull * lanes_max, 1u << 20), 1ull << 26);
         size_t ws = std::max({scan_workspace_bytes(static_cast<size_t>(n) + 1), radix_workspace_bytes(m),
                               radix_workspace_bytes(rcap), scan_workspace_bytes(static_cast<size_t>(kMaxWords) * 64)});
         c->ws_bytes = ws;
@@ -602,15 +680,9 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         // rank order of the n*l pairs
         TRY(dalloc(c, &c->srank, nl));
         TRY(dalloc(c, &c->spair, nl));
-        {
-            void *rws = nullptr;
-            TRYC(cudaMalloc(&rws, rank_sort_workspace_bytes(nl)));
-            cudaError_t e = rank_sort(prm->rank_key, nl, c->srank, c->spair, rws, c->st);
-            cudaError_t e2 = cudaStreamSynchronize(c->st);
-            cudaFree(rws);
-            TRYC(e);
-            TRYC(e2);
-        }
+        TRYC(cudaMalloc(&c->rank_ws, rank_sort_workspace_bytes(nl)));
+        c->rank_key = prm->rank_key;
+        TRY(rank_order(c));
         // traversal scratch
         c->lane_cap = static_cast<uint32_t>(std::min<uint64_t>(pow2_at_least(std::min<uint64_t>(nl, kMaxWords * 64ull)),
                                                                kMaxWords * 64ull));
@@ -649,6 +721,18 @@ fail:
     return rc;
 }
 
+int skim_rank_order(skim_ctx *c) {
+    if (!c) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    if (c->batch_active) {
+        RC(clear_batch(c));
+        c->batch_active = false;
+    }
+    RC(rank_order(c));
+    c->sk_init = false;
+    return SKIM_OK;
+}
+
 int skim_build_sketches(skim_ctx *c) {
     if (!c) return SKIM_EINVAL;
     if (c->broken) return SKIM_ECUDA;
@@ -680,8 +764,11 @@ int skim_build_sketches(skim_ctx *c) {
             B = std::max<uint32_t>(64, b / 2);
             continue;
         }
-        CK(c, launch_accept(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->lane_inst, c->srank + p0, c->l, c->k,
-                            c->lcnt, c->full, c->X, c->xlen, c->ctl, c->st));
+        {
+            KTimer kt(c, SKIM_K_ACCEPT);
+            CK(c, launch_accept(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->lane_inst, c->srank + p0, c->l,
+                                c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl, c->st));
+        }
         RC(clear_batch(c));
         p0 += b;
         c->hstats[SKIM_STAT_RANKS] += b;
@@ -773,13 +860,17 @@ int skim_oracle_query_batch(skim_ctx *c, const uint64_t *offsets, uint32_t q, co
     CK(c, cudaMemcpyAsync(c->qtoff, toff.data(), toff.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, c->st));
     CK(c, cudaMemsetAsync(c->dflag, 0, sizeof(unsigned), c->st));
     double *dout = on_device ? est_out : c->qout;
-    CK(c, launch_query(c->X, c->xlen, c->n, c->k, c->l, dseeds, c->qoff, c->qtoff, q, c->qk, c->qv, dout, c->dflag,
-                       c->st));
+    {
+        KTimer kt(c, SKIM_K_QUERY);
+        CK(c, launch_query(c->X, c->xlen, c->n, c->k, c->l, dseeds, c->qoff, c->qtoff, q, c->qk, c->qv, dout,
+                           c->dflag, c->st));
+    }
     unsigned bad = 0;
     CK(c, cudaMemcpyAsync(&bad, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
     if (!on_device)
         CK(c, cudaMemcpyAsync(est_out, c->qout, q * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaStreamSynchronize(c->st));
+    resolve_timers(c);
     return bad ? SKIM_EINVAL : SKIM_OK;
 }
 
@@ -787,6 +878,33 @@ int skim_oracle_query(skim_ctx *c, const uint32_t *seeds, uint32_t n_seeds, doub
     if (!c || !est_out || (n_seeds && !seeds)) return SKIM_EINVAL;
     uint64_t off[2] = {0, n_seeds};
     return skim_oracle_query_batch(c, off, 1, seeds, est_out, 0);
+}
+
+int skim_kernel_launches(uint64_t *out) {
+    if (!out) return SKIM_EINVAL;
+    *out = g_kernel_launches.load();
+    return SKIM_OK;
+}
+
+int skim_set_timing(skim_ctx *c, int on) {
+    if (!c) return SKIM_EINVAL;
+    c->timing = on != 0;
+    return SKIM_OK;
+}
+
+int skim_kernel_times(skim_ctx *c, double *ms_out, uint64_t *launches_out, uint32_t count, int reset) {
+    if (!c) return SKIM_EINVAL;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail_cuda(c, cudaGetLastError());
+    resolve_timers(c);
+    for (uint32_t i = 0; i < count && i < SKIM_K_COUNT; i++) {
+        if (ms_out) ms_out[i] = c->kms[i];
+        if (launches_out) launches_out[i] = c->klaunch[i];
+    }
+    if (reset) {
+        std::fill(c->kms, c->kms + SKIM_K_COUNT, 0.0);
+        std::fill(c->klaunch, c->klaunch + SKIM_K_COUNT, 0);
+    }
+    return SKIM_OK;
 }
 
 int skim_get_stats(skim_ctx *c, uint64_t *out, uint32_t count) {

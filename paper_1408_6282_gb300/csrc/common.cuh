@@ -6,6 +6,7 @@
 // Both are drawn from the SplitMix64 output function (Steele, Lea, Flood
 // 2014), read as 64-bit integers, so instances are never materialised.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -13,6 +14,11 @@
 #define SKIM_HD __host__ __device__ __forceinline__
 
 namespace skim {
+
+// Kernels launched by this library since it was loaded (every launch site
+// calls note_launch()).
+inline std::atomic<unsigned long long> g_kernel_launches{0};
+inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kEmptyKey = ~0ull;
@@ -24,7 +30,7 @@ constexpr uint32_t kChunk = 4096;
 constexpr uint32_t kChunkBits = 12;          // chunk id field width in Item::w
 constexpr uint32_t kMaxDegree = kChunk << kChunkBits;  // 16.7M
 constexpr uint32_t kEraseTag = 0x80000000u;
-constexpr uint32_t kNopTag = 0xFFFFFFFFu;      // placeholder item (a spilled reservation)
+constexpr uint32_t kNopTag = 0xFFFFFFFEu;      // placeholder item (a spilled reservation)
 constexpr uint32_t kMaxWords = 1u << 19;       // lane words per batch (w field: word << 12 | chunk < 2^31)
 
 // SplitMix64 output function.
@@ -46,11 +52,13 @@ SKIM_HD bool coin_live(uint64_t he, uint32_t inst, uint64_t tm1) {
     return fmix(he + kGolden * static_cast<uint64_t>(inst + 1)) <= tm1;
 }
 
-// Work item of the asynchronous traversals (16 bytes).  mask != 0 marks a
-// written slot.  Reverse searches: v = node, w = (lane word << 12) | chunk,
-// mask = lanes of that word visiting v.  Residual searches: w = chunk, mask =
-// instances.  Index-erase items: w = kEraseTag | chunk, v = segment length,
-// mask = segment start + 1.
+// Work item of the asynchronous traversals (16 bytes).  Reverse searches:
+// v = node, w = (lane word << 12) | chunk, mask = lanes of that word visiting
+// v.  Residual searches: w = chunk, mask = instances.  Index-erase items:
+// w = kEraseTag | chunk, v = segment length, mask = segment start + 1.
+// In the queue, v and w are stored plus one; every field of a written slot
+// is then non-zero, so a reader that sees three non-zero fields has the whole
+// item, and the queue needs no fences (slots start zeroed).
 struct __align__(16) Item {
     uint32_t v;
     uint32_t w;
@@ -63,10 +71,16 @@ struct __align__(16) Item {
 constexpr unsigned kErrRecords = 2u, kErrHash = 4u, kErrTimeout = 8u;
 constexpr unsigned kErrRetryable = kErrRecords | kErrHash;
 
+// A counter alone on its 128-byte line: the queue cursors are hit by every
+// warp, and sharing a line would serialise them at one L2 slice.
+struct alignas(128) HotCounter {
+    unsigned long long v;
+    unsigned long long pad[15];
+};
+
 // Device control block: queue cursors, counters, flags, reductions.
 struct DevCtl {
-    unsigned long long q_head, q_tail, q_done;
-    unsigned long long rec_count;
+    HotCounter q_head, q_tail, q_done, rec_count;
     unsigned long long best;        // SKIM stop candidate: (lane << 32) | node
     unsigned long long ix_cov;      // pairs newly covered by the residual search
     unsigned long long argmax;      // (size << 32) | ~node

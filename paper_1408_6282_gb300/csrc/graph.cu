@@ -168,34 +168,41 @@ int bucket_bits(uint64_t nl) {
 cudaError_t launch_check_edges(const uint32_t *src, const uint32_t *dst, uint64_t m, uint32_t n, unsigned *bad,
                                cudaStream_t s) {
     if (m == 0) return cudaSuccess;
+    note_launch();
     k_check_edges<<<grid_for(m, 256), 256, 0, s>>>(src, dst, m, n, bad);
     return cudaGetLastError();
 }
 cudaError_t launch_degree_count(const uint32_t *idx, uint64_t m, uint64_t *deg, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
+    note_launch();
     k_degree_count<<<grid_for(m, 256), 256, 0, s>>>(idx, m, deg);
     return cudaGetLastError();
 }
 cudaError_t launch_u64_to_u32(const uint64_t *in, uint32_t *out, size_t n, cudaStream_t s) {
+    note_launch();
     k_u64_to_u32<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
     return cudaGetLastError();
 }
 cudaError_t launch_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint64_t m, uint64_t *key, uint32_t *val,
                                  cudaStream_t s) {
     if (m == 0) return cudaSuccess;
+    note_launch();
     k_make_rev_keys<<<grid_for(m, 256), 256, 0, s>>>(src, dst, m, key, val);
     return cudaGetLastError();
 }
 cudaError_t launch_split_rev(const uint64_t *key, uint64_t m, uint32_t *rcol, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
+    note_launch();
     k_split_rev<<<grid_for(m, 256), 256, 0, s>>>(key, m, rcol);
     return cudaGetLastError();
 }
 cudaError_t launch_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr, cudaStream_t s) {
+    note_launch();
     k_wc_thresholds<<<grid_for(n, 256), 256, 0, s>>>(rptr, n, thr);
     return cudaGetLastError();
 }
 cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out, cudaStream_t s) {
+    note_launch();
     k_max_degree<<<grid_for(n, 256), 256, 0, s>>>(ptr, n, out);
     return cudaGetLastError();
 }
@@ -221,11 +228,14 @@ cudaError_t rank_sort(uint64_t rank_key, uint64_t nl, uint64_t *sorted_rank, uin
     cudaError_t e = cudaMemsetAsync(cnt, 0, (nb + 1) * sizeof(uint64_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, nb * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
+    note_launch();
     k_rank_count<<<grid_for(nl, 256), 256, 0, s>>>(rank_key, nl, bb, reinterpret_cast<unsigned long long *>(cnt));
     // off[b] = exclusive prefix; off[nb] = nl (scan over nb+1 entries with cnt[nb] = 0)
     e = exclusive_scan_u64(cnt, off, nb + 1, nullptr, sws, s);
     if (e != cudaSuccess) return e;
+    note_launch();
     k_rank_scatter<<<grid_for(nl, 256), 256, 0, s>>>(rank_key, nl, bb, off, fill, tmp);
+    note_launch();
     k_bucket_sort<<<static_cast<unsigned>(nb), kBucketThreads, 0, s>>>(rank_key, off, tmp, sorted_rank, sorted_pair);
     return cudaGetLastError();
 }

@@ -181,13 +181,16 @@ cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, size_t n, uint
     }
     size_t nb = cdiv(n, kScanTile);
     if (nb == 1) {
+        note_launch();
         k_scan_tile<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total);
         return cudaGetLastError();
     }
     uint64_t *bsum = static_cast<uint64_t *>(ws);
+    note_launch();
     k_block_sums<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(in, n, bsum);
     cudaError_t e = exclusive_scan_u64(bsum, bsum, nb, total, bsum + nb, s);
     if (e != cudaSuccess) return e;
+    note_launch();
     k_scan_tile<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(in, out, n, bsum, nullptr);
     return cudaGetLastError();
 }
@@ -209,9 +212,11 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *alt_keys,
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; p++) {
         int shift = p * 8;
+        note_launch();
         k_rs_hist<<<static_cast<unsigned>(ntiles), kRsThreads, 0, s>>>(sk, n, shift, hist, ntiles);
         cudaError_t e = exclusive_scan_u64(hist, hist, 256 * ntiles, nullptr, sws, s);
         if (e != cudaSuccess) return e;
+        note_launch();
         k_rs_scatter<<<static_cast<unsigned>(ntiles), kRsThreads, 0, s>>>(sk, sv, dk, dv, n, shift, hist, ntiles);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -173,6 +173,7 @@ cudaError_t launch_query(const uint64_t *X, const uint32_t *xlen, uint32_t n, ui
                          const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off, uint32_t q,
                          uint64_t *hkeys, uint64_t *hvals, double *out, unsigned *err, cudaStream_t s) {
     if (q == 0) return cudaSuccess;
+    note_launch();
     k_query<<<q, kQThreads, 0, s>>>(X, xlen, n, k, l, seeds, offsets, table_off, hkeys, hvals, out, err);
     return cudaGetLastError();
 }

@@ -72,6 +72,17 @@ SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t
 
 SKIM_DEV uint32_t n_chunks(uint32_t deg) { return (deg + kChunk - 1) / kChunk; }
 
+// Per-lane counters, added to DevCtl once when a warp finishes.
+struct Acc {
+    unsigned long long visits = 0, coins = 0, cov = 0;
+};
+
+SKIM_DEV void flush_acc(const TravArgs &A, const Acc &acc, bool fwd) {
+    warp_add(&A.ctl->stats[fwd ? kStFwdVisits : kStRevVisits], acc.visits);
+    warp_add(&A.ctl->stats[fwd ? kStFwdCoins : kStRevCoins], acc.coins);
+    if (fwd) warp_add(&A.ctl->ix_cov, acc.cov);
+}
+
 // Reserve `cnt` queue slots per lane (warp-aggregated); returns the lane's
 // first slot.  Slots at or beyond capacity never receive an item: they are
 // counted as done at once, and the caller parks that work in a pending mask.
@@ -79,21 +90,31 @@ SKIM_DEV unsigned long long reserve_slots(const TravArgs &A, uint32_t cnt) {
     unsigned long long tot;
     unsigned long long ex = warp_excl_scan(cnt, &tot);
     unsigned long long base = 0;
-    if ((threadIdx.x & 31) == 0 && tot) base = atomicAdd(&A.ctl->q_tail, tot);
+    if ((threadIdx.x & 31) == 0 && tot) base = atomicAdd(&A.ctl->q_tail.v, tot);
     base = __shfl_sync(kFull, base, 0);
     if ((threadIdx.x & 31) == 0 && tot && base + tot > A.qcap) {
         unsigned long long lost = base + tot - (base >= A.qcap ? base : A.qcap);
-        atomicAdd(&A.ctl->q_done, lost);
+        atomicAdd(&A.ctl->q_done.v, lost);
     }
     return base + ex;
 }
 
 SKIM_DEV void write_item(const TravArgs &A, unsigned long long slot, uint32_t v, uint32_t w, uint64_t mask) {
     if (slot >= A.qcap) return;
-    Item *it = &A.q[slot];
-    it->v = v;
-    it->w = w;
-    st_release(&it->mask, mask);
+    const uint64_t lo = (static_cast<uint64_t>(w + 1) << 32) | (v + 1);
+    asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(&A.q[slot]), "l"(lo), "l"(mask) : "memory");
+}
+
+// Reads a slot; true once all of its fields have arrived.
+SKIM_DEV bool read_item(const TravArgs &A, unsigned long long slot, Item *it) {
+    uint64_t lo, m;
+    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(m) : "l"(&A.q[slot]) : "memory");
+    const uint32_t v1 = static_cast<uint32_t>(lo), w1 = static_cast<uint32_t>(lo >> 32);
+    if (v1 == 0 || w1 == 0 || m == 0) return false;
+    it->v = v1 - 1;
+    it->w = w1 - 1;
+    it->mask = m;
+    return true;
 }
 
 // A lane whose reservation does not fit fills its in-capacity slots with
@@ -120,7 +141,7 @@ SKIM_DEV void push_rev(const TravArgs &A, uint32_t u, uint32_t t, uint64_t nb, u
 }
 
 // Warp-collective: lanes with `act` visit node u with lane bits `bits` in word t.
-SKIM_DEV void emit_rev(const TravArgs &A, bool act, uint32_t u, uint32_t t, uint64_t bits) {
+SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32_t t, uint64_t bits) {
     uint64_t nb = 0;
     bool first = false;
     uint64_t slot = 0;
@@ -138,7 +159,7 @@ SKIM_DEV void emit_rev(const TravArgs &A, bool act, uint32_t u, uint32_t t, uint
         unsigned ball = __ballot_sync(kFull, first);
         if (ball) {
             unsigned long long base = 0;
-            if ((threadIdx.x & 31) == 0) base = atomicAdd(&A.ctl->rec_count, static_cast<unsigned long long>(__popc(ball)));
+            if ((threadIdx.x & 31) == 0) base = atomicAdd(&A.ctl->rec_count.v, static_cast<unsigned long long>(__popc(ball)));
             base = __shfl_sync(kFull, base, 0);
             if (first) {
                 unsigned long long r = base + __popc(ball & lanemask_lt());
@@ -151,7 +172,7 @@ SKIM_DEV void emit_rev(const TravArgs &A, bool act, uint32_t u, uint32_t t, uint
             }
         }
     }
-    warp_add(&A.ctl->stats[kStRevVisits], __popcll(nb));
+    acc.visits += __popcll(nb);
     push_rev(A, u, t, nb, slot);
 }
 
@@ -190,7 +211,7 @@ SKIM_DEV void push_fwd(const TravArgs &A, uint32_t w, uint64_t trav, uint64_t er
 
 // Warp-collective: lanes with `act` reach node w in the instances of `live`
 // during a residual search.
-SKIM_DEV void emit_fwd(const TravArgs &A, bool act, uint32_t w, uint64_t live) {
+SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64_t live) {
     uint64_t nb = 0;
     if (act && live) {
         uint64_t cov = *reinterpret_cast<volatile uint64_t *>(&A.covered[w]);
@@ -200,8 +221,8 @@ SKIM_DEV void emit_fwd(const TravArgs &A, bool act, uint32_t w, uint64_t live) {
             nb &= ~old;
         }
     }
-    warp_add(&A.ctl->ix_cov, __popcll(nb));
-    warp_add(&A.ctl->stats[kStFwdVisits], __popcll(nb));
+    acc.cov += __popcll(nb);
+    acc.visits += __popcll(nb);
     uint64_t erase = 0;
     for (uint64_t m = nb; m; m &= m - 1) {
         int i = __ffsll(m) - 1;
@@ -213,7 +234,7 @@ SKIM_DEV void emit_fwd(const TravArgs &A, bool act, uint32_t w, uint64_t live) {
 // Process the items held by the lanes with `have`, edges (or index entries)
 // of all items flattened over the warp.
 template <bool FWD>
-SKIM_DEV void process_items(const TravArgs &A, bool have, const Item &it) {
+SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &it) {
     const int lane = threadIdx.x & 31;
     uint32_t begin = 0, cnt = 0;
     uint64_t tm1 = 0;
@@ -236,7 +257,6 @@ SKIM_DEV void process_items(const TravArgs &A, bool have, const Item &it) {
     unsigned long long tot;
     unsigned long long excl = warp_excl_scan(cnt, &tot);
     unsigned long long incl = excl + cnt;
-    unsigned long long coins = 0;
     for (unsigned long long b0 = 0; b0 < tot; b0 += 32) {
         unsigned long long f = b0 + lane;
         int lo = 0;
@@ -268,7 +288,7 @@ SKIM_DEV void process_items(const TravArgs &A, bool have, const Item &it) {
                     uint64_t he = edge_state(A.cm.coin_key, ov, w);
                     uint64_t t1 = edge_tm1_fwd(A.cm, ov, w);
                     uint64_t m = om;
-                    coins += __popcll(m);
+                    acc.coins += __popcll(m);
                     while (m) {
                         int i = __ffsll(m) - 1;
                         m &= m - 1;
@@ -277,7 +297,7 @@ SKIM_DEV void process_items(const TravArgs &A, bool have, const Item &it) {
                     act = live != 0;
                 }
             }
-            emit_fwd(A, act, w, live);
+            emit_fwd(A, acc, act, w, live);
         } else {
             bool act = false;
             uint32_t u = 0;
@@ -289,7 +309,7 @@ SKIM_DEV void process_items(const TravArgs &A, bool have, const Item &it) {
                 uint64_t t1 = edge_tm1_rev(A.cm, u, ov, otm1);
                 const uint8_t *li = A.lane_inst + static_cast<size_t>(t) * 64;
                 uint64_t m = om;
-                coins += __popcll(m);
+                acc.coins += __popcll(m);
                 while (m) {
                     int j = __ffsll(m) - 1;
                     m &= m - 1;
@@ -308,53 +328,50 @@ SKIM_DEV void process_items(const TravArgs &A, bool have, const Item &it) {
                 }
                 act = live != 0;
             }
-            emit_rev(A, act, u, t, live);
+            emit_rev(A, acc, act, u, t, live);
         }
     }
-    warp_add(&A.ctl->stats[FWD ? kStFwdCoins : kStRevCoins], coins);
 }
 
 template <bool FWD>
 __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs A) {
     const int lane = threadIdx.x & 31;
     DevCtl *C = A.ctl;
+    Acc acc;
     uint64_t t_progress = globaltimer();
-    unsigned long long seen_done = ld_volatile(&C->q_done);
-    for (;;) {
+    unsigned long long seen_done = ld_volatile(&C->q_done.v);
+    bool done = false;
+    while (!done) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&C->q_head, 32ull);
+        if (lane == 0) base = atomicAdd(&C->q_head.v, 32ull);
         base = __shfl_sync(kFull, base, 0);
         const unsigned long long slot = base + lane;
         bool pending = slot < A.qcap;
         bool empty = !pending;  // resolved without an item
+        unsigned backoff = 32;
         for (;;) {
             Item it{0, 0, 0};
             bool have = false;
-            if (pending) {
-                uint64_t m = ld_acquire(&A.q[slot].mask);
-                if (m) {
-                    it.v = *reinterpret_cast<volatile uint32_t *>(&A.q[slot].v);
-                    it.w = *reinterpret_cast<volatile uint32_t *>(&A.q[slot].w);
-                    it.mask = m;
-                    have = true;
-                    pending = false;
-                }
+            if (pending && read_item(A, slot, &it)) {
+                have = true;
+                pending = false;
             }
             const unsigned hb = __ballot_sync(kFull, have);
             if (hb) {
-                process_items<FWD>(A, have, it);
+                process_items<FWD>(A, acc, have, it);
                 __syncwarp();
                 if (lane == 0) {
                     __threadfence();
-                    atomicAdd(&C->q_done, static_cast<unsigned long long>(__popc(hb)));
+                    atomicAdd(&C->q_done.v, static_cast<unsigned long long>(__popc(hb)));
                 }
                 t_progress = globaltimer();
+                backoff = 32;
             } else if (__any_sync(kFull, pending)) {
-                // nothing ready: either items are still being written, or more
-                // may be pushed, or the queue has drained
-                unsigned long long d = ld_volatile(&C->q_done);
+                // nothing ready: items are still being written, more may be
+                // pushed, or the queue has drained
+                unsigned long long d = ld_volatile(&C->q_done.v);
                 __threadfence();
-                unsigned long long tl = ld_volatile(&C->q_tail);
+                unsigned long long tl = ld_volatile(&C->q_tail.v);
                 if (d == tl && pending && slot >= tl) {
                     pending = false;
                     empty = true;
@@ -363,17 +380,21 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs A) {
                     seen_done = d;
                     t_progress = globaltimer();
                 }
-                if (*reinterpret_cast<volatile unsigned *>(&C->err) & kErrTimeout) return;
-                if (globaltimer() - t_progress > A.timeout_ns) {
-                    if (lane == 0) atomicOr(&C->err, kErrTimeout);
-                    return;
+                const bool other_gave_up = *reinterpret_cast<volatile unsigned *>(&C->err) & kErrTimeout;
+                const bool gave_up = globaltimer() - t_progress > A.timeout_ns;
+                if (__any_sync(kFull, gave_up) && lane == 0) atomicOr(&C->err, kErrTimeout);
+                if (__any_sync(kFull, gave_up || other_gave_up)) {
+                    done = true;
+                    break;
                 }
-                __nanosleep(128);
+                __nanosleep(backoff);
+                if (backoff < 2048) backoff <<= 1;
             }
             if (!__any_sync(kFull, pending)) break;
         }
-        if (__any_sync(kFull, empty)) return;
+        if (__any_sync(kFull, empty)) done = true;
     }
+    flush_acc(A, acc, FWD);
 }
 
 }  // namespace
@@ -391,6 +412,7 @@ int traverse_grid(bool forward) {
 }
 
 cudaError_t launch_traverse(const TravArgs &a, bool forward, int grid, cudaStream_t s) {
+    note_launch();
     if (forward)
         k_traverse<true><<<grid, kTravThreads, 0, s>>>(a);
     else
@@ -406,6 +428,7 @@ namespace {
 __global__ void k_rev_sources(TravArgs A, const uint32_t *lane_pair, uint32_t B, uint32_t l, const uint64_t *covered,
                               uint64_t *alive) {
     const int lane = threadIdx.x & 31;
+    Acc acc;
     const uint32_t warps = gridDim.x * (blockDim.x / 32);
     for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w * 32 < B; w += warps) {
         const uint32_t j = w * 32 + lane;
@@ -425,8 +448,9 @@ __global__ void k_rev_sources(TravArgs A, const uint32_t *lane_pair, uint32_t B,
                 atomicOr(reinterpret_cast<unsigned long long *>(&alive[w >> 1]), bits);
             }
         }
-        emit_rev(A, act, u, j >> 6, 1ull << (j & 63));
+        emit_rev(A, acc, act, u, j >> 6, 1ull << (j & 63));
     }
+    flush_acc(A, acc, false);
 }
 
 __global__ void k_respill_rev(TravArgs A, uint64_t R) {
@@ -461,7 +485,9 @@ __global__ void k_respill_fwd(TravArgs A, uint32_t n) {
 
 __global__ void k_fwd_source(TravArgs A, uint32_t x) {
     const uint64_t lmask = A.l == 64 ? ~0ull : ((1ull << A.l) - 1);
-    emit_fwd(A, threadIdx.x == 0, x, lmask);
+    Acc acc;
+    emit_fwd(A, acc, threadIdx.x == 0, x, lmask);
+    flush_acc(A, acc, true);
 }
 
 }  // namespace
@@ -472,6 +498,7 @@ cudaError_t launch_rev_sources(const TravArgs &a, const uint32_t *lane_pair, uin
     unsigned warps = (B + 31) / 32;
     unsigned blocks = (warps + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    note_launch();
     k_rev_sources<<<blocks, 256, 0, s>>>(a, lane_pair, B, l, covered, alive);
     return cudaGetLastError();
 }
@@ -481,6 +508,7 @@ cudaError_t launch_respill_rev(const TravArgs &a, uint64_t R, cudaStream_t s) {
     uint64_t warps = (R + 31) / 32;
     uint64_t blocks = (warps + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    note_launch();
     k_respill_rev<<<static_cast<unsigned>(blocks), 256, 0, s>>>(a, R);
     return cudaGetLastError();
 }
@@ -489,11 +517,13 @@ cudaError_t launch_respill_fwd(const TravArgs &a, uint32_t n, cudaStream_t s) {
     uint64_t warps = (n + 31) / 32;
     uint64_t blocks = (warps + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    note_launch();
     k_respill_fwd<<<static_cast<unsigned>(blocks), 256, 0, s>>>(a, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_source(const TravArgs &a, uint32_t x, cudaStream_t s) {
+    note_launch();
     k_fwd_source<<<1, 32, 0, s>>>(a, x);
     return cudaGetLastError();
 }
