@@ -21,7 +21,8 @@ _ERR = {-1: "SKIM_EINVAL", -2: "SKIM_ENOMEM", -3: "SKIM_ENOTBUILT", -4: "SKIM_ET
         -6: "SKIM_EGRAPH", -7: "SKIM_ERANGE"}
 PROB_UNIFORM, PROB_WC, PROB_TRIVALENCY = 0, 1, 2
 KERNEL_NAMES = ("rev_search", "fwd_search", "accept", "record_sort", "skim_step", "rank_order", "query", "setup")
-STAT_NAMES = ("rev_visits", "rev_coins", "insertions", "fwd_visits", "fwd_coins", "batches", "ranks", "retries")
+STAT_NAMES = ("rev_visits", "rev_coins", "insertions", "fwd_visits", "fwd_coins", "batches", "ranks", "retries",
+              "rev_edges", "fwd_edges")
 
 
 class SkimError(RuntimeError):

@@ -28,10 +28,13 @@ inline unsigned grid_for(size_t n, int threads, unsigned cap = 152 * 32) {
     return static_cast<unsigned>(g ? g : 1);
 }
 
-__global__ void k_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst) {
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < B; j += gridDim.x * blockDim.x)
-        lane_inst[j] = static_cast<uint8_t>(lane_pair[j] % l);
-    // pad the last word so that reads of absent lanes stay in bounds and harmless
+// Instance of every lane and the offset of its coin stream, (i + 1) * G.
+__global__ void k_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, uint64_t *lane_g) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < B; j += gridDim.x * blockDim.x) {
+        const uint32_t i = lane_pair[j] % l;
+        lane_inst[j] = static_cast<uint8_t>(i);
+        lane_g[j] = kGolden * static_cast<uint64_t>(i + 1);
+    }
 }
 
 SKIM_DEV bool run_start(const uint64_t *rec_key, uint64_t r, uint32_t tbits) {
@@ -210,9 +213,10 @@ __global__ void k_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl) {
 
 }  // namespace
 
-cudaError_t launch_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, cudaStream_t s) {
+cudaError_t launch_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, uint64_t *lane_g,
+                             cudaStream_t s) {
     note_launch();
-    k_lane_inst<<<grid_for(B, 256), 256, 0, s>>>(lane_pair, B, l, lane_inst);
+    k_lane_inst<<<grid_for(B, 256), 256, 0, s>>>(lane_pair, B, l, lane_inst, lane_g);
     return cudaGetLastError();
 }
 cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,

@@ -29,6 +29,7 @@ struct skim_ctx {
     // graph
     uint32_t *fptr = nullptr, *fcol = nullptr, *rptr = nullptr, *rcol = nullptr;
     uint64_t *thr_wc = nullptr;
+    uint64_t *rhe = nullptr, *fhe = nullptr;  // per-edge coin-stream states
     // rank order
     uint64_t *srank = nullptr;
     uint32_t *spair = nullptr;
@@ -49,6 +50,7 @@ struct skim_ctx {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     uint8_t *lane_inst = nullptr;
+    uint64_t *lane_g = nullptr;
     uint64_t *alive = nullptr, *lane_cnt = nullptr, *lane_off = nullptr;
     uint32_t *lane_fill = nullptr;
     uint32_t lane_cap = 0;
@@ -228,6 +230,8 @@ TravArgs base_args(skim_ctx *c, bool forward) {
     a.rec_val = c->rval;
     a.rcap = c->rcap;
     a.lane_inst = c->lane_inst;
+    a.lane_g = c->lane_g;
+    a.he = forward ? c->fhe : c->rhe;
     a.full = c->full;
     a.pend = c->pend;
     a.covered = c->covered;
@@ -273,7 +277,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     const uint32_t T = (B + 63) / 64;
     const uint32_t tbits = bitlen(T - 1);
     RC(reset_ctl(c));
-    CK(c, launch_lane_inst(c->spair + p0, B, c->l, c->lane_inst, c->st));
+    CK(c, launch_lane_inst(c->spair + p0, B, c->l, c->lane_inst, c->lane_g, c->st));
     if (!mode_build) CK(c, cudaMemsetAsync(c->alive, 0, T * sizeof(uint64_t), c->st));
     TravArgs a = base_args(c, false);
     a.tbits = tbits;
@@ -317,6 +321,8 @@ int pull_stats(skim_ctx *c) {
     c->hstats[SKIM_STAT_INSERTIONS] = c->hctl->stats[kStInsert];
     c->hstats[SKIM_STAT_FWD_VISITS] = c->hctl->stats[kStFwdVisits];
     c->hstats[SKIM_STAT_FWD_COINS] = c->hctl->stats[kStFwdCoins];
+    c->hstats[SKIM_STAT_REV_EDGES] = c->hctl->stats[kStRevEdges];
+    c->hstats[SKIM_STAT_FWD_EDGES] = c->hctl->stats[kStFwdEdges];
     return SKIM_OK;
 }
 
@@ -327,7 +333,7 @@ int reset_stats(skim_ctx *c) {
 }
 
 uint32_t default_lanes(skim_ctx *c) {
-    uint64_t b = c->batch_cfg ? c->batch_cfg : (1u << 18);
+    uint64_t b = c->batch_cfg ? c->batch_cfg : (1u << 21);
     b = std::min<uint64_t>(b, static_cast<uint64_t>(kMaxWords) * 64);
     b = std::min<uint64_t>(b, c->lane_cap);
     return static_cast<uint32_t>(std::max<uint64_t>(64, b));
@@ -528,6 +534,7 @@ int skim_destroy(skim_ctx *c) {
     if (!c) return SKIM_EINVAL;
     cudaStreamSynchronize(c->st);
     dfree(c->fptr); dfree(c->fcol); dfree(c->rptr); dfree(c->rcol); dfree(c->thr_wc);
+    dfree(c->rhe); dfree(c->fhe);
     dfree(c->srank); dfree(c->spair);
     if (c->rank_ws) cudaFree(c->rank_ws);
     dfree(c->ctl); dfree(c->dflag);
@@ -535,7 +542,7 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->q); dfree(c->hkeys); dfree(c->hvals); dfree(c->pend);
     dfree(c->rkey); dfree(c->rkey2); dfree(c->rval); dfree(c->rval2);
     if (c->ws) cudaFree(c->ws);
-    dfree(c->lane_inst); dfree(c->alive); dfree(c->lane_cnt); dfree(c->lane_off); dfree(c->lane_fill);
+    dfree(c->lane_inst); dfree(c->lane_g); dfree(c->alive); dfree(c->lane_cnt); dfree(c->lane_off); dfree(c->lane_fill);
     dfree(c->lcnt); dfree(c->full); dfree(c->X); dfree(c->xlen);
     dfree(c->covered); dfree(c->seg_start); dfree(c->pend_trav); dfree(c->pend_erase);
     dfree(c->size); dfree(c->seg_len); dfree(c->idx); dfree(c->chosen);
@@ -623,7 +630,7 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         // workspace for scans and sorts
         // visit records per batch: a few per lane; sized generously so that
         // re-running a batch with fewer lanes stays rare
-        const uint64_t lanes_max = std::min<uint64_t>(nl, prm->batch_lanes ? prm->batch_lanes : (1u << 18));
+        const uint64_t lanes_max = std::min<uint64_t>(nl, prm->batch_lanes ? prm->batch_lanes : (1u << 21));
         const uint64_t rcap = std::min<uint64_t>(std::max<uint64_t>(16ull * lanes_max, 1u << 20), 1ull << 26);
         size_t ws = std::max({scan_workspace_bytes(static_cast<size_t>(n) + 1), radix_workspace_bytes(m),
                               radix_workspace_bytes(rcap), scan_workspace_bytes(static_cast<size_t>(kMaxWords) * 64)});
@@ -671,7 +678,11 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         TRYC(cudaMemcpyAsync(&maxdeg, md, sizeof(maxdeg), cudaMemcpyDeviceToHost, c->st));
         TRYC(cudaStreamSynchronize(c->st));
         TRYC(cudaMemsetAsync(c->ctl, 0, sizeof(DevCtl), c->st));
-        if (maxdeg > kMaxDegree) { rc = SKIM_ERANGE; goto fail; }
+        (void)maxdeg;
+        TRY(dalloc(c, &c->rhe, m));
+        TRY(dalloc(c, &c->fhe, m));
+        TRYC(launch_edge_states(c->rptr, c->rcol, n, prm->coin_key, 1, c->rhe, c->st));
+        TRYC(launch_edge_states(c->fptr, c->fcol, n, prm->coin_key, 0, c->fhe, c->st));
         if (prm->prob_model == 1) {
             TRY(dalloc(c, &c->thr_wc, n));
             TRYC(launch_wc_thresholds(c->rptr, n, c->thr_wc, c->st));
@@ -704,6 +715,7 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         TRY(dalloc(c, &c->rval2, c->rcap));
         TRY(dalloc(c, &c->lane_inst, c->lane_cap));
         TRYC(cudaMemsetAsync(c->lane_inst, 0, c->lane_cap, c->st));
+        TRY(dalloc(c, &c->lane_g, c->lane_cap));
         TRY(dalloc(c, &c->alive, c->lane_cap / 64 + 1));
         TRY(dalloc(c, &c->lane_cnt, c->lane_cap));
         TRY(dalloc(c, &c->lane_off, c->lane_cap));

@@ -24,11 +24,13 @@ constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Edges (or index entries) per work item: a node of larger degree is split
-// into several items so that one hub never serialises a warp for long.
+// Work items are cut so that one item costs about kTargetCoins coin
+// evaluations (edges x lanes): a hub never serialises a warp for long.  At
+// most 2^kChunkBits chunks per node; index-erase items hold kChunk entries.
 constexpr uint32_t kChunk = 4096;
 constexpr uint32_t kChunkBits = 12;          // chunk id field width in Item::w
-constexpr uint32_t kMaxDegree = kChunk << kChunkBits;  // 16.7M
+constexpr uint32_t kTargetCoins = 8192;
+constexpr uint32_t kMinChunkEdges = 32;
 constexpr uint32_t kEraseTag = 0x80000000u;
 constexpr uint32_t kNopTag = 0xFFFFFFFEu;      // placeholder item (a spilled reservation)
 constexpr uint32_t kMaxWords = 1u << 19;       // lane words per batch (w field: word << 12 | chunk < 2^31)
@@ -50,6 +52,16 @@ SKIM_HD uint64_t edge_state(uint64_t coin_key, uint32_t u, uint32_t v) {
 }
 SKIM_HD bool coin_live(uint64_t he, uint32_t inst, uint64_t tm1) {
     return fmix(he + kGolden * static_cast<uint64_t>(inst + 1)) <= tm1;
+}
+
+// Edges per work item for a node of degree deg expanded for the lanes of mask.
+SKIM_HD uint32_t chunk_edges(uint32_t deg, uint64_t mask) {
+    const uint32_t pc = static_cast<uint32_t>(__builtin_popcountll(mask));
+    uint32_t want = kTargetCoins / (pc ? pc : 1);
+    if (want < kMinChunkEdges) want = kMinChunkEdges;
+    if (want > kChunk) want = kChunk;
+    const uint32_t floor_c = (deg + (1u << kChunkBits) - 1) >> kChunkBits;  // keeps chunk ids < 2^kChunkBits
+    return want > floor_c ? want : floor_c;
 }
 
 // Work item of the asynchronous traversals (16 bytes).  Reverse searches:
@@ -91,7 +103,7 @@ struct DevCtl {
     unsigned int pad[2];
 };
 
-enum Stat { kStRevVisits = 0, kStRevCoins, kStInsert, kStFwdVisits, kStFwdCoins };
+enum Stat { kStRevVisits = 0, kStRevCoins, kStInsert, kStFwdVisits, kStFwdCoins, kStRevEdges, kStFwdEdges };
 
 SKIM_DEV uint64_t ld_acquire(const uint64_t *p) {
     uint64_t v;

@@ -62,6 +62,18 @@ __global__ void k_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr)
     }
 }
 
+__global__ void k_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_t n, uint64_t coin_key, int reverse,
+                              uint64_t *he) {
+    // one warp per row
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
+        for (uint32_t e = ptr[v] + lane; e < ptr[v + 1]; e += 32) {
+            const uint32_t c = col[e];
+            he[e] = reverse ? edge_state(coin_key, c, v) : edge_state(coin_key, v, c);
+        }
+    }
+}
+
 __global__ void k_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out) {
     unsigned long long best = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
@@ -201,6 +213,13 @@ cudaError_t launch_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr
     k_wc_thresholds<<<grid_for(n, 256), 256, 0, s>>>(rptr, n, thr);
     return cudaGetLastError();
 }
+cudaError_t launch_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_t n, uint64_t coin_key, int reverse,
+                               uint64_t *he, cudaStream_t s) {
+    note_launch();
+    k_edge_states<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(ptr, col, n, coin_key, reverse, he);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out, cudaStream_t s) {
     note_launch();
     k_max_degree<<<grid_for(n, 256), 256, 0, s>>>(ptr, n, out);

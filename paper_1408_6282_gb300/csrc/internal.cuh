@@ -38,6 +38,8 @@ struct TravArgs {
     uint64_t rcap;
     uint32_t tbits;             // record key = (node << tbits) | word
     const uint8_t *lane_inst;   // instance of every lane of the batch
+    const uint64_t *lane_g;     // per lane: (instance + 1) * G, the lane's coin-stream offset
+    const uint64_t *he;         // per CSR edge: state of its coin stream, fmix(coin_key ^ (u << 32 | v))
     const uint64_t *full;       // Algorithm 2 pruning: instances whose local sketch holds k ranks
     int prune;
     uint64_t *pend;             // per table slot: lane bits whose expansion was spilled
@@ -61,6 +63,10 @@ cudaError_t launch_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint6
                                  cudaStream_t s);
 cudaError_t launch_split_rev(const uint64_t *key, uint64_t m, uint32_t *rcol, cudaStream_t s);
 cudaError_t launch_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr, cudaStream_t s);
+// Per-edge coin-stream states of a CSR: he[e] for edge (row node, col[e]);
+// reverse = 1 when rows are heads (edge col[e] -> row).
+cudaError_t launch_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_t n, uint64_t coin_key, int reverse,
+                               uint64_t *he, cudaStream_t s);
 cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out, cudaStream_t s);
 
 // Rank order of all pairs: bucket by the top bits, then sort each bucket.
@@ -79,7 +85,8 @@ cudaError_t launch_respill_fwd(const TravArgs &a, uint32_t n, cudaStream_t s);
 int traverse_grid(bool forward);  // resident blocks for the persistent traversal
 
 // batch.cu
-cudaError_t launch_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, cudaStream_t s);
+cudaError_t launch_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, uint64_t *lane_g,
+                             cudaStream_t s);
 cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                           const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
                           uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,

@@ -71,22 +71,31 @@ SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t
 }
 
 SKIM_DEV uint32_t n_chunks(uint32_t deg) { return (deg + kChunk - 1) / kChunk; }
+SKIM_DEV uint32_t n_chunks(uint32_t deg, uint64_t mask) {
+    const uint32_t ce = chunk_edges(deg, mask);
+    return (deg + ce - 1) / ce;
+}
 
-// Per-lane counters, added to DevCtl once when a warp finishes.
+// Per-lane counters, added to DevCtl once when a warp finishes.  `pushed`
+// records that the lane reserved queue slots since the warp last reported
+// items done.
 struct Acc {
-    unsigned long long visits = 0, coins = 0, cov = 0;
+    unsigned long long visits = 0, coins = 0, cov = 0, edges = 0;
+    bool pushed = false;
 };
 
 SKIM_DEV void flush_acc(const TravArgs &A, const Acc &acc, bool fwd) {
     warp_add(&A.ctl->stats[fwd ? kStFwdVisits : kStRevVisits], acc.visits);
     warp_add(&A.ctl->stats[fwd ? kStFwdCoins : kStRevCoins], acc.coins);
     if (fwd) warp_add(&A.ctl->ix_cov, acc.cov);
+    warp_add(&A.ctl->stats[fwd ? kStFwdEdges : kStRevEdges], acc.edges);
 }
 
 // Reserve `cnt` queue slots per lane (warp-aggregated); returns the lane's
 // first slot.  Slots at or beyond capacity never receive an item: they are
 // counted as done at once, and the caller parks that work in a pending mask.
-SKIM_DEV unsigned long long reserve_slots(const TravArgs &A, uint32_t cnt) {
+SKIM_DEV unsigned long long reserve_slots(const TravArgs &A, Acc &acc, uint32_t cnt) {
+    if (cnt) acc.pushed = true;
     unsigned long long tot;
     unsigned long long ex = warp_excl_scan(cnt, &tot);
     unsigned long long base = 0;
@@ -128,11 +137,11 @@ SKIM_DEV bool spill_if_full(const TravArgs &A, unsigned long long s, uint32_t ni
 
 // Warp-collective: queue the expansion of lane bits `nb` of entry (u, t)
 // (table slot `slot`).
-SKIM_DEV void push_rev(const TravArgs &A, uint32_t u, uint32_t t, uint64_t nb, uint64_t slot) {
+SKIM_DEV void push_rev(const TravArgs &A, Acc &acc, uint32_t u, uint32_t t, uint64_t nb, uint64_t slot) {
     uint32_t ni = 0;
-    if (nb) ni = n_chunks(A.ptr[u + 1] - A.ptr[u]);
+    if (nb) ni = n_chunks(A.ptr[u + 1] - A.ptr[u], nb);
     if (!__any_sync(kFull, ni != 0)) return;
-    unsigned long long s = reserve_slots(A, ni);
+    unsigned long long s = reserve_slots(A, acc, ni);
     if (ni && spill_if_full(A, s, ni)) {
         atomicOr(reinterpret_cast<unsigned long long *>(&A.pend[slot]), nb);
         return;
@@ -142,6 +151,7 @@ SKIM_DEV void push_rev(const TravArgs &A, uint32_t u, uint32_t t, uint64_t nb, u
 
 // Warp-collective: lanes with `act` visit node u with lane bits `bits` in word t.
 SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32_t t, uint64_t bits) {
+    if (!__any_sync(kFull, act && bits)) return;
     uint64_t nb = 0;
     bool first = false;
     uint64_t slot = 0;
@@ -173,20 +183,20 @@ SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32
         }
     }
     acc.visits += __popcll(nb);
-    push_rev(A, u, t, nb, slot);
+    push_rev(A, acc, u, t, nb, slot);
 }
 
 // Warp-collective: queue the expansion of node w in instances `trav` and the
 // erasure of the index entries of pairs (w, i), i in `erase`.
-SKIM_DEV void push_fwd(const TravArgs &A, uint32_t w, uint64_t trav, uint64_t erase) {
+SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, uint64_t erase) {
     uint32_t ni = 0;
-    if (trav) ni = n_chunks(A.ptr[w + 1] - A.ptr[w]);
+    if (trav) ni = n_chunks(A.ptr[w + 1] - A.ptr[w], trav);
     for (uint64_t m = erase; m; m &= m - 1) {
         int i = __ffsll(m) - 1;
         ni += n_chunks(A.seg_len[static_cast<uint64_t>(w) * A.l + i]);
     }
     if (!__any_sync(kFull, ni != 0)) return;
-    unsigned long long s = reserve_slots(A, ni);
+    unsigned long long s = reserve_slots(A, acc, ni);
     if (ni && spill_if_full(A, s, ni)) {
         if (trav) atomicOr(reinterpret_cast<unsigned long long *>(&A.pend_trav[w]), trav);
         if (erase) atomicOr(reinterpret_cast<unsigned long long *>(&A.pend_erase[w]), erase);
@@ -194,7 +204,7 @@ SKIM_DEV void push_fwd(const TravArgs &A, uint32_t w, uint64_t trav, uint64_t er
     }
     uint32_t c = 0;
     if (trav) {
-        uint32_t nc = n_chunks(A.ptr[w + 1] - A.ptr[w]);
+        uint32_t nc = n_chunks(A.ptr[w + 1] - A.ptr[w], trav);
         for (; c < nc; c++) write_item(A, s + c, w, c, trav);
     }
     for (uint64_t m = erase; m; m &= m - 1) {
@@ -212,6 +222,7 @@ SKIM_DEV void push_fwd(const TravArgs &A, uint32_t w, uint64_t trav, uint64_t er
 // Warp-collective: lanes with `act` reach node w in the instances of `live`
 // during a residual search.
 SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64_t live) {
+    if (!__any_sync(kFull, act && live)) return;
     uint64_t nb = 0;
     if (act && live) {
         uint64_t cov = *reinterpret_cast<volatile uint64_t *>(&A.covered[w]);
@@ -228,113 +239,160 @@ SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64
         int i = __ffsll(m) - 1;
         if (A.seg_len[static_cast<uint64_t>(w) * A.l + i]) erase |= 1ull << i;
     }
-    push_fwd(A, w, nb, erase);
+    push_fwd(A, acc, w, nb, erase);
 }
 
 // Process the items held by the lanes with `have`, edges (or index entries)
 // of all items flattened over the warp.
-template <bool FWD>
-SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &it) {
-    const int lane = threadIdx.x & 31;
-    uint32_t begin = 0, cnt = 0;
-    uint64_t tm1 = 0;
-    bool erase = false;
-    if (have) {
-        if (it.w == kNopTag) {
-            cnt = 0;
-        } else if (FWD && (it.w & kEraseTag)) {
-            erase = true;
-            begin = (it.w & ~kEraseTag) * kChunk;
-            cnt = min(kChunk, it.v - begin);
+// Live lanes of an edge whose coin stream has state he: lane j is live iff
+// fmix(he + g[j]) <= t1, g[j] = (instance of j + 1) * G.  Two coins per step
+// so that the two hash chains overlap.
+SKIM_DEV uint64_t live_lanes(uint64_t he, uint64_t m, uint64_t t1, const uint64_t *g) {
+    uint64_t live = 0;
+    while (m) {
+        const int j1 = __ffsll(m) - 1;
+        m &= m - 1;
+        const uint64_t g1 = g[j1];
+        if (m) {
+            const int j2 = __ffsll(m) - 1;
+            m &= m - 1;
+            const uint64_t g2 = g[j2];
+            const uint64_t c1 = fmix(he + g1), c2 = fmix(he + g2);
+            live |= static_cast<uint64_t>(c1 <= t1) << j1;
+            live |= static_cast<uint64_t>(c2 <= t1) << j2;
         } else {
-            uint32_t chunk = it.w & ((1u << kChunkBits) - 1);
-            uint32_t e0 = A.ptr[it.v], e1 = A.ptr[it.v + 1];
-            begin = e0 + chunk * kChunk;
-            cnt = min(kChunk, e1 - begin);
-            if (!FWD) tm1 = A.cm.model == 1 ? A.cm.thr_wc[it.v] : A.cm.tm1_uniform;
+            live |= static_cast<uint64_t>(fmix(he + g1) <= t1) << j1;
         }
     }
-    unsigned long long tot;
-    unsigned long long excl = warp_excl_scan(cnt, &tot);
-    unsigned long long incl = excl + cnt;
-    for (unsigned long long b0 = 0; b0 < tot; b0 += 32) {
-        unsigned long long f = b0 + lane;
-        int lo = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            unsigned long long iv = __shfl_sync(kFull, incl, lo + step - 1);
-            if (iv <= f) lo += step;
-        }
-        const int owner = lo;
-        const uint32_t ov = __shfl_sync(kFull, it.v, owner);
-        const uint32_t ow = __shfl_sync(kFull, it.w, owner);
-        const uint64_t om = __shfl_sync(kFull, it.mask, owner);
-        const uint32_t ob = __shfl_sync(kFull, begin, owner);
-        const unsigned long long oex = __shfl_sync(kFull, excl, owner);
-        const bool oerase = __shfl_sync(kFull, erase, owner);
-        const uint64_t otm1 = __shfl_sync(kFull, tm1, owner);
-        const bool valid = f < tot;
-        const uint32_t idx = ob + static_cast<uint32_t>(f - oex);
-        if (FWD) {
-            bool act = false;
-            uint32_t w = 0;
-            uint64_t live = 0;
-            if (valid) {
-                if (oerase) {
-                    uint32_t node = A.idx_nodes[(om - 1) + idx];
-                    atomicSub(&A.size[node], 1u);
-                } else {
-                    w = A.col[idx];
-                    uint64_t he = edge_state(A.cm.coin_key, ov, w);
-                    uint64_t t1 = edge_tm1_fwd(A.cm, ov, w);
-                    uint64_t m = om;
-                    acc.coins += __popcll(m);
-                    while (m) {
-                        int i = __ffsll(m) - 1;
-                        m &= m - 1;
-                        if (coin_live(he, static_cast<uint32_t>(i), t1)) live |= 1ull << i;
-                    }
-                    act = live != 0;
-                }
-            }
-            emit_fwd(A, acc, act, w, live);
-        } else {
-            bool act = false;
-            uint32_t u = 0;
-            uint64_t live = 0;
-            const uint32_t t = ow >> kChunkBits;
-            if (valid) {
-                u = A.col[idx];
-                uint64_t he = edge_state(A.cm.coin_key, u, ov);
-                uint64_t t1 = edge_tm1_rev(A.cm, u, ov, otm1);
-                const uint8_t *li = A.lane_inst + static_cast<size_t>(t) * 64;
-                uint64_t m = om;
-                acc.coins += __popcll(m);
-                while (m) {
-                    int j = __ffsll(m) - 1;
-                    m &= m - 1;
-                    if (coin_live(he, li[j], t1)) live |= 1ull << j;
-                }
-                if (live && A.prune) {
-                    uint64_t fu = A.full[u];
-                    if (fu) {
-                        uint64_t mm = live;
-                        while (mm) {
-                            int j = __ffsll(mm) - 1;
-                            mm &= mm - 1;
-                            if ((fu >> li[j]) & 1ull) live &= ~(1ull << j);
-                        }
-                    }
-                }
+    return live;
+}
+
+// What one lane needs to expand its item.
+struct Desc {
+    uint32_t v, w, begin, cnt;
+    uint64_t mask, tm1, g1;  // g1: stream offset when the item has a single lane
+    bool erase, single;
+};
+
+SKIM_DEV Desc describe(const TravArgs &A, bool have, const Item &it) {
+    Desc d{};
+    if (!have || it.w == kNopTag) return d;
+    d.v = it.v;
+    d.w = it.w;
+    d.mask = it.mask;
+    if (it.w & kEraseTag) {  // only residual searches create erase items
+        d.erase = true;
+        d.begin = (it.w & ~kEraseTag) * kChunk;
+        d.cnt = min(kChunk, it.v - d.begin);
+        return d;
+    }
+    const uint32_t chunk = it.w & ((1u << kChunkBits) - 1);
+    const uint32_t e0 = A.ptr[it.v], e1 = A.ptr[it.v + 1];
+    const uint32_t ce = chunk_edges(e1 - e0, it.mask);
+    d.begin = e0 + chunk * ce;
+    d.cnt = min(ce, e1 - d.begin);
+    return d;
+}
+
+SKIM_DEV Desc shfl_desc(const Desc &d, int src) {
+    Desc o;
+    o.v = __shfl_sync(kFull, d.v, src);
+    o.w = __shfl_sync(kFull, d.w, src);
+    o.begin = __shfl_sync(kFull, d.begin, src);
+    o.cnt = __shfl_sync(kFull, d.cnt, src);
+    o.mask = __shfl_sync(kFull, d.mask, src);
+    o.tm1 = __shfl_sync(kFull, d.tm1, src);
+    o.g1 = __shfl_sync(kFull, d.g1, src);
+    o.erase = __shfl_sync(kFull, d.erase, src);
+    o.single = __shfl_sync(kFull, d.single, src);
+    return o;
+}
+
+// Expand edge (or index entry) number idx of item d; warp-collective (every
+// lane calls it, `valid` marks lanes with work).
+template <bool FWD>
+SKIM_DEV void expand_one(const TravArgs &A, Acc &acc, bool valid, const Desc &d, uint32_t idx,
+                         const uint64_t *ginst) {
+    if (FWD) {
+        bool act = false;
+        uint32_t w = 0;
+        uint64_t live = 0;
+        if (valid) {
+            if (d.erase) {
+                atomicSub(&A.size[A.idx_nodes[(d.mask - 1) + idx]], 1u);
+            } else {
+                w = A.col[idx];
+                const uint64_t he = A.he[idx];
+                acc.edges++;
+                acc.coins += __popcll(d.mask);
+                live = live_lanes(he, d.mask, edge_tm1_fwd(A.cm, d.v, w), ginst);
                 act = live != 0;
             }
-            emit_rev(A, acc, act, u, t, live);
         }
+        emit_fwd(A, acc, act, w, live);
+    } else {
+        bool act = false;
+        uint32_t u = 0;
+        uint64_t live = 0;
+        const uint32_t t = d.w >> kChunkBits;
+        if (valid) {
+            u = A.col[idx];
+            const uint64_t he = A.he[idx];
+            const uint64_t t1 = edge_tm1_rev(A.cm, u, d.v, d.tm1);
+            acc.edges++;
+            acc.coins += __popcll(d.mask);
+            if (d.single)
+                live = fmix(he + d.g1) <= t1 ? d.mask : 0;
+            else
+                live = live_lanes(he, d.mask, t1, A.lane_g + static_cast<size_t>(t) * 64);
+            if (live && A.prune) {  // Algorithm 2: u's local sketch of the lane's instance is full
+                const uint64_t fu = A.full[u];
+                if (fu) {
+                    const uint8_t *li = A.lane_inst + static_cast<size_t>(t) * 64;
+                    for (uint64_t m = live; m; m &= m - 1) {
+                        const int j = __ffsll(m) - 1;
+                        if ((fu >> li[j]) & 1ull) live &= ~(1ull << j);
+                    }
+                }
+            }
+            act = live != 0;
+        }
+        emit_rev(A, acc, act, u, t, live);
     }
+}
+
+// Expand the items held by the lanes with `have`: an item of 32 or more
+// edges is swept by the whole warp (lane = edge), smaller items by their own
+// lane, one edge per step.
+template <bool FWD>
+SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &it, const uint64_t *ginst) {
+    const int lane = threadIdx.x & 31;
+    Desc d = describe(A, have, it);
+    if (!FWD && d.cnt) {
+        d.tm1 = A.cm.model == 1 ? A.cm.thr_wc[d.v] : A.cm.tm1_uniform;
+        d.single = (d.mask & (d.mask - 1)) == 0;
+        if (d.single) d.g1 = A.lane_g[static_cast<size_t>(d.w >> kChunkBits) * 64 + (__ffsll(d.mask) - 1)];
+    }
+    unsigned big = __ballot_sync(kFull, d.cnt >= 32);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const Desc b = shfl_desc(d, src);
+        for (uint32_t e0 = 0; e0 < b.cnt; e0 += 32)
+            expand_one<FWD>(A, acc, e0 + lane < b.cnt, b, b.begin + e0 + lane, ginst);
+    }
+    const uint32_t mine = d.cnt < 32 ? d.cnt : 0;
+    uint32_t steps = mine;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) steps = max(steps, __shfl_xor_sync(kFull, steps, o));
+    for (uint32_t k = 0; k < steps; k++) expand_one<FWD>(A, acc, k < mine, d, d.begin + k, ginst);
 }
 
 template <bool FWD>
 __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs A) {
+    __shared__ uint64_t ginst[64];  // (i + 1) * G for instance i (residual searches)
+    if (threadIdx.x < 64) ginst[threadIdx.x] = kGolden * static_cast<uint64_t>(threadIdx.x + 1);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     DevCtl *C = A.ctl;
     Acc acc;
@@ -348,7 +406,7 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs A) {
         const unsigned long long slot = base + lane;
         bool pending = slot < A.qcap;
         bool empty = !pending;  // resolved without an item
-        unsigned backoff = 32;
+        unsigned backoff = 32, polls = 0;
         for (;;) {
             Item it{0, 0, 0};
             bool have = false;
@@ -358,29 +416,37 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs A) {
             }
             const unsigned hb = __ballot_sync(kFull, have);
             if (hb) {
-                process_items<FWD>(A, acc, have, it);
-                __syncwarp();
+                process_items<FWD>(A, acc, have, it, ginst);
+                // slots reserved while processing must be visible before the
+                // items count as done (the drain test reads done, then tail)
+                const bool fence = __any_sync(kFull, acc.pushed);
+                acc.pushed = false;
                 if (lane == 0) {
-                    __threadfence();
+                    if (fence) __threadfence();
                     atomicAdd(&C->q_done.v, static_cast<unsigned long long>(__popc(hb)));
                 }
                 t_progress = globaltimer();
                 backoff = 32;
+                polls = 0;
             } else if (__any_sync(kFull, pending)) {
                 // nothing ready: items are still being written, more may be
-                // pushed, or the queue has drained
-                unsigned long long d = ld_volatile(&C->q_done.v);
-                __threadfence();
-                unsigned long long tl = ld_volatile(&C->q_tail.v);
-                if (d == tl && pending && slot >= tl) {
-                    pending = false;
-                    empty = true;
+                // pushed, or the queue has drained.  The shared cursors are
+                // read only every 8th poll of the warp's own slots.
+                if ((++polls & 7) == 0) {
+                    unsigned long long d = ld_volatile(&C->q_done.v);
+                    __threadfence();
+                    unsigned long long tl = ld_volatile(&C->q_tail.v);
+                    if (d == tl && pending && slot >= tl) {
+                        pending = false;
+                        empty = true;
+                    }
+                    if (d != seen_done) {
+                        seen_done = d;
+                        t_progress = globaltimer();
+                    }
                 }
-                if (d != seen_done) {
-                    seen_done = d;
-                    t_progress = globaltimer();
-                }
-                const bool other_gave_up = *reinterpret_cast<volatile unsigned *>(&C->err) & kErrTimeout;
+                const bool other_gave_up =
+                    (polls & 7) == 0 && (*reinterpret_cast<volatile unsigned *>(&C->err) & kErrTimeout);
                 const bool gave_up = globaltimer() - t_progress > A.timeout_ns;
                 if (__any_sync(kFull, gave_up) && lane == 0) atomicOr(&C->err, kErrTimeout);
                 if (__any_sync(kFull, gave_up || other_gave_up)) {
@@ -388,7 +454,7 @@ __global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs A) {
                     break;
                 }
                 __nanosleep(backoff);
-                if (backoff < 2048) backoff <<= 1;
+                if (backoff < 512) backoff <<= 1;
             }
             if (!__any_sync(kFull, pending)) break;
         }
@@ -465,7 +531,8 @@ __global__ void k_respill_rev(TravArgs A, uint64_t R) {
             key = A.rec_key[r];
             p = atomicExch(reinterpret_cast<unsigned long long *>(&A.pend[slot]), 0ull);
         }
-        push_rev(A, static_cast<uint32_t>(key >> A.tbits), static_cast<uint32_t>(key & tmask), p, slot);
+        Acc acc;
+        push_rev(A, acc, static_cast<uint32_t>(key >> A.tbits), static_cast<uint32_t>(key & tmask), p, slot);
     }
 }
 
@@ -479,7 +546,8 @@ __global__ void k_respill_fwd(TravArgs A, uint32_t n) {
             pt = atomicExch(reinterpret_cast<unsigned long long *>(&A.pend_trav[v]), 0ull);
             pe = atomicExch(reinterpret_cast<unsigned long long *>(&A.pend_erase[v]), 0ull);
         }
-        push_fwd(A, v < n ? v : 0, pt, pe);
+        Acc acc;
+        push_fwd(A, acc, v < n ? v : 0, pt, pe);
     }
 }
 
