@@ -177,6 +177,32 @@ int skim_set_timing(skim_ctx *ctx, int on);
 int skim_kernel_launches(uint64_t *out);
 int skim_kernel_times(skim_ctx *ctx, double *ms_out, uint64_t *launches_out, uint32_t count, int reset);
 
+/* Allocation-free influence query, for callers that cannot allocate device
+ * memory (code that runs inside another framework's memory pool or under a
+ * fixed memory budget, where a cudaMalloc is not allowed).  The paper has no
+ * counterpart: it computes the same estimate as skim_oracle_query (Eq.
+ * unionest, summed exactly and rounded once), but its scratch hash table is a
+ * fixed 4 MiB array of static device memory that every GPU loading the
+ * library holds until the process exits.  Nothing is allocated and nothing
+ * is synchronised: the call is asynchronous on `stream` (a cudaStream_t, or
+ * NULL).
+ *   x_dev, len_dev  sketches in device memory, as skim_get_sketches lays them
+ *                   out (n*k ranks row-major, n lengths), e.g. from
+ *                   skim_sketch_pointers();
+ *   seeds_dev       n_seeds node ids in device memory (duplicates allowed);
+ *   est_dev         one double in device memory; receives the estimate, or a
+ *                   quiet NaN if a seed id is >= n.
+ * Limit: 2*n_seeds*(k-1)+2 <= 2^18 (n_seeds <= 2080 for k = 64); larger
+ * queries return SKIM_ERANGE.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls on a device
+ * share the array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Errors: SKIM_EINVAL (null pointer, k or l out of range), SKIM_ERANGE,
+ * SKIM_ECUDA. */
+int skim_union_estimate_static(const uint64_t *x_dev, const uint32_t *len_dev, uint32_t n, uint32_t k, uint32_t l,
+                               const uint32_t *seeds_dev, uint32_t n_seeds, double *est_dev, void *stream);
+
 int skim_destroy(skim_ctx *ctx);
 
 const char *skim_strerror(int code);

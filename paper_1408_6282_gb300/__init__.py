@@ -69,6 +69,7 @@ def load():
     lib.skim_set_timing.argtypes = [vp, C.c_int]
     lib.skim_kernel_times.argtypes = [vp, vp, vp, u32, C.c_int]
     lib.skim_kernel_launches.argtypes = [vp]
+    lib.skim_union_estimate_static.argtypes = [vp, vp, u32, u32, u32, vp, u32, vp, vp]
     lib.skim_strerror.argtypes = [C.c_int]
     lib.skim_strerror.restype = C.c_char_p
     _lib = lib
@@ -148,6 +149,13 @@ def skim_kernel_launches() -> int:
     out = np.zeros(1, np.uint64)
     _check(load().skim_kernel_launches(_ptr(out)), "skim_kernel_launches")
     return int(out[0])
+
+
+def skim_union_estimate_static(x_dev: int, len_dev: int, n: int, k: int, l: int, seeds_dev: int, n_seeds: int,
+                               est_dev: int, stream: int = 0):
+    """Allocation-free query (static scratch); all pointers are device addresses."""
+    _check(load().skim_union_estimate_static(x_dev, len_dev, n, k, l, seeds_dev or None, n_seeds, est_dev,
+                                             stream or None), "skim_union_estimate_static")
 
 
 def skim_destroy(ctx: int):

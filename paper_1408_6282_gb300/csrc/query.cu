@@ -179,3 +179,133 @@ cudaError_t launch_query(const uint64_t *X, const uint32_t *xlen, uint32_t n, ui
 }
 
 }  // namespace skim
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code running inside another
+// framework's memory pool, inside a region where allocation would break a
+// memory budget, or in processes whose allocator is owned by someone else.
+// This entry point keeps the query's scratch hash table in a fixed array of
+// static device memory instead (every GPU that loads the library holds it
+// until the process exits).  The caller still passes the sketches, the seed
+// list and the output.  All calls on a device share the one array, so calls
+// whose work overlaps on the GPU race with each other; the kernel clears the
+// part of the table it uses before every query.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#include "skim.h"
+
+namespace skim {
+namespace {
+
+constexpr uint64_t kStaticSlots = 1ull << 18;  // hash slots: 2^18 keys + 2^18 values = 4 MiB
+static __device__ __align__(256) uint64_t g_static_table[2 * kStaticSlots];
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+uint64_t *g_static_ptr[kMaxDevices] = {};  // device address of g_static_table, per device
+
+__global__ void __launch_bounds__(kQThreads) k_query_static(const uint64_t *X, const uint32_t *xlen, uint32_t n,
+                                                            uint32_t k, uint32_t l, const uint32_t *seeds,
+                                                            uint32_t s, uint64_t *table, uint64_t H, double *out) {
+    __shared__ unsigned long long top_tau;
+    __shared__ int top_used, bad;
+    __shared__ U192 wsum[kQThreads / 32];
+    uint64_t *tk = table;
+    uint64_t *tv = table + H;
+    if (threadIdx.x == 0) {
+        top_tau = 0;
+        top_used = 0;
+        bad = 0;
+    }
+    for (uint64_t i = threadIdx.x; i < H; i += blockDim.x) {
+        tk[i] = kEmptyKey;
+        tv[i] = 0;
+    }
+    __syncthreads();
+    const uint64_t hmask = H - 1;
+    const uint64_t work = static_cast<uint64_t>(s) * k;
+    for (uint64_t e = threadIdx.x; e < work; e += blockDim.x) {
+        const uint32_t u = seeds[e / k];
+        const uint32_t pos = static_cast<uint32_t>(e % k);
+        if (u >= n) {
+            bad = 1;
+            continue;
+        }
+        const uint32_t ln = xlen[u];
+        const uint32_t body = ln == k ? k - 1 : ln;
+        if (pos >= body) continue;
+        const uint64_t z = X[static_cast<uint64_t>(u) * k + pos];
+        const uint64_t tau = ln == k ? X[static_cast<uint64_t>(u) * k + k - 1] : ~0ull;
+        if (z == kEmptyKey) {
+            atomicMax(&top_tau, static_cast<unsigned long long>(tau));
+            top_used = 1;
+            continue;
+        }
+        uint64_t h = fmix(z) & hmask;
+        for (uint64_t p = 0; p < H; p++) {
+            unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long *>(&tk[h]),
+                                                static_cast<unsigned long long>(kEmptyKey),
+                                                static_cast<unsigned long long>(z));
+            if (prev == kEmptyKey || prev == z) {
+                atomicMax(reinterpret_cast<unsigned long long *>(&tv[h]), static_cast<unsigned long long>(tau));
+                break;
+            }
+            h = (h + 1) & hmask;
+        }
+    }
+    __syncthreads();
+    U192 acc{{0, 0, 0}};
+    for (uint64_t i = threadIdx.x; i < H; i += blockDim.x)
+        if (tk[i] != kEmptyKey) add192(acc, to_fixed(inv_tau(tv[i])));
+    if (threadIdx.x == 0 && top_used) add192(acc, to_fixed(inv_tau(top_tau)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        U192 other;
+        for (int w = 0; w < 3; w++) other.w[w] = __shfl_down_sync(kFull, acc.w[w], o);
+        add192(acc, other);
+    }
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        U192 tot{{0, 0, 0}};
+        for (int w = 0; w < kQThreads / 32; w++) add192(tot, wsum[w]);
+        out[0] = bad ? __longlong_as_double(0x7ff8000000000000ll) : fixed_to_double(tot) / static_cast<double>(l);
+    }
+}
+
+}  // namespace
+}  // namespace skim
+
+extern "C" int skim_union_estimate_static(const uint64_t *x_dev, const uint32_t *len_dev, uint32_t n, uint32_t k,
+                                          uint32_t l, const uint32_t *seeds_dev, uint32_t n_seeds, double *est_dev,
+                                          void *stream) {
+    using namespace skim;
+    if (!x_dev || !len_dev || !est_dev || (n_seeds && !seeds_dev)) return SKIM_EINVAL;
+    if (n == 0 || k < 2 || k > 255 || l == 0 || l > 64) return SKIM_EINVAL;
+    uint64_t H = 64;
+    const uint64_t need = 2ull * n_seeds * (k - 1) + 2;
+    while (H < need) H <<= 1;
+    if (H > kStaticSlots) return SKIM_ERANGE;  // the static table holds 2^18 slots
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SKIM_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return SKIM_ERANGE;
+    uint64_t *table = nullptr;
+    {
+        // once per device, with that device current: the device address of
+        // the static array (its name in host code is only a stand-in)
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_static_table) != cudaSuccess || !p) return SKIM_ECUDA;
+            g_static_ptr[dev] = static_cast<uint64_t *>(p);
+        }
+        table = g_static_ptr[dev];
+    }
+    note_launch();
+    k_query_static<<<1, kQThreads, 0, static_cast<cudaStream_t>(stream)>>>(x_dev, len_dev, n, k, l, seeds_dev,
+                                                                           n_seeds, table, H, est_dev);
+    return cudaGetLastError() == cudaSuccess ? SKIM_OK : SKIM_ECUDA;
+}
