@@ -308,88 +308,112 @@ SKIM_DEV Desc shfl_desc(const Desc &d, int src) {
     return o;
 }
 
-// Expand edge (or index entry) number idx of item d; warp-collective (every
-// lane calls it, `valid` marks lanes with work).
+#ifndef SKIM_UNROLL
+#define SKIM_UNROLL 1
+#endif
+#ifndef SKIM_TRAV_MIN_BLOCKS
+#define SKIM_TRAV_MIN_BLOCKS 4
+#endif
+constexpr int kUnroll = SKIM_UNROLL;  // edges per lane per step: independent hash chains
+
+// Coin test of CSR edge idx for item d: the lanes (reverse) or instances
+// (forward) for which the edge is live; *tgt = the edge's other end.
 template <bool FWD>
-SKIM_DEV void expand_one(const TravArgs &A, Acc &acc, bool valid, const Desc &d, uint32_t idx,
-                         const uint64_t *ginst) {
-    if (FWD) {
-        bool act = false;
-        uint32_t w = 0;
-        uint64_t live = 0;
-        if (valid) {
-            if (d.erase) {
-                atomicSub(&A.size[A.idx_nodes[(d.mask - 1) + idx]], 1u);
-            } else {
-                w = A.col[idx];
-                const uint64_t he = A.he[idx];
-                acc.edges++;
-                acc.coins += __popcll(d.mask);
-                live = live_lanes(he, d.mask, edge_tm1_fwd(A.cm, d.v, w), ginst);
-                act = live != 0;
-            }
+SKIM_DEV uint64_t edge_live(const TravArgs &A, const Desc &d, uint32_t idx, uint32_t *tgt, const uint64_t *ginst) {
+    const uint32_t x = A.col[idx];
+    const uint64_t he = A.he[idx];
+    *tgt = x;
+    if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A.cm, d.v, x), ginst);
+    const uint64_t t1 = edge_tm1_rev(A.cm, x, d.v, d.tm1);
+    if (d.single) return fmix(he + d.g1) <= t1 ? d.mask : 0;
+    return live_lanes(he, d.mask, t1, A.lane_g + static_cast<size_t>(d.w >> kChunkBits) * 64);
+}
+
+// Algorithm 2: drop lanes whose instance-local sketch at u already holds k ranks.
+SKIM_DEV uint64_t prune_full(const TravArgs &A, const Desc &d, uint32_t u, uint64_t live) {
+    const uint64_t fu = A.full[u];
+    if (!fu) return live;
+    const uint8_t *li = A.lane_inst + static_cast<size_t>(d.w >> kChunkBits) * 64;
+    for (uint64_t m = live; m; m &= m - 1) {
+        const int j = __ffsll(m) - 1;
+        if ((fu >> li[j]) & 1ull) live &= ~(1ull << j);
+    }
+    return live;
+}
+
+// Hand the live results of one step to the emitters (warp-collective).
+template <bool FWD>
+SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, const Desc &d, const uint64_t *lv, const uint32_t *tg) {
+#pragma unroll
+    for (int q = 0; q < kUnroll; q++) {
+        uint64_t live = lv[q];
+        if (FWD) {
+            emit_fwd(A, acc, live != 0, tg[q], live);
+        } else {
+            if (live && A.prune) live = prune_full(A, d, tg[q], live);
+            emit_rev(A, acc, live != 0, tg[q], d.w >> kChunkBits, live);
         }
-        emit_fwd(A, acc, act, w, live);
-    } else {
-        bool act = false;
-        uint32_t u = 0;
-        uint64_t live = 0;
-        const uint32_t t = d.w >> kChunkBits;
-        if (valid) {
-            u = A.col[idx];
-            const uint64_t he = A.he[idx];
-            const uint64_t t1 = edge_tm1_rev(A.cm, u, d.v, d.tm1);
-            acc.edges++;
-            acc.coins += __popcll(d.mask);
-            if (d.single)
-                live = fmix(he + d.g1) <= t1 ? d.mask : 0;
-            else
-                live = live_lanes(he, d.mask, t1, A.lane_g + static_cast<size_t>(t) * 64);
-            if (live && A.prune) {  // Algorithm 2: u's local sketch of the lane's instance is full
-                const uint64_t fu = A.full[u];
-                if (fu) {
-                    const uint8_t *li = A.lane_inst + static_cast<size_t>(t) * 64;
-                    for (uint64_t m = live; m; m &= m - 1) {
-                        const int j = __ffsll(m) - 1;
-                        if ((fu >> li[j]) & 1ull) live &= ~(1ull << j);
-                    }
-                }
-            }
-            act = live != 0;
-        }
-        emit_rev(A, acc, act, u, t, live);
     }
 }
 
+// Expand entries [k0, k0 + kUnroll*stride) of item d, entry k at index
+// begin + k for k < cnt (stride = 32 when the warp shares the item, 1 when
+// the lane owns it).  Warp-collective.
+template <bool FWD>
+SKIM_DEV void expand_step(const TravArgs &A, Acc &acc, const Desc &d, uint32_t k0, uint32_t stride, bool own,
+                          const uint64_t *ginst) {
+    uint64_t lv[kUnroll];
+    uint32_t tg[kUnroll];
+#pragma unroll
+    for (int q = 0; q < kUnroll; q++) {
+        const uint32_t k = k0 + q * stride;
+        lv[q] = 0;
+        tg[q] = 0;
+        if (own && k < d.cnt) {
+            if (FWD && d.erase)
+                atomicSub(&A.size[A.idx_nodes[(d.mask - 1) + d.begin + k]], 1u);
+            else
+                lv[q] = edge_live<FWD>(A, d, d.begin + k, &tg[q], ginst);
+        }
+    }
+    uint64_t anyl = 0;
+#pragma unroll
+    for (int q = 0; q < kUnroll; q++) anyl |= lv[q];
+    if (__any_sync(kFull, anyl != 0)) emit_step<FWD>(A, acc, d, lv, tg);
+}
+
 // Expand the items held by the lanes with `have`: an item of 32 or more
-// edges is swept by the whole warp (lane = edge), smaller items by their own
-// lane, one edge per step.
+// entries is swept by the whole warp (lane = entry), smaller items by their
+// own lane.
 template <bool FWD>
 SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &it, const uint64_t *ginst) {
     const int lane = threadIdx.x & 31;
     Desc d = describe(A, have, it);
-    if (!FWD && d.cnt) {
-        d.tm1 = A.cm.model == 1 ? A.cm.thr_wc[d.v] : A.cm.tm1_uniform;
-        d.single = (d.mask & (d.mask - 1)) == 0;
-        if (d.single) d.g1 = A.lane_g[static_cast<size_t>(d.w >> kChunkBits) * 64 + (__ffsll(d.mask) - 1)];
+    if (d.cnt && !d.erase) {
+        acc.edges += d.cnt;
+        acc.coins += static_cast<unsigned long long>(d.cnt) * __popcll(d.mask);
+        if (!FWD) {
+            d.tm1 = A.cm.model == 1 ? A.cm.thr_wc[d.v] : A.cm.tm1_uniform;
+            d.single = (d.mask & (d.mask - 1)) == 0;
+            if (d.single) d.g1 = A.lane_g[static_cast<size_t>(d.w >> kChunkBits) * 64 + (__ffsll(d.mask) - 1)];
+        }
     }
     unsigned big = __ballot_sync(kFull, d.cnt >= 32);
     while (big) {
         const int src = __ffs(big) - 1;
         big &= big - 1;
         const Desc b = shfl_desc(d, src);
-        for (uint32_t e0 = 0; e0 < b.cnt; e0 += 32)
-            expand_one<FWD>(A, acc, e0 + lane < b.cnt, b, b.begin + e0 + lane, ginst);
+        for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD>(A, acc, b, k0 + lane, 32, true, ginst);
     }
     const uint32_t mine = d.cnt < 32 ? d.cnt : 0;
-    uint32_t steps = mine;
+    uint32_t steps = (mine + kUnroll - 1) / kUnroll;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) steps = max(steps, __shfl_xor_sync(kFull, steps, o));
-    for (uint32_t k = 0; k < steps; k++) expand_one<FWD>(A, acc, k < mine, d, d.begin + k, ginst);
+    for (uint32_t st = 0; st < steps; st++) expand_step<FWD>(A, acc, d, st * kUnroll, 1, mine != 0, ginst);
 }
 
 template <bool FWD>
-__global__ void __launch_bounds__(kTravThreads) k_traverse(TravArgs A) {
+__global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse(TravArgs A) {
     __shared__ uint64_t ginst[64];  // (i + 1) * G for instance i (residual searches)
     if (threadIdx.x < 64) ginst[threadIdx.x] = kGolden * static_cast<uint64_t>(threadIdx.x + 1);
     __syncthreads();
@@ -469,10 +493,11 @@ int traverse_grid(bool forward) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (forward)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_traverse<true>, kTravThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_traverse<false>, kTravThreads, 0);
+    // A residual search starts from one seed and stays narrow: one block per
+    // SM keeps the idle warps (which poll) few.  Reverse searches of a batch
+    // fill the machine: as many blocks as fit.
+    if (forward) return sms;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_traverse<false>, kTravThreads, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
