@@ -318,10 +318,37 @@ constexpr int kUnroll = SKIM_UNROLL;  // edges per lane per step: independent ha
 
 // Coin test of CSR edge idx for item d: the lanes (reverse) or instances
 // (forward) for which the edge is live; *tgt = the edge's other end.
+#ifndef SKIM_HE_TABLE
+#define SKIM_HE_TABLE 1
+#endif
+#ifndef SKIM_PREFETCH
+#define SKIM_PREFETCH 1
+#endif
+
+// Coin-stream state of CSR edge idx whose other end is x.
+template <bool FWD>
+SKIM_DEV uint64_t edge_key(const TravArgs &A, const Desc &d, uint32_t idx, uint32_t x) {
+#if SKIM_HE_TABLE
+    return A.he[idx];
+#else
+    return FWD ? edge_state(A.cm.coin_key, d.v, x) : edge_state(A.cm.coin_key, x, d.v);
+#endif
+}
+
+// Live lanes (reverse) or instances (forward) of an edge with other end x
+// and coin-stream state he.
+template <bool FWD>
+SKIM_DEV uint64_t edge_live_xh(const TravArgs &A, const Desc &d, uint32_t x, uint64_t he, const uint64_t *ginst) {
+    if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A.cm, d.v, x), ginst);
+    const uint64_t t1 = edge_tm1_rev(A.cm, x, d.v, d.tm1);
+    if (d.single) return fmix(he + d.g1) <= t1 ? d.mask : 0;
+    return live_lanes(he, d.mask, t1, A.lane_g + static_cast<size_t>(d.w >> kChunkBits) * 64);
+}
+
 template <bool FWD>
 SKIM_DEV uint64_t edge_live(const TravArgs &A, const Desc &d, uint32_t idx, uint32_t *tgt, const uint64_t *ginst) {
     const uint32_t x = A.col[idx];
-    const uint64_t he = A.he[idx];
+    const uint64_t he = edge_key<FWD>(A, d, idx, x);
     *tgt = x;
     if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A.cm, d.v, x), ginst);
     const uint64_t t1 = edge_tm1_rev(A.cm, x, d.v, d.tm1);
@@ -403,6 +430,38 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
         const int src = __ffs(big) - 1;
         big &= big - 1;
         const Desc b = shfl_desc(d, src);
+#if SKIM_PREFETCH
+        if (!(FWD && b.erase)) {
+            // one step ahead: the next edge's column and key are in flight
+            // while the current coin is computed
+            uint32_t x = 0;
+            uint64_t h = 0;
+            if (lane < b.cnt) {
+                x = A.col[b.begin + lane];
+                h = edge_key<FWD>(A, b, b.begin + lane, x);
+            }
+            for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                uint32_t xn = 0;
+                uint64_t hn = 0;
+                if (k + 32 < b.cnt) {
+                    xn = A.col[b.begin + k + 32];
+                    hn = edge_key<FWD>(A, b, b.begin + k + 32, xn);
+                }
+                uint64_t lv[kUnroll] = {0};
+                uint32_t tg[kUnroll] = {0};
+                if (k < b.cnt) {
+                    lv[0] = edge_live_xh<FWD>(A, b, x, h, ginst);
+                    tg[0] = x;
+                }
+                if (__any_sync(kFull, lv[0] != 0)) emit_step<FWD>(A, acc, b, lv, tg);
+                x = xn;
+                h = hn;
+            }
+            continue;
+        }
+#endif
+        // index-erase items (and the variant without prefetch)
         for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD>(A, acc, b, k0 + lane, 32, true, ginst);
     }
     const uint32_t mine = d.cnt < 32 ? d.cnt : 0;
