@@ -431,7 +431,9 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
         big &= big - 1;
         const Desc b = shfl_desc(d, src);
 #if SKIM_PREFETCH
-        if (!(FWD && b.erase)) {
+        if (FWD && b.erase) {  // index-erase items
+            for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD>(A, acc, b, k0 + lane, 32, true, ginst);
+        } else {
             // one step ahead: the next edge's column and key are in flight
             // while the current coin is computed
             uint32_t x = 0;
@@ -458,11 +460,10 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
                 x = xn;
                 h = hn;
             }
-            continue;
         }
-#endif
-        // index-erase items (and the variant without prefetch)
+#else
         for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD>(A, acc, b, k0 + lane, 32, true, ginst);
+#endif
     }
     const uint32_t mine = d.cnt < 32 ? d.cnt : 0;
     uint32_t steps = (mine + kUnroll - 1) / kUnroll;
