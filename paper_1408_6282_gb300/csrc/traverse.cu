@@ -484,10 +484,15 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
     unsigned long long seen_done = ld_volatile(&C->q_done.v);
     bool done = false;
     while (!done) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&C->q_head.v, 32ull);
-        base = __shfl_sync(kFull, base, 0);
-        const unsigned long long slot = base + lane;
+        // Claims are interleaved across warps: claim c of a grid with W warps
+        // takes, for lane l, queue slot (c / W) * 32W + l * W + (c mod W), so
+        // consecutive items go to different warps.  (With contiguous claims
+        // a narrow search - one seed - would run on a single warp.)
+        unsigned long long claim = 0;
+        if (lane == 0) claim = atomicAdd(&C->q_head.v, 1ull);
+        claim = __shfl_sync(kFull, claim, 0);
+        const unsigned long long W = static_cast<unsigned long long>(gridDim.x) * (blockDim.x / 32);
+        const unsigned long long slot = (claim / W) * 32 * W + static_cast<unsigned long long>(lane) * W + claim % W;
         bool pending = slot < A.qcap;
         bool empty = !pending;  // resolved without an item
         unsigned backoff = 32, polls = 0;
@@ -537,8 +542,19 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
                     done = true;
                     break;
                 }
+#ifndef SKIM_SPIN
+#define SKIM_SPIN 0
+#endif
+#if SKIM_SPIN == 0
                 __nanosleep(backoff);
                 if (backoff < 512) backoff <<= 1;
+#elif SKIM_SPIN == 2
+                {
+                    const long long t0 = clock64();
+                    while (clock64() - t0 < 256) {
+                    }
+                }
+#endif
             }
             if (!__any_sync(kFull, pending)) break;
         }
