@@ -326,41 +326,12 @@ done:
     return rc;
 }
 
-/* ------------------------------------------------------------------------ */
-/* index: hash map from node-instance pair to a list of nodes (Algorithm 1). */
-/* Open addressing with linear probing on the pair id; lists live in one     */
-/* growing node array; an erased entry keeps its slot as a tombstone.        */
-/* ------------------------------------------------------------------------ */
-typedef struct {
-    uint64_t *keys;      /* pair id + 1, 0 = empty */
-    uint64_t *start;     /* offset into nodes */
-    uint32_t *len;       /* UINT32_MAX = erased */
-    uint64_t cap, used;
-    uint32_t *nodes;
-    uint64_t ncap, nused;
-} index_t;
-
-static uint64_t slot_of(const index_t *ix, uint64_t pair) {
-    uint64_t h = fmix(pair * 0xD6E8FEB86659FD93ULL) & (ix->cap - 1);
-    while (ix->keys[h] != 0 && ix->keys[h] != pair + 1) h = (h + 1) & (ix->cap - 1);
-    return h;
-}
-
-static int index_grow(index_t *ix) {
-    index_t nx = *ix;
-    nx.cap = ix->cap ? ix->cap * 2 : 1024;
-    nx.keys = calloc(nx.cap, sizeof(uint64_t));
-    nx.start = malloc(nx.cap * sizeof(uint64_t));
-    nx.len = malloc(nx.cap * sizeof(uint32_t));
-    if (!nx.keys || !nx.start || !nx.len) { free(nx.keys); free(nx.start); free(nx.len); return OR_ENOMEM; }
-    for (uint64_t s = 0; s < ix->cap; s++) {
-        if (!ix->keys[s]) continue;
-        uint64_t t = slot_of(&nx, ix->keys[s] - 1);
-        nx.keys[t] = ix->keys[s]; nx.start[t] = ix->start[s]; nx.len[t] = ix->len[s];
-    }
-    free(ix->keys); free(ix->start); free(ix->len);
-    *ix = nx;
-    return OR_OK;
+/* Sort records of all n*l pairs by rank: 12 bytes each (packed) so that the
+ * largest runs fit in host memory. */
+typedef struct __attribute__((packed)) { uint64_t key; uint32_t val; } kv12_t;
+static int cmp_kv12(const void *a, const void *b) {
+    uint64_t x = ((const kv12_t *)a)->key, y = ((const kv12_t *)b)->key;
+    return x < y ? -1 : x > y;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -388,24 +359,31 @@ int or_skim(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
     if (n_seeds > n) { graph_free(&g); return OR_EINVAL; }
     uint64_t nl = (uint64_t)n * l;
     uint64_t cnt[OR_NCOUNT] = {0};
-    kv_t *order = malloc(nl * sizeof(kv_t));
+    kv12_t *order = malloc(nl * sizeof(kv12_t));
     uint8_t *covered = calloc(nl, 1);           /* covered[u*l + i] */
     uint32_t *size = calloc(n, sizeof(uint32_t));
     uint32_t *stamp = calloc(n, sizeof(uint32_t));
     uint32_t *queue = malloc((size_t)n * sizeof(uint32_t));
     uint8_t *chosen = calloc(n, 1);
-    index_t ix; memset(&ix, 0, sizeof(ix));
-    if (!order || !covered || !size || !stamp || !queue || !chosen) { rc = OR_ENOMEM; goto done; }
-    if ((rc = index_grow(&ix))) goto done;
-    ix.ncap = 1024; ix.nodes = malloc(ix.ncap * sizeof(uint32_t));
-    if (!ix.nodes) { rc = OR_ENOMEM; goto done; }
+    /* index: map from a processed pair to the list of nodes whose partial
+     * sketch holds its rank.  Keys are pair ids < n*l, so the map is
+     * addressed directly: list of pair p = nodes[ix_start[p] .. + ix_len[p]),
+     * ix_len[p] = 0 for a pair with no entry (never processed, or erased). */
+    uint64_t *ix_start = malloc(nl * sizeof(uint64_t));
+    uint32_t *ix_len = calloc(nl, sizeof(uint32_t));
+    uint64_t ncap = 1 << 20, nused = 0;
+    uint32_t *nodes = malloc(ncap * sizeof(uint32_t));
+    if (!order || !covered || !size || !stamp || !queue || !chosen || !ix_start || !ix_len || !nodes) {
+        rc = OR_ENOMEM;
+        goto done;
+    }
 
     /* "shuffle the nl pairs": increasing rank order */
     for (uint64_t x = 0; x < nl; x++) {
         order[x].key = or_rank(rank_key, l, (uint32_t)(x / l), (uint32_t)(x % l));
         order[x].val = (uint32_t)x;
     }
-    qsort(order, nl, sizeof(kv_t), cmp_kv);
+    qsort(order, nl, sizeof(kv12_t), cmp_kv12);
 
     uint64_t rank = 0;
     uint32_t bfs_id = 0;
@@ -419,9 +397,8 @@ int or_skim(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
             uint32_t u = (uint32_t)(pair / l), i = (uint32_t)(pair % l);
             if (covered[pair]) continue;
             cnt[5]++;
-            if (ix.used * 2 >= ix.cap && (rc = index_grow(&ix))) goto done;
-            uint64_t slot = slot_of(&ix, pair);
-            ix.keys[slot] = pair + 1; ix.start[slot] = ix.nused; ix.len[slot] = 0; ix.used++;
+            ix_start[pair] = nused;
+            ix_len[pair] = 0;
             bfs_id++;
             if (bfs_id == 0) { memset(stamp, 0, (size_t)n * sizeof(uint32_t)); bfs_id = 1; }
             uint32_t head = 0, tail = 0;
@@ -429,13 +406,13 @@ int or_skim(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
             while (head < tail) {
                 uint32_t v = queue[head++];
                 size[v]++;
-                if (ix.nused == ix.ncap) {
-                    ix.ncap *= 2;
-                    uint32_t *n2 = realloc(ix.nodes, ix.ncap * sizeof(uint32_t));
+                if (nused == ncap) {
+                    ncap += ncap / 2;
+                    uint32_t *n2 = realloc(nodes, ncap * sizeof(uint32_t));
                     if (!n2) { rc = OR_ENOMEM; goto done; }
-                    ix.nodes = n2;
+                    nodes = n2;
                 }
-                ix.nodes[ix.nused++] = v; ix.len[slot]++;
+                nodes[nused++] = v; ix_len[pair]++;
                 cnt[0]++; cnt[2]++;
                 if (size[v] == k && (x < 0 || v < (uint32_t)x)) x = v;
                 cnt[1] += g.rptr[v + 1] - g.rptr[v];
@@ -466,11 +443,10 @@ int or_skim(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
                 ix_cov++;
                 cnt[3]++;
                 uint64_t pair = (uint64_t)v * l + i;
-                uint64_t slot = slot_of(&ix, pair);
-                if (ix.keys[slot] && ix.len[slot] != UINT32_MAX) {
-                    for (uint32_t t = 0; t < ix.len[slot]; t++) size[ix.nodes[ix.start[slot] + t]]--;
-                    cnt[7] += ix.len[slot];
-                    ix.len[slot] = UINT32_MAX;          /* erase */
+                if (ix_len[pair]) {
+                    for (uint32_t t = 0; t < ix_len[pair]; t++) size[nodes[ix_start[pair] + t]]--;
+                    cnt[7] += ix_len[pair];
+                    ix_len[pair] = 0;                   /* erase */
                 }
                 cnt[4] += g.fptr[v + 1] - g.fptr[v];
                 for (uint64_t e = g.fptr[v]; e < g.fptr[v + 1]; e++) {
@@ -488,7 +464,7 @@ int or_skim(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
     if (counters) memcpy(counters, cnt, sizeof(cnt));
 done:
     free(order); free(covered); free(size); free(stamp); free(queue); free(chosen);
-    free(ix.keys); free(ix.start); free(ix.len); free(ix.nodes);
+    free(ix_start); free(ix_len); free(nodes);
     graph_free(&g);
     return rc;
 }
