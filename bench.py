@@ -123,7 +123,7 @@ def traffic_record(kernel: str):
     src = os.path.join(ROOT, "paper_1408_6282_gb300", "csrc", rec["source"])
     if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
         return None
-    return rec["dram_bytes_per_launch"]
+    return rec
 
 
 def cpu_baseline(w, g, instances: int):
@@ -298,10 +298,12 @@ def main():
         sm_max = json.load(open(PEAKS)).get("sm_max_mhz", 2070.0) if os.path.exists(PEAKS) else 2070.0
     peak = SMS * INT32_OPS_PER_SM_CLK * sm_max * 1e6 / 1e12
     trb = traffic_record("k_traverse_rev")
-    per_launch_traffic = trb if trb is not None else None
+    per_launch_traffic = trb["dram_bytes_per_launch"] if trb else None
     total_ms = sum(v[0] for v in kt.values())
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)",
                 "frac": achieved / peak, "traffic": per_launch_traffic,
+                "traffic_note": (f"DRAM bytes of one ncu-captured launch ({trb['launch']}, {trb['duration_ms']} ms), "
+                                 "from profiles/traffic.json") if trb else "no capture of the current source",
                 "kernel": "k_traverse<reverse> (batched reverse search)",
                 "avg_launch_ms": rev_ms / max(1, rev_launches), "launches_per_step": rev_launches / args.steps,
                 "share_of_kernel_time": rev_ms / total_ms if total_ms else None,

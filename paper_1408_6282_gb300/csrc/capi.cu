@@ -74,6 +74,11 @@ struct skim_ctx {
     uint32_t bB = 0, btbits = 0, blo = 0;
     uint64_t bR = 0;
     uint32_t skim_B = 0;
+    // SKIM batch sizing: ranks consumed since the last seed, and the gap (in
+    // ranks) between the last two seeds
+    uint64_t since_stop = 0, last_gap = 0;
+    double vpl_est = 0;  // visit records per lane of the last SKIM batch
+    uint32_t last_B = 0;
     // queries
     uint64_t *qk = nullptr, *qv = nullptr;
     uint64_t qtcap = 0;
@@ -332,6 +337,8 @@ int reset_stats(skim_ctx *c) {
     return SKIM_OK;
 }
 
+constexpr double kSkimVisitBudget = 4.0e6;
+
 uint32_t default_lanes(skim_ctx *c) {
     uint64_t b = c->batch_cfg ? c->batch_cfg : (1u << 21);
     b = std::min<uint64_t>(b, static_cast<uint64_t>(kMaxWords) * 64);
@@ -363,6 +370,10 @@ int skim_state_init(skim_ctx *c) {
     c->nseeds = 0;
     c->batch_active = false;
     c->skim_B = 0;
+    c->since_stop = 0;
+    c->last_gap = 0;
+    c->vpl_est = 0;
+    c->last_B = 0;
     c->sk_init = true;
     return SKIM_OK;
 }
@@ -429,6 +440,11 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
                 const uint32_t x = static_cast<uint32_t>(best & 0xffffffffu);
                 RC(commit_lanes(c, c->blo, p));
                 RC(residual(c, x, cov_out));
+                {
+                    const uint64_t after = c->bB - 1 - p;  // batch lanes not yet consumed
+                    c->last_gap = c->since_stop - after;
+                    c->since_stop = after;
+                }
                 c->blo = p + 1;
                 CK(c, launch_refilter(c->spair + c->bp0, c->blo, c->bB, c->l, c->covered, c->alive, c->st));
                 *x_out = x;
@@ -440,21 +456,41 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
             continue;
         }
         if (c->cursor < c->nl) {
-            if (!c->skim_B) c->skim_B = std::min<uint32_t>(default_lanes(c), 1u << 14);
-            uint32_t B = static_cast<uint32_t>(std::min<uint64_t>(c->skim_B, c->nl - c->cursor));
+            // A lane can cost a whole reverse search of a giant component,
+            // and lanes past the next stop are wasted if the new seed covers
+            // their source.  So a batch is sized to about kSkimVisitBudget
+            // visits, from the visits per lane of the previous batch (64
+            // lanes first; at most 16x growth per batch), and to at most four
+            // times the last gap between seeds (or the ranks consumed since the
+            // last seed, if that is longer).
+            uint64_t want = 64;
+            if (c->vpl_est > 0) {
+                want = static_cast<uint64_t>(kSkimVisitBudget / c->vpl_est);
+                want = std::min<uint64_t>(want, 16ull * std::max<uint32_t>(c->last_B, 64));
+                // each stop re-scans the batch for candidates: about four
+                // seeds' worth of ranks per batch once the gap is known
+                if (c->last_gap) want = std::min<uint64_t>(want, 4 * std::max(c->last_gap, c->since_stop));
+                want = std::max<uint64_t>(want, 64);
+            }
+            if (c->skim_B && c->skim_B < want) want = c->skim_B;  // shrunk after an overflow
+            want = std::min<uint64_t>(want, default_lanes(c));
+            uint32_t B = static_cast<uint32_t>(std::min<uint64_t>(want, c->nl - c->cursor));
             bool retry = false;
             RC(rev_batch(c, c->cursor, B, false, &retry));
             if (retry) {
                 c->skim_B = std::max<uint32_t>(64, B / 2);
                 continue;
             }
+            c->skim_B = 0;
             c->batch_active = true;
             c->bp0 = c->cursor;
             c->bB = B;
             c->blo = 0;
             c->cursor += B;
             c->hstats[SKIM_STAT_RANKS] += B;
-            c->skim_B = std::min<uint32_t>(default_lanes(c), c->skim_B * 2);
+            c->since_stop += B;
+            c->last_B = B;
+            c->vpl_est = static_cast<double>(c->bR ? c->bR : 1) / B;  // records ~ visits (one lane per entry)
             continue;
         }
         // ranks exhausted: the largest partial sketch (ties to the smallest id)
