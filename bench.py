@@ -187,6 +187,7 @@ def main():
     ap.add_argument("--queries", type=int, default=1000)
     ap.add_argument("--latency-queries", type=int, default=300)
     ap.add_argument("--cpu-instances", type=int, default=2)
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[50000.0, 200000.0, 500000.0])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -280,6 +281,23 @@ def main():
         lat.append((time.perf_counter() - a) * 1000.0)
     lat.sort()
 
+    # serving: Poisson query streams replayed through the continuous-batching
+    # server on the same resident sketches, against the one-query-at-a-time form
+    serving = []
+    with sk.server(max_inflight=4096, scratch_slots=1 << 24, streams=4) as srv:
+        for rate in args.serve_rates:
+            arr = synth.poisson_arrivals(len(qs), rate, w.keys().query + int(rate))
+            g0, q0 = srv.stats()
+            t_a = time.perf_counter()
+            slat, sest = srv.replay(arr, qs)
+            wall = time.perf_counter() - t_a
+            g1, q1 = srv.stats()
+            slat = np.sort(slat) * 1000.0
+            serving.append({"offered_qps": rate, "qps": len(qs) / wall,
+                            "p50_ms": float(slat[len(slat) // 2]),
+                            "p99_ms": float(slat[min(len(slat) - 1, int(0.99 * len(slat)))]),
+                            "mean_group": (q1 - q0) / max(1, g1 - g0)})
+
     # end to end through the C ABI with host buffers
     e2e_times = []
     h2d = 8 * g.m + 4 * int(q_off[-1]) + 8 * (len(qs) + 1)
@@ -333,6 +351,8 @@ def main():
             "rank_order_s": statistics.median(part["ranks"]),
             "oracle_qps": len(qs) / statistics.median(part["query"]),
             "query_p50_ms": lat[len(lat) // 2], "query_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "single_query_qps": 1000.0 / (sum(lat) / len(lat)),
+            "serving": serving,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

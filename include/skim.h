@@ -177,6 +177,44 @@ int skim_set_timing(skim_ctx *ctx, int on);
 int skim_kernel_launches(uint64_t *out);
 int skim_kernel_times(skim_ctx *ctx, double *ms_out, uint64_t *launches_out, uint32_t count, int reset);
 
+/* Shape of a context: nodes n, sketch size k, instances l (host outputs). */
+int skim_context_shape(skim_ctx *ctx, uint32_t *n, uint32_t *k, uint32_t *l);
+
+/* ---- Serving: the influence oracle as a continuous-batching request loop ----
+ * (queries of Section 5.1, Eq. unionest, over sketches resident on the GPU).
+ * A server thread admits submitted seed sets into launch groups while
+ * in-flight slots (max_inflight queries) and scratch memory (scratch_slots
+ * hash-table slots of 16 bytes, split over `streams` streams; a query of |S|
+ * seeds needs the next power of two >= 2|S|(k-1)+2) allow, and launches each
+ * group on a free stream.  Groups on different streams run concurrently; a
+ * request that arrives while others are on the GPU joins the next group as
+ * soon as slots and memory free up.  Each result is bitwise identical to
+ * skim_oracle_query on the same seeds.  The context's sketches must stay
+ * built, and the context must not be used by other calls, until
+ * skim_server_stop() returns.  Submit, poll and wait may be called from any
+ * host thread.  Errors: SKIM_EINVAL, SKIM_ENOTBUILT, SKIM_ENOMEM; submit
+ * returns SKIM_ERANGE for a query larger than one stream's scratch. */
+typedef struct skim_server skim_server;
+int skim_server_start(skim_ctx *ctx, uint32_t max_inflight, uint64_t scratch_slots, uint32_t streams,
+                      skim_server **out);
+/* Queue one query (seeds (host) are copied); *ticket identifies it. */
+int skim_server_submit(skim_server *srv, const uint32_t *seeds, uint32_t n_seeds, uint64_t *ticket);
+/* Non-blocking: *done = 1 and *est set once the result is ready (each
+ * result is returned once). */
+int skim_server_poll(skim_server *srv, uint64_t ticket, int *done, double *est);
+/* Blocking with a timeout: SKIM_ETIMEOUT if the result is not ready in time. */
+int skim_server_wait(skim_server *srv, uint64_t ticket, double *est, uint32_t timeout_ms);
+/* Load generator: submit query j (seeds[offsets[j] .. offsets[j+1]), host) at
+ * arrival_s[j] seconds after the call starts, from the calling thread, then
+ * wait for all; latency_s[j] = completion time - submit time, est_out[j] the
+ * estimate. */
+int skim_server_replay(skim_server *srv, const double *arrival_s, const uint64_t *offsets, const uint32_t *seeds,
+                       uint32_t q, double *latency_s, double *est_out);
+/* Launch groups so far and the queries they held. */
+int skim_server_stats(skim_server *srv, uint64_t *groups, uint64_t *queries);
+/* Finish the queued work, stop the thread and free the server. */
+int skim_server_stop(skim_server *srv);
+
 /* Allocation-free influence query, for callers that cannot allocate device
  * memory (code that runs inside another framework's memory pool or under a
  * fixed memory budget, where a cudaMalloc is not allowed).  The paper has no

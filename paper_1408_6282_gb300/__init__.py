@@ -70,6 +70,14 @@ def load():
     lib.skim_kernel_times.argtypes = [vp, vp, vp, u32, C.c_int]
     lib.skim_kernel_launches.argtypes = [vp]
     lib.skim_union_estimate_static.argtypes = [vp, vp, u32, u32, u32, vp, u32, vp, vp]
+    lib.skim_context_shape.argtypes = [vp, vp, vp, vp]
+    lib.skim_server_start.argtypes = [vp, u32, u64, u32, C.POINTER(vp)]
+    lib.skim_server_submit.argtypes = [vp, vp, u32, vp]
+    lib.skim_server_poll.argtypes = [vp, u64, vp, vp]
+    lib.skim_server_wait.argtypes = [vp, u64, vp, u32]
+    lib.skim_server_replay.argtypes = [vp, vp, vp, vp, u32, vp, vp]
+    lib.skim_server_stats.argtypes = [vp, vp, vp]
+    lib.skim_server_stop.argtypes = [vp]
     lib.skim_strerror.argtypes = [C.c_int]
     lib.skim_strerror.restype = C.c_char_p
     _lib = lib
@@ -156,6 +164,48 @@ def skim_union_estimate_static(x_dev: int, len_dev: int, n: int, k: int, l: int,
     """Allocation-free query (static scratch); all pointers are device addresses."""
     _check(load().skim_union_estimate_static(x_dev, len_dev, n, k, l, seeds_dev or None, n_seeds, est_dev,
                                              stream or None), "skim_union_estimate_static")
+
+
+def skim_server_start(ctx: int, max_inflight: int, scratch_slots: int, streams: int) -> int:
+    h = C.c_void_p()
+    _check(load().skim_server_start(ctx, max_inflight, scratch_slots, streams, C.byref(h)), "skim_server_start")
+    return h.value
+
+
+def skim_server_submit(srv: int, seeds: np.ndarray, n_seeds: int) -> int:
+    t = np.zeros(1, np.uint64)
+    _check(load().skim_server_submit(srv, _ptr(seeds) if n_seeds else None, n_seeds, _ptr(t)), "skim_server_submit")
+    return int(t[0])
+
+
+def skim_server_poll(srv: int, ticket: int):
+    done = np.zeros(1, np.int32)
+    est = np.zeros(1, np.float64)
+    _check(load().skim_server_poll(srv, ticket, _ptr(done), _ptr(est)), "skim_server_poll")
+    return bool(done[0]), float(est[0])
+
+
+def skim_server_wait(srv: int, ticket: int, timeout_ms: int = 60000) -> float:
+    est = np.zeros(1, np.float64)
+    _check(load().skim_server_wait(srv, ticket, _ptr(est), timeout_ms), "skim_server_wait")
+    return float(est[0])
+
+
+def skim_server_replay(srv: int, arrival_s: np.ndarray, offsets: np.ndarray, seeds: np.ndarray, q: int,
+                       latency_s: np.ndarray, est_out: np.ndarray):
+    _check(load().skim_server_replay(srv, _ptr(arrival_s), _ptr(offsets), _ptr(seeds), q, _ptr(latency_s),
+                                     _ptr(est_out)), "skim_server_replay")
+
+
+def skim_server_stats(srv: int) -> tuple[int, int]:
+    g = np.zeros(1, np.uint64)
+    q = np.zeros(1, np.uint64)
+    _check(load().skim_server_stats(srv, _ptr(g), _ptr(q)), "skim_server_stats")
+    return int(g[0]), int(q[0])
+
+
+def skim_server_stop(srv: int):
+    _check(load().skim_server_stop(srv), "skim_server_stop")
 
 
 def skim_destroy(ctx: int):
@@ -252,7 +302,53 @@ class Skim:
         skim_kernel_times(self.ctx, ms, cnt, len(KERNEL_NAMES), 1 if reset else 0)
         return {n: (float(a), int(b)) for n, a, b in zip(KERNEL_NAMES, ms, cnt)}
 
+    def server(self, max_inflight: int = 4096, scratch_slots: int = 1 << 24, streams: int = 4) -> "Server":
+        return Server(self, max_inflight, scratch_slots, streams)
+
     def stats(self) -> dict:
         out = np.zeros(len(STAT_NAMES), np.uint64)
         skim_get_stats(self.ctx, out, len(STAT_NAMES))
         return dict(zip(STAT_NAMES, (int(v) for v in out)))
+
+
+class Server:
+    """Continuous-batching query server over a Skim context's sketches."""
+
+    def __init__(self, sk: Skim, max_inflight: int = 4096, scratch_slots: int = 1 << 24, streams: int = 4):
+        self.sk = sk
+        self.srv = skim_server_start(sk.ctx, max_inflight, scratch_slots, streams)
+
+    def submit(self, seeds) -> int:
+        s = np.ascontiguousarray(seeds, dtype=np.uint32)
+        return skim_server_submit(self.srv, s, int(s.shape[0]))
+
+    def poll(self, ticket: int):
+        return skim_server_poll(self.srv, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> float:
+        return skim_server_wait(self.srv, ticket, timeout_ms)
+
+    def replay(self, arrival_s, seed_sets):
+        sets = [np.ascontiguousarray(x, dtype=np.uint32) for x in seed_sets]
+        off = np.zeros(len(sets) + 1, np.uint64)
+        off[1:] = np.cumsum([x.shape[0] for x in sets])
+        flat = np.concatenate(sets) if sets and off[-1] else np.zeros(1, np.uint32)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.zeros(max(1, len(sets)), np.float64)
+        est = np.zeros(max(1, len(sets)), np.float64)
+        skim_server_replay(self.srv, arr, off, flat, len(sets), lat, est)
+        return lat[: len(sets)], est[: len(sets)]
+
+    def stats(self) -> tuple[int, int]:
+        return skim_server_stats(self.srv)
+
+    def stop(self):
+        if self.srv:
+            skim_server_stop(self.srv)
+            self.srv = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()

@@ -955,6 +955,14 @@ int skim_kernel_times(skim_ctx *c, double *ms_out, uint64_t *launches_out, uint3
     return SKIM_OK;
 }
 
+int skim_context_shape(skim_ctx *c, uint32_t *n, uint32_t *k, uint32_t *l) {
+    if (!c || !n || !k || !l) return SKIM_EINVAL;
+    *n = c->n;
+    *k = c->k;
+    *l = c->l;
+    return SKIM_OK;
+}
+
 int skim_get_stats(skim_ctx *c, uint64_t *out, uint32_t count) {
     if (!c || !out) return SKIM_EINVAL;
     for (uint32_t i = 0; i < count && i < SKIM_STAT_COUNT; i++) out[i] = c->hstats[i];
