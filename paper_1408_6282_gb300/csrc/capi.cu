@@ -84,9 +84,13 @@ struct skim_ctx {
     uint64_t qtcap = 0;
     uint32_t *qseeds = nullptr;
     uint64_t qseeds_cap = 0;
-    uint64_t *qoff = nullptr, *qtoff = nullptr;
+    uint64_t *qoff = nullptr;  // seed, table and chunk offsets (3 x (q+1))
     double *qout = nullptr;
     uint64_t qmeta_cap = 0;
+    uint64_t *qtop = nullptr;
+    unsigned *qtopu = nullptr;
+    void *qpart = nullptr;
+    uint64_t qpart_cap = 0;
     // counters of the last build/greedy call
     uint64_t hstats[SKIM_STAT_COUNT] = {0};
     // kernel timing (CUDA events on the context stream)
@@ -521,7 +525,18 @@ int rank_order(skim_ctx *c) {
     return SKIM_OK;
 }
 
-int ensure_query_space(skim_ctx *c, uint64_t seeds, uint64_t q, uint64_t table) {
+int ensure_query_space(skim_ctx *c, uint64_t seeds, uint64_t q, uint64_t table, uint64_t chunks) {
+    if (chunks > c->qpart_cap) {
+        if (c->qpart) cudaFree(c->qpart);
+        c->qpart = nullptr;
+        c->qpart_cap = std::max<uint64_t>(chunks, 1024);
+        cudaError_t e = cudaMalloc(&c->qpart, c->qpart_cap * query_partial_bytes());
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->qpart_cap = 0;
+            return SKIM_ENOMEM;
+        }
+    }
     if (seeds > c->qseeds_cap) {
         dfree(c->qseeds);
         c->qseeds_cap = std::max<uint64_t>(seeds, 4096);
@@ -529,12 +544,14 @@ int ensure_query_space(skim_ctx *c, uint64_t seeds, uint64_t q, uint64_t table) 
     }
     if (q + 1 > c->qmeta_cap) {
         dfree(c->qoff);
-        dfree(c->qtoff);
         dfree(c->qout);
+        dfree(c->qtop);
+        dfree(c->qtopu);
         c->qmeta_cap = std::max<uint64_t>(q + 1, 1024);
-        RC(dalloc(c, &c->qoff, c->qmeta_cap));
-        RC(dalloc(c, &c->qtoff, c->qmeta_cap));
+        RC(dalloc(c, &c->qoff, 3 * c->qmeta_cap));  // seed, table and chunk offsets in one upload
         RC(dalloc(c, &c->qout, c->qmeta_cap));
+        RC(dalloc(c, &c->qtop, c->qmeta_cap));
+        RC(dalloc(c, &c->qtopu, c->qmeta_cap));
     }
     if (table > c->qtcap) {
         dfree(c->qk);
@@ -582,7 +599,9 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->lcnt); dfree(c->full); dfree(c->X); dfree(c->xlen);
     dfree(c->covered); dfree(c->seg_start); dfree(c->pend_trav); dfree(c->pend_erase);
     dfree(c->size); dfree(c->seg_len); dfree(c->idx); dfree(c->chosen);
-    dfree(c->qk); dfree(c->qv); dfree(c->qseeds); dfree(c->qoff); dfree(c->qtoff); dfree(c->qout);
+    dfree(c->qk); dfree(c->qv); dfree(c->qseeds); dfree(c->qoff); dfree(c->qout);
+    dfree(c->qtop); dfree(c->qtopu);
+    if (c->qpart) cudaFree(c->qpart);
     for (auto &p : c->kpend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->kpool) cudaEventDestroy(e);
     delete c;
@@ -886,32 +905,38 @@ int skim_oracle_query_batch(skim_ctx *c, const uint64_t *offsets, uint32_t q, co
     if (!c->built) return SKIM_ENOTBUILT;
     if (q == 0) return SKIM_OK;
     if (offsets[0] != 0) return SKIM_EINVAL;
-    std::vector<uint64_t> toff(static_cast<size_t>(q) + 1, 0);
+    // one host block: seed offsets | table offsets | chunk offsets
+    const size_t q1 = static_cast<size_t>(q) + 1;
+    std::vector<uint64_t> meta(3 * q1, 0);
+    uint64_t *toff = meta.data() + q1, *coff = meta.data() + 2 * q1;
     for (uint32_t i = 0; i < q; i++) {
         if (offsets[i + 1] < offsets[i]) return SKIM_EINVAL;
-        toff[i + 1] = toff[i] + query_table(offsets[i + 1] - offsets[i], c->k);
+        const uint64_t H = query_table(offsets[i + 1] - offsets[i], c->k);
+        toff[i + 1] = toff[i] + H;
+        coff[i + 1] = coff[i] + query_chunks(H);
     }
+    std::copy(offsets, offsets + q1, meta.data());
     const uint64_t total = offsets[q];
     if (total && !seeds) return SKIM_EINVAL;
     if (!on_device) {
         for (uint64_t i = 0; i < total; i++)
             if (seeds[i] >= c->n) return SKIM_EINVAL;
     }
-    RC(ensure_query_space(c, total, q, toff[q]));
+    RC(ensure_query_space(c, total, q, toff[q], coff[q]));
     const uint32_t *dseeds = seeds;
     if (!on_device && total) {
         CK(c, cudaMemcpyAsync(c->qseeds, seeds, total * sizeof(uint32_t), cudaMemcpyHostToDevice, c->st));
         dseeds = c->qseeds;
     }
-    CK(c, cudaMemcpyAsync(c->qoff, offsets, (static_cast<size_t>(q) + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
-                          c->st));
-    CK(c, cudaMemcpyAsync(c->qtoff, toff.data(), toff.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, c->st));
+    uint64_t *d_off = c->qoff, *d_toff = c->qoff + q1, *d_coff = c->qoff + 2 * q1;
+    CK(c, cudaMemcpyAsync(d_off, meta.data(), meta.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, c->st));
     CK(c, cudaMemsetAsync(c->dflag, 0, sizeof(unsigned), c->st));
     double *dout = on_device ? est_out : c->qout;
     {
         KTimer kt(c, SKIM_K_QUERY);
-        CK(c, launch_query(c->X, c->xlen, c->n, c->k, c->l, dseeds, c->qoff, c->qtoff, q, c->qk, c->qv, dout,
-                           c->dflag, c->st));
+        QueryScratch qs{c->qk, c->qv, c->qtop, c->qtopu, c->qpart, c->dflag};
+        CK(c, launch_query_multi(c->X, c->xlen, c->n, c->k, c->l, dseeds, d_off, d_toff, d_coff, q, toff[q], total,
+                                 static_cast<uint32_t>(coff[q]), qs, dout, c->st));
     }
     unsigned bad = 0;
     CK(c, cudaMemcpyAsync(&bad, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));

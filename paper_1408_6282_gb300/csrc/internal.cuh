@@ -111,8 +111,22 @@ cudaError_t launch_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl, cu
 cudaError_t launch_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl, cudaStream_t s);
 
 // query.cu
-cudaError_t launch_query(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
-                         const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off, uint32_t q,
-                         uint64_t *hkeys, uint64_t *hvals, double *out, unsigned *err, cudaStream_t s);
+// Scratch of the multi-block query path: hash tables (total_slots keys and
+// values), per-query top-rank slots, per-chunk partial sums, an error flag.
+struct QueryScratch {
+    uint64_t *hkeys;
+    uint64_t *hvals;
+    uint64_t *top_tau;
+    unsigned *top_used;
+    void *partial;
+    unsigned *err;
+};
+uint32_t query_chunks(uint64_t table_slots);  // chunks of one query's table
+size_t query_partial_bytes();                  // bytes per chunk partial
+cudaError_t launch_query_multi(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
+                               const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off,
+                               const uint64_t *chunk_off, uint32_t q, uint64_t total_slots, uint64_t total_seeds,
+                               uint32_t total_chunks, const QueryScratch &qs, double *out, cudaStream_t s);
+
 
 }  // namespace skim

@@ -5,8 +5,8 @@
 // is divided by l.  tau_u is the k-th smallest rank of a full sketch and 1 for
 // a sketch with fewer than k ranks (Eq. combinedthresh).
 //
-// One block per query: a hash table in global scratch keeps, per distinct z,
-// the largest tau (as a 64-bit integer; the integer order equals the order of
+// A hash table per query in global scratch keeps, per distinct z, the
+// largest tau (as a 64-bit integer; the integer order equals the order of
 // the reals h/2^64 and the rounding to double is monotone).  Each term 1/tau is
 // formed in double exactly as h -> double -> scale by 2^-64 -> 1/x, then added
 // exactly in 192-bit fixed point (64 fraction bits suffice: every term is >= 1
@@ -94,32 +94,45 @@ SKIM_DEV double fixed_to_double(const U192 &a) {
     return ldexp(static_cast<double>(mant), sh - 64);
 }
 
-__global__ void __launch_bounds__(kQThreads) k_query(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k,
-                                                     uint32_t l, const uint32_t *seeds, const uint64_t *offsets,
-                                                     const uint64_t *table_off, uint64_t *hkeys, uint64_t *hvals,
-                                                     double *out, unsigned *err) {
-    __shared__ unsigned long long top_tau;  // rank value ~0 has no table key: kept here
-    __shared__ int top_used;
-    __shared__ U192 wsum[kQThreads / 32];
-    const uint64_t q = blockIdx.x;
-    const uint64_t s0 = offsets[q], s1 = offsets[q + 1];
-    const uint64_t H = table_off[q + 1] - table_off[q];
-    uint64_t *tk = hkeys + table_off[q];
-    uint64_t *tv = hvals + table_off[q];
-    if (threadIdx.x == 0) {
-        top_tau = 0;
-        top_used = 0;
+// ---- multi-block form: the work of a group of queries is spread over the
+// whole GPU.  Each query owns a hash table of H_q slots (a power of two) in
+// one scratch array; table q is cut into chunks of kQChunk slots whose
+// partial sums (exact, 192-bit) are added per query at the end.
+
+constexpr uint32_t kQChunk = 2048;
+
+SKIM_DEV uint32_t upper_bound_u64(const uint64_t *a, uint32_t n, uint64_t x) {  // first i with a[i] > x
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1;
+        else hi = mid;
     }
-    for (uint64_t i = threadIdx.x; i < H; i += blockDim.x) {
-        tk[i] = kEmptyKey;
-        tv[i] = 0;
+    return lo;
+}
+
+__global__ void k_q_clear(uint64_t *hkeys, uint64_t *hvals, uint64_t total, unsigned long long *top_tau,
+                          unsigned *top_used, uint32_t q) {
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        hkeys[i] = kEmptyKey;
+        hvals[i] = 0;
     }
-    __syncthreads();
-    const uint64_t hmask = H - 1;
-    const uint64_t work = (s1 - s0) * k;
-    for (uint64_t e = threadIdx.x; e < work; e += blockDim.x) {
-        const uint32_t u = seeds[s0 + e / k];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < q; i += gridDim.x * blockDim.x) {
+        top_tau[i] = 0;
+        top_used[i] = 0;
+    }
+}
+
+__global__ void k_q_insert(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, const uint32_t *seeds,
+                           const uint64_t *offsets, const uint64_t *table_off, uint32_t q, uint64_t *hkeys,
+                           uint64_t *hvals, unsigned long long *top_tau, unsigned *top_used, unsigned *err) {
+    const uint64_t total = offsets[q] * k;
+    for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t j = e / k;
         const uint32_t pos = static_cast<uint32_t>(e % k);
+        const uint32_t u = seeds[j];
         if (u >= n) {
             atomicOr(err, 1u);
             continue;
@@ -127,14 +140,18 @@ __global__ void __launch_bounds__(kQThreads) k_query(const uint64_t *X, const ui
         const uint32_t ln = xlen[u];
         const uint32_t body = ln == k ? k - 1 : ln;
         if (pos >= body) continue;
+        const uint32_t qi = upper_bound_u64(offsets + 1, q, j);  // query holding seed j
         const uint64_t z = X[static_cast<uint64_t>(u) * k + pos];
         const uint64_t tau = ln == k ? X[static_cast<uint64_t>(u) * k + k - 1] : ~0ull;
         if (z == kEmptyKey) {
-            atomicMax(&top_tau, static_cast<unsigned long long>(tau));
-            top_used = 1;
+            atomicMax(&top_tau[qi], static_cast<unsigned long long>(tau));
+            top_used[qi] = 1;
             continue;
         }
-        uint64_t h = fmix(z) & hmask;
+        const uint64_t base = table_off[qi], H = table_off[qi + 1] - base;
+        uint64_t *tk = hkeys + base;
+        uint64_t *tv = hvals + base;
+        uint64_t h = fmix(z) & (H - 1);
         for (uint64_t p = 0; p < H; p++) {
             unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long *>(&tk[h]),
                                                 static_cast<unsigned long long>(kEmptyKey),
@@ -143,15 +160,26 @@ __global__ void __launch_bounds__(kQThreads) k_query(const uint64_t *X, const ui
                 atomicMax(reinterpret_cast<unsigned long long *>(&tv[h]), static_cast<unsigned long long>(tau));
                 break;
             }
-            h = (h + 1) & hmask;
+            h = (h + 1) & (H - 1);
         }
     }
-    __syncthreads();
+}
+
+// one block per chunk: partial[c] = exact sum of the chunk's terms
+__global__ void __launch_bounds__(256) k_q_sum(const uint64_t *hkeys, const uint64_t *hvals, const uint64_t *table_off,
+                                               const uint64_t *chunk_off, uint32_t q,
+                                               const unsigned long long *top_tau, const unsigned *top_used,
+                                               U192 *partial) {
+    __shared__ U192 wsum[8];
+    const uint32_t c = blockIdx.x;
+    const uint32_t qi = upper_bound_u64(chunk_off + 1, q, c);
+    const uint64_t first = chunk_off[qi];
+    const uint64_t lo = table_off[qi] + (c - first) * kQChunk;
+    const uint64_t hi = min(lo + kQChunk, table_off[qi + 1]);
     U192 acc{{0, 0, 0}};
-    for (uint64_t i = threadIdx.x; i < H; i += blockDim.x) {
-        if (tk[i] != kEmptyKey) add192(acc, to_fixed(inv_tau(tv[i])));
-    }
-    if (threadIdx.x == 0 && top_used) add192(acc, to_fixed(inv_tau(top_tau)));
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        if (hkeys[i] != kEmptyKey) add192(acc, to_fixed(inv_tau(hvals[i])));
+    if (c == first && threadIdx.x == 0 && top_used[qi]) add192(acc, to_fixed(inv_tau(top_tau[qi])));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         U192 other;
@@ -162,19 +190,45 @@ __global__ void __launch_bounds__(kQThreads) k_query(const uint64_t *X, const ui
     __syncthreads();
     if (threadIdx.x == 0) {
         U192 tot{{0, 0, 0}};
-        for (int w = 0; w < kQThreads / 32; w++) add192(tot, wsum[w]);
-        out[q] = fixed_to_double(tot) / static_cast<double>(l);
+        for (int w = 0; w < 8; w++) add192(tot, wsum[w]);
+        partial[c] = tot;
+    }
+}
+
+__global__ void k_q_final(const U192 *partial, const uint64_t *chunk_off, uint32_t q, uint32_t l, double *out) {
+    for (uint32_t qi = blockIdx.x * blockDim.x + threadIdx.x; qi < q; qi += gridDim.x * blockDim.x) {
+        U192 tot{{0, 0, 0}};
+        for (uint64_t c = chunk_off[qi]; c < chunk_off[qi + 1]; c++) add192(tot, partial[c]);
+        out[qi] = fixed_to_double(tot) / static_cast<double>(l);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_query(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
-                         const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off, uint32_t q,
-                         uint64_t *hkeys, uint64_t *hvals, double *out, unsigned *err, cudaStream_t s) {
+uint32_t query_chunks(uint64_t table_slots) { return static_cast<uint32_t>((table_slots + kQChunk - 1) / kQChunk); }
+
+size_t query_partial_bytes() { return sizeof(U192); }
+
+cudaError_t launch_query_multi(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
+                               const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off,
+                               const uint64_t *chunk_off, uint32_t q, uint64_t total_slots, uint64_t total_seeds,
+                               uint32_t total_chunks, const QueryScratch &qs, double *out, cudaStream_t s) {
     if (q == 0) return cudaSuccess;
+    auto grid = [](uint64_t work) {
+        uint64_t g = (work + 255) / 256;
+        return static_cast<unsigned>(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+    };
+    unsigned long long *top_tau = reinterpret_cast<unsigned long long *>(qs.top_tau);
     note_launch();
-    k_query<<<q, kQThreads, 0, s>>>(X, xlen, n, k, l, seeds, offsets, table_off, hkeys, hvals, out, err);
+    k_q_clear<<<grid(total_slots), 256, 0, s>>>(qs.hkeys, qs.hvals, total_slots, top_tau, qs.top_used, q);
+    note_launch();
+    k_q_insert<<<grid(total_seeds * k), 256, 0, s>>>(X, xlen, n, k, seeds, offsets, table_off, q, qs.hkeys, qs.hvals,
+                                                     top_tau, qs.top_used, qs.err);
+    note_launch();
+    k_q_sum<<<total_chunks, 256, 0, s>>>(qs.hkeys, qs.hvals, table_off, chunk_off, q, top_tau, qs.top_used,
+                                         static_cast<U192 *>(qs.partial));
+    note_launch();
+    k_q_final<<<grid(q), 256, 0, s>>>(static_cast<const U192 *>(qs.partial), chunk_off, q, l, out);
     return cudaGetLastError();
 }
 

@@ -44,9 +44,13 @@ struct Lane {  // one stream and its buffers
     uint64_t *hk = nullptr, *hv = nullptr;
     uint32_t *d_seeds = nullptr, *h_seeds = nullptr;
     uint64_t seed_cap = 0;
-    uint64_t *d_off = nullptr, *h_off = nullptr, *d_toff = nullptr, *h_toff = nullptr;
+    uint64_t *d_meta = nullptr, *h_meta = nullptr;  // seed | table | chunk offsets, 3 x (group_cap + 1)
     double *d_out = nullptr, *h_out = nullptr;
     unsigned *d_err = nullptr;
+    uint64_t *d_top = nullptr;
+    unsigned *d_topu = nullptr;
+    void *d_part = nullptr;
+    uint64_t part_cap = 0;
     uint32_t group_cap = 0;
     std::vector<uint64_t> tickets;
 };
@@ -86,13 +90,14 @@ void free_lane(Lane &ln) {
     if (ln.hk) cudaFree(ln.hk);
     if (ln.hv) cudaFree(ln.hv);
     if (ln.d_seeds) cudaFree(ln.d_seeds);
-    if (ln.d_off) cudaFree(ln.d_off);
-    if (ln.d_toff) cudaFree(ln.d_toff);
+    if (ln.d_meta) cudaFree(ln.d_meta);
     if (ln.d_out) cudaFree(ln.d_out);
     if (ln.d_err) cudaFree(ln.d_err);
+    if (ln.d_top) cudaFree(ln.d_top);
+    if (ln.d_topu) cudaFree(ln.d_topu);
+    if (ln.d_part) cudaFree(ln.d_part);
     if (ln.h_seeds) cudaFreeHost(ln.h_seeds);
-    if (ln.h_off) cudaFreeHost(ln.h_off);
-    if (ln.h_toff) cudaFreeHost(ln.h_toff);
+    if (ln.h_meta) cudaFreeHost(ln.h_meta);
     if (ln.h_out) cudaFreeHost(ln.h_out);
     if (ln.done) cudaEventDestroy(ln.done);
     if (ln.st) cudaStreamDestroy(ln.st);
@@ -129,18 +134,21 @@ bool admit(skim_server *s) {
             break;
         }
     if (!ln) return false;
-    uint64_t used = 0, nseeds = 0;
+    uint64_t used = 0, nseeds = 0, chunks = 0;
     uint32_t cnt = 0;
-    ln->h_off[0] = 0;
-    ln->h_toff[0] = 0;
+    const size_t g1 = static_cast<size_t>(ln->group_cap) + 1;
+    uint64_t *h_off = ln->h_meta, *h_toff = ln->h_meta + g1, *h_coff = ln->h_meta + 2 * g1;
+    h_off[0] = h_toff[0] = h_coff[0] = 0;
     while (!s->pending.empty() && cnt < ln->group_cap && s->inflight + cnt < s->max_inflight) {
         Request &r = s->pending.front();
         if (used + r.slots > ln->arena_slots || nseeds + r.seeds.size() > ln->seed_cap) break;  // memory admission
         if (!r.seeds.empty()) std::memcpy(ln->h_seeds + nseeds, r.seeds.data(), r.seeds.size() * sizeof(uint32_t));
         nseeds += r.seeds.size();
         used += r.slots;
-        ln->h_off[cnt + 1] = nseeds;
-        ln->h_toff[cnt + 1] = used;
+        chunks += query_chunks(r.slots);
+        h_off[cnt + 1] = nseeds;
+        h_toff[cnt + 1] = used;
+        h_coff[cnt + 1] = chunks;
         ln->tickets.push_back(r.ticket);
         cnt++;
         s->pending.pop_front();
@@ -154,12 +162,12 @@ bool admit(skim_server *s) {
     if (nseeds)
         ok &= cudaMemcpyAsync(ln->d_seeds, ln->h_seeds, nseeds * sizeof(uint32_t), cudaMemcpyHostToDevice, ln->st) ==
               cudaSuccess;
-    ok &= cudaMemcpyAsync(ln->d_off, ln->h_off, (cnt + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, ln->st) ==
+    ok &= cudaMemcpyAsync(ln->d_meta, ln->h_meta, 3 * g1 * sizeof(uint64_t), cudaMemcpyHostToDevice, ln->st) ==
           cudaSuccess;
-    ok &= cudaMemcpyAsync(ln->d_toff, ln->h_toff, (cnt + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, ln->st) ==
-          cudaSuccess;
-    ok &= launch_query(s->X, s->xlen, s->n, s->k, s->l, ln->d_seeds, ln->d_off, ln->d_toff, cnt, ln->hk, ln->hv,
-                       ln->d_out, ln->d_err, ln->st) == cudaSuccess;
+    QueryScratch qs{ln->hk, ln->hv, ln->d_top, ln->d_topu, ln->d_part, ln->d_err};
+    ok &= launch_query_multi(s->X, s->xlen, s->n, s->k, s->l, ln->d_seeds, ln->d_meta, ln->d_meta + g1,
+                             ln->d_meta + 2 * g1, cnt, used, nseeds, static_cast<uint32_t>(chunks), qs, ln->d_out,
+                             ln->st) == cudaSuccess;
     ok &= cudaMemcpyAsync(ln->h_out, ln->d_out, cnt * sizeof(double), cudaMemcpyDeviceToHost, ln->st) == cudaSuccess;
     ok &= cudaEventRecord(ln->done, ln->st) == cudaSuccess;
     if (!ok) s->error = SKIM_ECUDA;
@@ -222,13 +230,15 @@ int skim_server_start(skim_ctx *ctx, uint32_t max_inflight, uint64_t scratch_slo
         ok &= cudaMalloc(&ln.hk, arena * sizeof(uint64_t)) == cudaSuccess;
         ok &= cudaMalloc(&ln.hv, arena * sizeof(uint64_t)) == cudaSuccess;
         ok &= cudaMalloc(&ln.d_seeds, ln.seed_cap * sizeof(uint32_t)) == cudaSuccess;
-        ok &= cudaMalloc(&ln.d_off, (gcap + 1) * sizeof(uint64_t)) == cudaSuccess;
-        ok &= cudaMalloc(&ln.d_toff, (gcap + 1) * sizeof(uint64_t)) == cudaSuccess;
+        ln.part_cap = arena / 64 + gcap;  // chunks: at most one per 64 slots (smallest table) per query
+        ok &= cudaMalloc(&ln.d_meta, 3 * (gcap + 1) * sizeof(uint64_t)) == cudaSuccess;
         ok &= cudaMalloc(&ln.d_out, gcap * sizeof(double)) == cudaSuccess;
         ok &= cudaMalloc(&ln.d_err, sizeof(unsigned)) == cudaSuccess;
+        ok &= cudaMalloc(&ln.d_top, gcap * sizeof(uint64_t)) == cudaSuccess;
+        ok &= cudaMalloc(&ln.d_topu, gcap * sizeof(unsigned)) == cudaSuccess;
+        ok &= cudaMalloc(&ln.d_part, ln.part_cap * query_partial_bytes()) == cudaSuccess;
         ok &= cudaMallocHost(&ln.h_seeds, ln.seed_cap * sizeof(uint32_t)) == cudaSuccess;
-        ok &= cudaMallocHost(&ln.h_off, (gcap + 1) * sizeof(uint64_t)) == cudaSuccess;
-        ok &= cudaMallocHost(&ln.h_toff, (gcap + 1) * sizeof(uint64_t)) == cudaSuccess;
+        ok &= cudaMallocHost(&ln.h_meta, 3 * (gcap + 1) * sizeof(uint64_t)) == cudaSuccess;
         ok &= cudaMallocHost(&ln.h_out, gcap * sizeof(double)) == cudaSuccess;
         if (!ok) break;
     }
