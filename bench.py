@@ -188,6 +188,7 @@ def main():
     ap.add_argument("--latency-queries", type=int, default=300)
     ap.add_argument("--cpu-instances", type=int, default=2)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[50000.0, 200000.0, 500000.0])
+    ap.add_argument("--batched-graphs", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -298,6 +299,41 @@ def main():
                             "p99_ms": float(slat[min(len(slat) - 1, int(0.99 * len(slat)))]),
                             "mean_group": (q1 - q0) / max(1, g1 - g0)})
 
+    # batched form: many independent graphs in one context and one pass,
+    # against building them one context at a time on the same GPU
+    batched = None
+    if args.batched_graphs:
+        specs = synth.batched_graph_specs(args.batched_graphs)
+        gl = [synth.rmat(sc, ef, key, device=f"cuda:{local}") for sc, ef, key in specs]
+        gk = [synth.Keys.from_seed(key) for _, _, key in specs]
+        bl, bk = 64, 32
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        for gr, kk in zip(gl, gk):
+            with pkg.Skim(gr.n, gr.src, gr.dst, bl, bk, 2, 0.0, kk.coin, kk.rank, kk.prob,
+                          stream=stream.cuda_stream) as one:
+                one.build_sketches()
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - t_a
+        many = pkg.Skim.batch([(gr.n, gr.src, gr.dst) for gr in gl], bl, bk, [2] * len(gl), [0.0] * len(gl),
+                              [kk.coin for kk in gk], [kk.rank for kk in gk], [kk.prob for kk in gk],
+                              stream=stream.cuda_stream)
+        with many:
+            best, secs = many.autotune([1 << 18, 1 << 20, 1 << 21, 1 << 22])
+            many.build_sketches()  # warm
+            torch.cuda.synchronize()
+            t_a = time.perf_counter()
+            many.build_sketches()
+            torch.cuda.synchronize()
+            t_batch = time.perf_counter() - t_a
+            bstats = many.stats()
+        batched = {"graphs": len(gl), "nodes": int(sum(gr.n for gr in gl)), "edges": int(sum(gr.m for gr in gl)),
+                   "batched_build_s": t_batch, "one_graph_at_a_time_s": t_plain, "speedup": t_plain / t_batch,
+                   "autotuned_batch_lanes": best, "autotune_s": [float(x) for x in secs],
+                   "batches": bstats["batches"], "retries": bstats["retries"], "coins": bstats["rev_coins"],
+                   "note": "one-at-a-time includes creating each context (CSR, rank order); batched is the "
+                           "build of the ready union context"}
+
     # end to end through the C ABI with host buffers
     e2e_times = []
     h2d = 8 * g.m + 4 * int(q_off[-1]) + 8 * (len(qs) + 1)
@@ -353,6 +389,7 @@ def main():
             "query_p50_ms": lat[len(lat) // 2], "query_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "single_query_qps": 1000.0 / (sum(lat) / len(lat)),
             "serving": serving,
+            "batched": batched,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -89,6 +89,23 @@ typedef struct skim_ctx skim_ctx;
  * Errors: SKIM_EINVAL, SKIM_EGRAPH, SKIM_ENOMEM, SKIM_ECUDA. */
 int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_ctx **out);
 
+/* Many independent graphs in one context (the batched form): graph g's node
+ * v becomes node off_g + v, off_g = n_0 + ... + n_{g-1}, of a disjoint union
+ * whose sketches are built in one pass of rank-batched searches
+ * (skim_build_sketches; each graph's ranks stay in increasing order inside
+ * the merged order, so Algorithm 2 stays exact per graph).  Every graph keeps
+ * its own keys and probability model (params[g]); l and k must be equal.
+ * graphs[g] are host edge lists.  Queries take union node ids; skim_greedy is
+ * not defined on a batch (SKIM_EINVAL).  Errors as skim_create. */
+int skim_create_batch(const skim_graph *graphs, const skim_params *params, uint32_t count, void *stream,
+                      skim_ctx **out);
+
+/* Autotuner of the rank-batch size: builds the sketches once per candidate
+ * lane count, keeps the fastest for later builds.  best (host) receives it;
+ * seconds (host, optional) the time of each candidate. */
+int skim_autotune_batch_lanes(skim_ctx *ctx, const uint32_t *candidates, uint32_t count, uint32_t *best,
+                              double *seconds);
+
 /* Recompute the rank order of the n*l pairs (done by skim_create; exposed so
  * that a caller can time it).  Restarts SKIM (as skim_greedy_reset); the
  * sketches are unaffected (the ranks themselves do not change). */

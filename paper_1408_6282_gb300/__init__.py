@@ -71,6 +71,8 @@ def load():
     lib.skim_kernel_launches.argtypes = [vp]
     lib.skim_union_estimate_static.argtypes = [vp, vp, u32, u32, u32, vp, u32, vp, vp]
     lib.skim_context_shape.argtypes = [vp, vp, vp, vp]
+    lib.skim_create_batch.argtypes = [vp, vp, u32, vp, C.POINTER(vp)]
+    lib.skim_autotune_batch_lanes.argtypes = [vp, vp, u32, vp, vp]
     lib.skim_server_start.argtypes = [vp, u32, u64, u32, C.POINTER(vp)]
     lib.skim_server_submit.argtypes = [vp, vp, u32, vp]
     lib.skim_server_poll.argtypes = [vp, u64, vp, vp]
@@ -103,6 +105,25 @@ def skim_create(graph: skim_graph, params: skim_params, stream: int = 0) -> int:
     _check(load().skim_create(C.byref(graph), C.byref(params), C.c_void_p(stream or None), C.byref(h)),
            "skim_create")
     return h.value
+
+
+def skim_create_batch(graphs, params, stream: int = 0) -> int:
+    """graphs: sequence of skim_graph (host edge lists), params: sequence of skim_params."""
+    G = (skim_graph * len(graphs))(*graphs)
+    P = (skim_params * len(params))(*params)
+    h = C.c_void_p()
+    _check(load().skim_create_batch(C.cast(G, C.c_void_p), C.cast(P, C.c_void_p), len(graphs),
+                                    C.c_void_p(stream or None), C.byref(h)), "skim_create_batch")
+    return h.value
+
+
+def skim_autotune_batch_lanes(ctx: int, candidates) -> tuple[int, np.ndarray]:
+    cand = np.ascontiguousarray(candidates, dtype=np.uint32)
+    best = np.zeros(1, np.uint32)
+    secs = np.zeros(cand.shape[0], np.float64)
+    _check(load().skim_autotune_batch_lanes(ctx, _ptr(cand), cand.shape[0], _ptr(best), _ptr(secs)),
+           "skim_autotune_batch_lanes")
+    return int(best[0]), secs
 
 
 def skim_rank_order(ctx: int):
@@ -239,6 +260,29 @@ class Skim:
         self.n, self.m, self.l, self.k = n, m, l, k
         self.ctx = skim_create(g, prm, stream)
         self._keep = None
+
+    @classmethod
+    def batch(cls, graphs, l: int, k: int, models, ps, coin_keys, rank_keys, prob_keys, batch_lanes: int = 0,
+              stream: int = 0) -> "Skim":
+        """Many graphs in one context: graphs = [(n, src, dst), ...] (host uint32 arrays)."""
+        keep, gs, prms = [], [], []
+        for (n, src, dst), mdl, p, ck, rk, pk in zip(graphs, models, ps, coin_keys, rank_keys, prob_keys):
+            src = np.ascontiguousarray(src, dtype=np.uint32)
+            dst = np.ascontiguousarray(dst, dtype=np.uint32)
+            keep += [src, dst]
+            m = int(src.shape[0])
+            gs.append(skim_graph(n, m, _ptr(src) if m else None, _ptr(dst) if m else None, 0))
+            prms.append(skim_params(l, k, mdl, p, ck & (2**64 - 1), rk & (2**64 - 1), pk & (2**64 - 1), batch_lanes))
+        self = cls.__new__(cls)
+        self.n = sum(g[0] for g in graphs)
+        self.m = sum(int(g[1].shape[0]) for g in graphs)
+        self.l, self.k = l, k
+        self.ctx = skim_create_batch(gs, prms, stream)
+        self.offsets = np.concatenate([[0], np.cumsum([g[0] for g in graphs])]).astype(np.int64)
+        return self
+
+    def autotune(self, candidates) -> tuple[int, np.ndarray]:
+        return skim_autotune_batch_lanes(self.ctx, candidates)
 
     def close(self):
         if getattr(self, "ctx", None):

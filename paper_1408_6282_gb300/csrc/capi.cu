@@ -35,6 +35,10 @@ struct skim_ctx {
     uint32_t *spair = nullptr;
     void *rank_ws = nullptr;
     uint64_t rank_key = 0;
+    // graphs of a batch (skim_create_batch): per-node rank bases, per-edge
+    // thresholds, node offsets of the graphs
+    uint64_t *rbase = nullptr, *rtm1 = nullptr, *ftm1 = nullptr;
+    uint32_t batch_count = 0;
     // control
     DevCtl *ctl = nullptr;
     DevCtl *hctl = nullptr;  // pinned mirror
@@ -241,6 +245,7 @@ TravArgs base_args(skim_ctx *c, bool forward) {
     a.lane_inst = c->lane_inst;
     a.lane_g = c->lane_g;
     a.he = forward ? c->fhe : c->rhe;
+    a.tm1e = forward ? c->ftm1 : c->rtm1;
     a.full = c->full;
     a.pend = c->pend;
     a.covered = c->covered;
@@ -518,7 +523,7 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
 int rank_order(skim_ctx *c) {
     {
         KTimer kt(c, SKIM_K_RANKS);
-        CK(c, rank_sort(c->rank_key, c->nl, c->srank, c->spair, c->rank_ws, c->st));
+        CK(c, rank_sort(c->rank_key, c->rbase, c->l, c->nl, c->srank, c->spair, c->rank_ws, c->st));
     }
     CK(c, cudaStreamSynchronize(c->st));
     resolve_timers(c);
@@ -590,6 +595,7 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->rhe); dfree(c->fhe);
     dfree(c->srank); dfree(c->spair);
     if (c->rank_ws) cudaFree(c->rank_ws);
+    dfree(c->rbase); dfree(c->rtm1); dfree(c->ftm1);
     dfree(c->ctl); dfree(c->dflag);
     if (c->hctl) cudaFreeHost(c->hctl);
     dfree(c->q); dfree(c->hkeys); dfree(c->hvals); dfree(c->pend);
@@ -788,6 +794,125 @@ fail:
     return rc;
 }
 
+int skim_create_batch(const skim_graph *graphs, const skim_params *prm, uint32_t count, void *stream,
+                      skim_ctx **out) {
+    if (!graphs || !prm || !out || count == 0) return SKIM_EINVAL;
+    *out = nullptr;
+    const uint32_t l = prm[0].l, k = prm[0].k;
+    uint64_t n_tot = 0, m_tot = 0;
+    std::vector<uint32_t> node_off(count + 1, 0);
+    std::vector<uint64_t> ck(count), rk(count), pk(count), tu(count);
+    std::vector<int> model(count);
+    for (uint32_t g = 0; g < count; g++) {
+        const skim_params &p = prm[g];
+        if (graphs[g].on_device) return SKIM_EINVAL;  // host edge lists only
+        if (graphs[g].n == 0 || p.l != l || p.k != k) return SKIM_EINVAL;
+        if (p.prob_model < 0 || p.prob_model > 2) return SKIM_EINVAL;
+        if (p.prob_model == 0 && !(p.p > 0.0 && p.p <= 1.0)) return SKIM_EINVAL;
+        if (graphs[g].m && (!graphs[g].src || !graphs[g].dst)) return SKIM_EINVAL;
+        node_off[g] = static_cast<uint32_t>(n_tot);
+        n_tot += graphs[g].n;
+        m_tot += graphs[g].m;
+        if (n_tot >= (1ull << 32) || m_tot >= (1ull << 32)) return SKIM_ERANGE;
+        ck[g] = p.coin_key;
+        rk[g] = p.rank_key;
+        pk[g] = p.prob_key;
+        model[g] = p.prob_model;
+        tu[g] = p.prob_model == 0 ? tm1_of(p.p) : 0;
+    }
+    node_off[count] = static_cast<uint32_t>(n_tot);
+    // the disjoint union: graph g's node v becomes node_off[g] + v (the
+    // concatenated lists stay sorted)
+    std::vector<uint32_t> us(m_tot), ud(m_tot);
+    uint64_t e = 0;
+    for (uint32_t g = 0; g < count; g++) {
+        for (uint64_t j = 0; j < graphs[g].m; j++, e++) {
+            if (graphs[g].src[j] >= graphs[g].n || graphs[g].dst[j] >= graphs[g].n) return SKIM_EGRAPH;
+            us[e] = graphs[g].src[j] + node_off[g];
+            ud[e] = graphs[g].dst[j] + node_off[g];
+        }
+    }
+    skim_graph ug{static_cast<uint32_t>(n_tot), m_tot, us.data(), ud.data(), 0};
+    skim_params up = prm[0];
+    up.prob_model = 1;  // builds the per-node 1/indeg thresholds; replaced by per-edge thresholds below
+    skim_ctx *c = nullptr;
+    int rc = skim_create(&ug, &up, stream, &c);
+    if (rc) return rc;
+    auto fail = [&](int r) {
+        skim_destroy(c);
+        return r;
+    };
+    // per-graph tables on the device
+    uint32_t *d_off = nullptr, *d_ng = nullptr;
+    uint64_t *d_keys = nullptr;
+    int *d_model = nullptr;
+    if ((rc = dalloc(c, &d_off, count + 1)) || (rc = dalloc(c, &d_ng, n_tot)) || (rc = dalloc(c, &d_keys, 4ull * count)) ||
+        (rc = dalloc(c, &d_model, count)))
+        return fail(rc);
+    std::vector<uint64_t> keys;
+    keys.insert(keys.end(), ck.begin(), ck.end());
+    keys.insert(keys.end(), rk.begin(), rk.end());
+    keys.insert(keys.end(), pk.begin(), pk.end());
+    keys.insert(keys.end(), tu.begin(), tu.end());
+    BatchDesc b{count, d_ng, d_off, d_keys, d_keys + count, d_keys + 2 * count, d_keys + 3 * count, d_model,
+                {tm1_of(0.1), tm1_of(0.01), tm1_of(0.001)}};
+    bool ok = cudaMemcpyAsync(d_off, node_off.data(), (count + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, c->st) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(d_keys, keys.data(), keys.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, c->st) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(d_model, model.data(), count * sizeof(int), cudaMemcpyHostToDevice, c->st) == cudaSuccess &&
+              launch_node_graph(d_off, count, d_ng, c->st) == cudaSuccess;
+    if (ok) {
+        if ((rc = dalloc(c, &c->rbase, n_tot)) || (rc = dalloc(c, &c->rtm1, m_tot)) || (rc = dalloc(c, &c->ftm1, m_tot)))
+            return fail(rc);
+        ok = launch_edge_states_batch(c->rptr, c->rcol, c->n, b, 1, c->rhe, c->st) == cudaSuccess &&
+             launch_edge_states_batch(c->fptr, c->fcol, c->n, b, 0, c->fhe, c->st) == cudaSuccess &&
+             launch_edge_tm1_batch(c->rptr, c->rcol, c->n, b, c->thr_wc, 1, c->rtm1, c->st) == cudaSuccess &&
+             launch_edge_tm1_batch(c->fptr, c->fcol, c->n, b, c->thr_wc, 0, c->ftm1, c->st) == cudaSuccess &&
+             launch_rank_bases(b, c->n, c->l, c->rbase, c->st) == cudaSuccess;
+    }
+    if (ok) ok = cudaStreamSynchronize(c->st) == cudaSuccess;
+    dfree(d_off);
+    dfree(d_ng);
+    dfree(d_keys);
+    dfree(d_model);
+    if (!ok) return fail(fail_cuda(c, cudaGetLastError()));
+    c->cm.model = 3;
+    c->batch_count = count;
+    if ((rc = rank_order(c))) return fail(rc);
+    *out = c;
+    return SKIM_OK;
+}
+
+int skim_autotune_batch_lanes(skim_ctx *c, const uint32_t *candidates, uint32_t count, uint32_t *best,
+                              double *seconds) {
+    if (!c || !candidates || !count || !best) return SKIM_EINVAL;
+    double best_t = 1e300;
+    uint32_t best_b = c->batch_cfg;
+    cudaEvent_t a = nullptr, z = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return fail_cuda(c, cudaGetLastError());
+    int rc = SKIM_OK;
+    for (uint32_t i = 0; i < count && rc == SKIM_OK; i++) {
+        c->batch_cfg = std::max<uint32_t>(64, candidates[i]);
+        cudaEventRecord(a, c->st);
+        rc = skim_build_sketches(c);
+        cudaEventRecord(z, c->st);
+        cudaEventSynchronize(z);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, z);
+        if (seconds) seconds[i] = ms / 1000.0;
+        if (rc == SKIM_OK && ms < best_t) {
+            best_t = ms;
+            best_b = c->batch_cfg;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    c->batch_cfg = best_b;
+    *best = best_b;
+    return rc;
+}
+
 int skim_rank_order(skim_ctx *c) {
     if (!c) return SKIM_EINVAL;
     if (c->broken) return SKIM_ECUDA;
@@ -828,7 +953,7 @@ int skim_build_sketches(skim_ctx *c) {
         bool retry = false;
         RC(rev_batch(c, p0, b, true, &retry));
         if (retry) {
-            B = std::max<uint32_t>(64, b / 2);
+            B = std::max<uint32_t>(64, b / 4);
             continue;
         }
         {
@@ -836,10 +961,15 @@ int skim_build_sketches(skim_ctx *c) {
             CK(c, launch_accept(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->lane_inst, c->srank + p0, c->l,
                                 c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl, c->st));
         }
+        const uint64_t recs = c->bR;
         RC(clear_batch(c));
         p0 += b;
         c->hstats[SKIM_STAT_RANKS] += b;
-        B = std::min<uint32_t>(Bmax, B * 2);
+        // next batch: double, but keep the visit records near a quarter of
+        // the table (dense instances can give thousands of records per lane)
+        const double per_lane = static_cast<double>(recs ? recs : 1) / b;
+        const uint64_t fit = static_cast<uint64_t>(static_cast<double>(c->rcap) / 4.0 / per_lane);
+        B = static_cast<uint32_t>(std::max<uint64_t>(64, std::min<uint64_t>({Bmax, 2ull * B, fit})));
     }
     uint64_t batches = c->hstats[SKIM_STAT_BATCHES], ranks = c->hstats[SKIM_STAT_RANKS],
              retries = c->hstats[SKIM_STAT_RETRIES];
@@ -878,6 +1008,7 @@ int skim_greedy_reset(skim_ctx *c) {
 
 int skim_greedy(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out) {
     if (!c || (n_seeds && (!seeds_out || !cov_out))) return SKIM_EINVAL;
+    if (c->batch_count) return SKIM_EINVAL;  // a batch of graphs has no single seed sequence
     if (c->broken) return SKIM_ECUDA;
     if (!c->sk_init) RC(skim_state_init(c));
     if (static_cast<uint64_t>(c->nseeds) + n_seeds > c->n) return SKIM_EINVAL;

@@ -88,20 +88,25 @@ constexpr int kBucketCap = 4096;     // pairs sorted in shared memory per bucket
 constexpr int kBucketThreads = 512;
 constexpr uint64_t kBucketMean = 1024;  // target mean bucket size
 
-__global__ void k_rank_count(uint64_t rank_key, uint64_t nl, int bb, unsigned long long *cnt) {
+SKIM_DEV uint64_t rank_of(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t x) {
+    return rbase ? fmix(rbase[x / l] + kGolden * (x % l)) : pair_rank(rank_key, x);
+}
+
+__global__ void k_rank_count(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t nl, int bb,
+                             unsigned long long *cnt) {
     for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < nl;
          x += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        uint64_t r = pair_rank(rank_key, x);
+        uint64_t r = rank_of(rank_key, rbase, l, x);
         uint64_t b = bb ? (r >> (64 - bb)) : 0;
         atomicAdd(&cnt[b], 1ull);
     }
 }
 
-__global__ void k_rank_scatter(uint64_t rank_key, uint64_t nl, int bb, const uint64_t *off, unsigned *fill,
-                               uint32_t *tmp) {
+__global__ void k_rank_scatter(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t nl, int bb,
+                               const uint64_t *off, unsigned *fill, uint32_t *tmp) {
     for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < nl;
          x += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        uint64_t r = pair_rank(rank_key, x);
+        uint64_t r = rank_of(rank_key, rbase, l, x);
         uint64_t b = bb ? (r >> (64 - bb)) : 0;
         unsigned p = atomicAdd(&fill[b], 1u);
         tmp[off[b] + p] = static_cast<uint32_t>(x);
@@ -112,9 +117,9 @@ __global__ void k_rank_scatter(uint64_t rank_key, uint64_t nl, int bb, const uin
 // bijection), so a bucket larger than the shared-memory capacity can be
 // placed by counting smaller keys; that path is correct for any size and
 // only its speed depends on the (uniform) bucket sizes.
-__global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(uint64_t rank_key, const uint64_t *off,
-                                                                const uint32_t *tmp, uint64_t *sorted_rank,
-                                                                uint32_t *sorted_pair) {
+__global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(uint64_t rank_key, const uint64_t *rbase, uint32_t l,
+                                                                const uint64_t *off, const uint32_t *tmp,
+                                                                uint64_t *sorted_rank, uint32_t *sorted_pair) {
     __shared__ uint64_t key[kBucketCap];
     __shared__ uint32_t val[kBucketCap];
     const uint64_t b0 = off[blockIdx.x], b1 = off[blockIdx.x + 1];
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(uint64_t rank_ke
             if (i < s) {
                 uint32_t x = tmp[b0 + i];
                 val[i] = x;
-                key[i] = pair_rank(rank_key, x);
+                key[i] = rank_of(rank_key, rbase, l, x);
             } else {
                 key[i] = ~0ull;
                 val[i] = 0;
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(uint64_t rank_ke
         return;
     }
     // oversize bucket: ranks to the output rank slots, then place pairs by count
-    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) sorted_rank[b0 + i] = pair_rank(rank_key, tmp[b0 + i]);
+    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) sorted_rank[b0 + i] = rank_of(rank_key, rbase, l, tmp[b0 + i]);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) {
         uint64_t r = sorted_rank[b0 + i];
@@ -166,7 +171,55 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(uint64_t rank_ke
         sorted_pair[b0 + pos] = tmp[b0 + i];
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) sorted_rank[b0 + i] = pair_rank(rank_key, sorted_pair[b0 + i]);
+    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x)
+        sorted_rank[b0 + i] = rank_of(rank_key, rbase, l, sorted_pair[b0 + i]);
+}
+
+// ---- graphs of a batch -----------------------------------------------------
+__global__ void k_node_graph(const uint32_t *node_off, uint32_t count, uint32_t *node_graph) {
+    for (uint32_t g = blockIdx.x; g < count; g += gridDim.x)
+        for (uint32_t v = node_off[g] + threadIdx.x; v < node_off[g + 1]; v += blockDim.x) node_graph[v] = g;
+}
+
+__global__ void k_edge_states_batch(const uint32_t *ptr, const uint32_t *col, uint32_t n, BatchDesc b, int reverse,
+                                    uint64_t *he) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t g = b.node_graph[v], o = b.node_off[g];
+        for (uint32_t e = ptr[v] + lane; e < ptr[v + 1]; e += 32) {
+            const uint32_t c = col[e] - o, r = v - o;  // ids inside the graph
+            he[e] = reverse ? edge_state(b.coin_key[g], c, r) : edge_state(b.coin_key[g], r, c);
+        }
+    }
+}
+
+__global__ void k_edge_tm1_batch(const uint32_t *ptr, const uint32_t *col, uint32_t n, BatchDesc b,
+                                 const uint64_t *thr_wc, int reverse, uint64_t *tm1) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t g = b.node_graph[v], o = b.node_off[g];
+        const int model = b.model[g];
+        for (uint32_t e = ptr[v] + lane; e < ptr[v + 1]; e += 32) {
+            const uint32_t c = col[e];
+            const uint32_t head = reverse ? v : c;
+            const uint32_t tu = (reverse ? c : v) - o, tv = head - o;  // edge (tu -> tv) inside the graph
+            uint64_t t;
+            if (model == 0)
+                t = b.tm1_uniform[g];
+            else if (model == 1)
+                t = thr_wc[head];
+            else
+                t = b.tm1_class[fmix(b.prob_key[g] ^ ((static_cast<uint64_t>(tu) << 32) | tv)) % 3u];
+            tm1[e] = t;
+        }
+    }
+}
+
+__global__ void k_rank_bases(BatchDesc b, uint32_t n, uint32_t l, uint64_t *rbase) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint32_t g = b.node_graph[v];
+        rbase[v] = b.rank_key[g] + kGolden * (static_cast<uint64_t>(v - b.node_off[g]) * l);
+    }
 }
 
 int bucket_bits(uint64_t nl) {
@@ -226,14 +279,37 @@ cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long lon
     return cudaGetLastError();
 }
 
+cudaError_t launch_node_graph(const uint32_t *node_off, uint32_t count, uint32_t *node_graph, cudaStream_t s) {
+    note_launch();
+    k_node_graph<<<count < 4096 ? count : 4096, 256, 0, s>>>(node_off, count, node_graph);
+    return cudaGetLastError();
+}
+cudaError_t launch_edge_states_batch(const uint32_t *ptr, const uint32_t *col, uint32_t n, const BatchDesc &b,
+                                     int reverse, uint64_t *he, cudaStream_t s) {
+    note_launch();
+    k_edge_states_batch<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(ptr, col, n, b, reverse, he);
+    return cudaGetLastError();
+}
+cudaError_t launch_edge_tm1_batch(const uint32_t *ptr, const uint32_t *col, uint32_t n, const BatchDesc &b,
+                                  const uint64_t *thr_wc, int reverse, uint64_t *tm1, cudaStream_t s) {
+    note_launch();
+    k_edge_tm1_batch<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(ptr, col, n, b, thr_wc, reverse, tm1);
+    return cudaGetLastError();
+}
+cudaError_t launch_rank_bases(const BatchDesc &b, uint32_t n, uint32_t l, uint64_t *rbase, cudaStream_t s) {
+    note_launch();
+    k_rank_bases<<<grid_for(n, 256), 256, 0, s>>>(b, n, l, rbase);
+    return cudaGetLastError();
+}
+
 size_t rank_sort_workspace_bytes(uint64_t nl) {
     uint64_t nb = 1ull << bucket_bits(nl);
     size_t b = (nb + 1) * sizeof(uint64_t) * 2 + nb * sizeof(unsigned) + nl * sizeof(uint32_t);
     return b + scan_workspace_bytes(nb + 1) + 1024;
 }
 
-cudaError_t rank_sort(uint64_t rank_key, uint64_t nl, uint64_t *sorted_rank, uint32_t *sorted_pair, void *ws,
-                      cudaStream_t s) {
+cudaError_t rank_sort(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t nl, uint64_t *sorted_rank,
+                      uint32_t *sorted_pair, void *ws, cudaStream_t s) {
     if (nl == 0) return cudaSuccess;
     const int bb = bucket_bits(nl);
     const uint64_t nb = 1ull << bb;
@@ -248,14 +324,15 @@ cudaError_t rank_sort(uint64_t rank_key, uint64_t nl, uint64_t *sorted_rank, uin
     if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, nb * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_rank_count<<<grid_for(nl, 256), 256, 0, s>>>(rank_key, nl, bb, reinterpret_cast<unsigned long long *>(cnt));
+    k_rank_count<<<grid_for(nl, 256), 256, 0, s>>>(rank_key, rbase, l, nl, bb, reinterpret_cast<unsigned long long *>(cnt));
     // off[b] = exclusive prefix; off[nb] = nl (scan over nb+1 entries with cnt[nb] = 0)
     e = exclusive_scan_u64(cnt, off, nb + 1, nullptr, sws, s);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_rank_scatter<<<grid_for(nl, 256), 256, 0, s>>>(rank_key, nl, bb, off, fill, tmp);
+    k_rank_scatter<<<grid_for(nl, 256), 256, 0, s>>>(rank_key, rbase, l, nl, bb, off, fill, tmp);
     note_launch();
-    k_bucket_sort<<<static_cast<unsigned>(nb), kBucketThreads, 0, s>>>(rank_key, off, tmp, sorted_rank, sorted_pair);
+    k_bucket_sort<<<static_cast<unsigned>(nb), kBucketThreads, 0, s>>>(rank_key, rbase, l, off, tmp, sorted_rank,
+                                                                   sorted_pair);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ namespace skim {
 // Live-edge threshold model (Section 6: uniform p, weighted cascade 1/indeg,
 // trivalency classes).
 struct CoinModel {
-    int model;            // 0 uniform, 1 weighted cascade, 2 trivalency
+    int model;            // 0 uniform, 1 weighted cascade, 2 trivalency, 3 per-edge thresholds (many graphs)
     uint64_t tm1_uniform;  // floor(p * 2^64) - 1
     uint64_t tm1_class[3];
     const uint64_t *thr_wc;  // per node: floor((2^64-1) / indeg(node))
@@ -40,6 +40,7 @@ struct TravArgs {
     const uint8_t *lane_inst;   // instance of every lane of the batch
     const uint64_t *lane_g;     // per lane: (instance + 1) * G, the lane's coin-stream offset
     const uint64_t *he;         // per CSR edge: state of its coin stream, fmix(coin_key ^ (u << 32 | v))
+    const uint64_t *tm1e;       // per CSR edge: live threshold (model 3)
     const uint64_t *full;       // Algorithm 2 pruning: instances whose local sketch holds k ranks
     int prune;
     uint64_t *pend;             // per table slot: lane bits whose expansion was spilled
@@ -70,9 +71,28 @@ cudaError_t launch_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_
 cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out, cudaStream_t s);
 
 // Rank order of all pairs: bucket by the top bits, then sort each bucket.
+// rank of pair x = v*l+i is fmix(rank_key + G*x), or fmix(rbase[v] + G*i)
+// when a per-node base is given (graphs of a batch, each with its own key).
 size_t rank_sort_workspace_bytes(uint64_t nl);
-cudaError_t rank_sort(uint64_t rank_key, uint64_t nl, uint64_t *sorted_rank, uint32_t *sorted_pair, void *ws,
-                      cudaStream_t s);
+cudaError_t rank_sort(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t nl, uint64_t *sorted_rank,
+                      uint32_t *sorted_pair, void *ws, cudaStream_t s);
+
+// Graphs of a batch (a disjoint union): per-graph keys and models, node ->
+// graph, and the per-node / per-edge tables derived from them.
+struct BatchDesc {
+    uint32_t count;
+    const uint32_t *node_graph;  // per node
+    const uint32_t *node_off;    // per graph: first node
+    const uint64_t *coin_key, *rank_key, *prob_key, *tm1_uniform;  // per graph
+    const int *model;            // per graph: 0 uniform, 1 wc, 2 trivalency
+    uint64_t tm1_class[3];       // trivalency thresholds for p = 0.1, 0.01, 0.001
+};
+cudaError_t launch_node_graph(const uint32_t *node_off, uint32_t count, uint32_t *node_graph, cudaStream_t s);
+cudaError_t launch_edge_states_batch(const uint32_t *ptr, const uint32_t *col, uint32_t n, const BatchDesc &b,
+                                     int reverse, uint64_t *he, cudaStream_t s);
+cudaError_t launch_edge_tm1_batch(const uint32_t *ptr, const uint32_t *col, uint32_t n, const BatchDesc &b,
+                                  const uint64_t *thr_wc, int reverse, uint64_t *tm1, cudaStream_t s);
+cudaError_t launch_rank_bases(const BatchDesc &b, uint32_t n, uint32_t l, uint64_t *rbase, cudaStream_t s);
 
 // traverse.cu
 cudaError_t launch_rev_sources(const TravArgs &a, const uint32_t *lane_pair, uint32_t B, uint32_t l,

@@ -28,12 +28,18 @@ namespace {
 constexpr int kTravThreads = 256;
 constexpr int kMaxProbe = 4096;
 
-SKIM_DEV uint64_t edge_tm1_rev(const CoinModel &cm, uint32_t u, uint32_t v, uint64_t tm1_head) {
+// Live threshold of CSR edge idx = (u -> v); tm1_head is the item's value
+// for the models whose threshold depends on the head node only.
+SKIM_DEV uint64_t edge_tm1_rev(const TravArgs &A, uint32_t idx, uint32_t u, uint32_t v, uint64_t tm1_head) {
+    const CoinModel &cm = A.cm;
+    if (cm.model == 3) return A.tm1e[idx];
     if (cm.model == 2) return cm.tm1_class[fmix(cm.prob_key ^ ((static_cast<uint64_t>(u) << 32) | v)) % 3u];
     return tm1_head;
 }
 
-SKIM_DEV uint64_t edge_tm1_fwd(const CoinModel &cm, uint32_t u, uint32_t w) {
+SKIM_DEV uint64_t edge_tm1_fwd(const TravArgs &A, uint32_t idx, uint32_t u, uint32_t w) {
+    const CoinModel &cm = A.cm;
+    if (cm.model == 3) return A.tm1e[idx];
     if (cm.model == 0) return cm.tm1_uniform;
     if (cm.model == 1) return cm.thr_wc[w];
     return cm.tm1_class[fmix(cm.prob_key ^ ((static_cast<uint64_t>(u) << 32) | w)) % 3u];
@@ -338,9 +344,10 @@ SKIM_DEV uint64_t edge_key(const TravArgs &A, const Desc &d, uint32_t idx, uint3
 // Live lanes (reverse) or instances (forward) of an edge with other end x
 // and coin-stream state he.
 template <bool FWD>
-SKIM_DEV uint64_t edge_live_xh(const TravArgs &A, const Desc &d, uint32_t x, uint64_t he, const uint64_t *ginst) {
-    if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A.cm, d.v, x), ginst);
-    const uint64_t t1 = edge_tm1_rev(A.cm, x, d.v, d.tm1);
+SKIM_DEV uint64_t edge_live_xh(const TravArgs &A, const Desc &d, uint32_t idx, uint32_t x, uint64_t he,
+                               const uint64_t *ginst) {
+    if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A, idx, d.v, x), ginst);
+    const uint64_t t1 = edge_tm1_rev(A, idx, x, d.v, d.tm1);
     if (d.single) return fmix(he + d.g1) <= t1 ? d.mask : 0;
     return live_lanes(he, d.mask, t1, A.lane_g + static_cast<size_t>(d.w >> kChunkBits) * 64);
 }
@@ -350,8 +357,8 @@ SKIM_DEV uint64_t edge_live(const TravArgs &A, const Desc &d, uint32_t idx, uint
     const uint32_t x = A.col[idx];
     const uint64_t he = edge_key<FWD>(A, d, idx, x);
     *tgt = x;
-    if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A.cm, d.v, x), ginst);
-    const uint64_t t1 = edge_tm1_rev(A.cm, x, d.v, d.tm1);
+    if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A, idx, d.v, x), ginst);
+    const uint64_t t1 = edge_tm1_rev(A, idx, x, d.v, d.tm1);
     if (d.single) return fmix(he + d.g1) <= t1 ? d.mask : 0;
     return live_lanes(he, d.mask, t1, A.lane_g + static_cast<size_t>(d.w >> kChunkBits) * 64);
 }
@@ -453,7 +460,7 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
                 uint64_t lv[kUnroll] = {0};
                 uint32_t tg[kUnroll] = {0};
                 if (k < b.cnt) {
-                    lv[0] = edge_live_xh<FWD>(A, b, x, h, ginst);
+                    lv[0] = edge_live_xh<FWD>(A, b, b.begin + k, x, h, ginst);
                     tg[0] = x;
                 }
                 if (__any_sync(kFull, lv[0] != 0)) emit_step<FWD>(A, acc, b, lv, tg);

@@ -1,0 +1,55 @@
+"""Many graphs in one context: every graph's slice of the sketches equals the
+oracle's sketches of that graph alone (its own keys and probability model)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs(count, seed):
+    ks = synth.Keys.from_seed(seed)
+    h = synth.stream(ks.graph, 4 * count)
+    out = []
+    for g in range(count):
+        scale = 6 + int(h[4 * g] % np.uint64(5))
+        ef = 4 + int(h[4 * g + 1] % np.uint64(12))
+        gr = synth.rmat(scale, ef, int(h[4 * g + 2]))
+        model = int(h[4 * g + 3] % np.uint64(3))
+        out.append((gr, model, 0.05 + 0.1 * (g % 3)))
+    return out
+
+
+@pytest.mark.parametrize("bl", [0, 256])
+def test_batch_matches_each_graph_alone(bl):
+    import paper_1408_6282_gb300 as pkg
+    from paper_1408_6282_gb300 import build as b
+    b.build()
+    gs = _graphs(12, 31)
+    l, k = 16, 8
+    keys = [synth.Keys.from_seed(100 + g) for g in range(len(gs))]
+    sk = pkg.Skim.batch([(gr.n, gr.src, gr.dst) for gr, _, _ in gs], l, k, [m for _, m, _ in gs],
+                        [p for _, _, p in gs], [kk.coin for kk in keys], [kk.rank for kk in keys],
+                        [kk.prob for kk in keys], batch_lanes=bl)
+    with sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        for g, ((gr, model, p), kk) in enumerate(zip(gs, keys)):
+            pb = oracle.Problem(gr.n, gr.src, gr.dst, l, k, model, p, kk.coin, kk.rank, kk.prob)
+            ox, oln, _ = oracle.build_sketches(pb)
+            o = sk.offsets[g]
+            assert np.array_equal(ln[o:o + gr.n], oln), g
+            assert np.array_equal(x[o:o + gr.n], ox), g
+            # a query inside graph g uses union ids
+            q = np.arange(0, gr.n, 5, dtype=np.uint32)
+            ref = oracle.union_estimate(ox, oln, l, q)
+            assert abs(sk.query(q + o) - ref) <= 1e-12 * max(1.0, abs(ref))
+        with pytest.raises(pkg.SkimError):
+            sk.greedy(1)
+        best, secs = sk.autotune([64, 1024, 1 << 16])
+        assert best in (64, 1024, 1 << 16) and np.all(secs > 0)
+        sk.build_sketches()
+        x2, ln2 = sk.sketches()
+        assert np.array_equal(x2, x) and np.array_equal(ln2, ln)
