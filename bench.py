@@ -282,6 +282,27 @@ def main():
         lat.append((time.perf_counter() - a) * 1000.0)
     lat.sort()
 
+    # adaptive error estimation (Section 4.3.2) for the step's seed set: the
+    # same SKIM run with each selection's threshold rank and k' recorded
+    # (untimed), then the confidence bound on the summed discrepancy
+    sk.greedy_reset()
+    a = time.perf_counter()
+    sseeds, scov, stau, skp = sk.greedy_stops(w.seeds)
+    t_stops = time.perf_counter() - a
+    assert sseeds.tolist() == gold["skim"]["seeds"]
+    if "tau" in gold["skim"]:
+        assert [str(int(t)) for t in stau] == gold["skim"]["tau"]
+        assert [int(x) for x in skp] == gold["skim"]["kprime"]
+    tot = float(scov.sum())
+    conf = [0.5, 0.9, 0.99]
+    a = time.perf_counter()
+    bnd, _ = pkg.discrepancy_bound(scov, stau, skp, tot / 1024, 4096, conf)
+    adaptive = {"seed_set_pairs": int(tot), "confidence": conf,
+                "discrepancy_bound_pairs": [float(b) for b in bnd],
+                "relative_to_seed_set": [float(b) / tot for b in bnd],
+                "exact_selections": int((skp < 0).sum()), "greedy_with_records_s": t_stops,
+                "bound_host_s": time.perf_counter() - a}
+
     # serving: Poisson query streams replayed through the continuous-batching
     # server on the same resident sketches, against the one-query-at-a-time form
     serving = []
@@ -390,6 +411,7 @@ def main():
             "single_query_qps": 1000.0 / (sum(lat) / len(lat)),
             "serving": serving,
             "batched": batched,
+            "adaptive_error": adaptive,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -136,6 +136,40 @@ int skim_sketch_pointers(skim_ctx *ctx, const uint64_t **x_dev, const uint32_t *
  * Errors: SKIM_EINVAL if the total would exceed n. */
 int skim_greedy(skim_ctx *ctx, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out);
 
+/* skim_greedy plus what each selection saw, for adaptive error estimation
+ * (Section 4.3.2).  For the j-th new seed, tau_out[j] is the threshold rank:
+ * the 64-bit rank whose reverse search made the seed's partial sketch reach k
+ * (read as tau * 2^-64), and kprime_out[j] is k', the largest partial sketch
+ * size among all other nodes once that rank is taken out (k' <= k - 1).  When
+ * the ranks have run out the seed comes from exact residual counts: then
+ * tau_out[j] = 0 and kprime_out[j] = -1.  Either output may be NULL; with both
+ * NULL this is skim_greedy.  Recording costs three small kernels per seed and
+ * device arrays of 12 * n_seeds bytes for the call.  Errors as skim_greedy. */
+int skim_greedy_ex(skim_ctx *ctx, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out, uint64_t *tau_out,
+                   int32_t *kprime_out);
+
+/* Confidence bound on the sum of discrepancies of a SKIM run (Section 4.3.2,
+ * Eq. chernoff); host-only FP64, no context, no GPU.  The discrepancy of
+ * iteration j is the gap, in node-instance pairs, between the largest
+ * marginal coverage in that residual problem and delta[j], the coverage of
+ * the seed selected.  With mu = tau_j (delta_j + d) (tau_j = tau[j] * 2^-64)
+ * and nu = 1 - k'_j / mu, P[D_j > d] <= B_j(d) = (e^-nu / (1-nu)^(1-nu))^mu,
+ * or 1 where mu <= k'_j; kprime[j] = -1 is a point mass at 0.  Each D_j is
+ * rounded up to the grid {0, step, 2 step, ...} of `bins` cells, with the mass
+ * past the last cell held in an overflow cell that counts as unbounded; the
+ * sum's bound is the convolution over j.
+ * Inputs (host): delta, tau, kprime as written by skim_greedy_ex (s entries);
+ * step > 0 in pairs; bins >= 1; conf[c] in (0, 1).
+ * Outputs (host): bound_out[c] = the smallest grid value b with
+ * P[sum > b] <= 1 - conf[c] (pairs; +inf if only the overflow cell would do);
+ * ccdf_out (may be NULL, bins + 1 entries): ccdf_out[i] bounds P[sum > i step]
+ * for i < bins, ccdf_out[bins] is the overflow mass.
+ * Errors: SKIM_EINVAL for a null array that is needed, step <= 0 or not
+ * finite, bins = 0, a confidence outside (0, 1), or kprime[j] < -1. */
+int skim_discrepancy_bound(uint32_t s, const uint64_t *delta, const uint64_t *tau, const int32_t *kprime,
+                           double step, uint32_t bins, uint32_t n_conf, const double *conf, double *bound_out,
+                           double *ccdf_out);
+
 /* Restart SKIM from the empty seed set (drops covered pairs and the index). */
 int skim_greedy_reset(skim_ctx *ctx);
 
@@ -177,7 +211,10 @@ int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
  *   SKIM_K_STEP  SKIM per-node steps (first-to-k candidates, commits)
  *   SKIM_K_RANKS rank order of the n*l pairs
  *   SKIM_K_QUERY union-estimator queries
- *   SKIM_K_SETUP CSR construction and validation */
+ *   SKIM_K_SETUP CSR construction and validation
+ * Turning timing on creates a pool of 2048 CUDA events at once (so that no
+ * event is created inside a timed bracket).  A bracket that holds a host
+ * synchronisation (SKIM_K_STEP) also counts the host's share of that wait. */
 #define SKIM_K_REV 0
 #define SKIM_K_FWD 1
 #define SKIM_K_ACCEPT 2

@@ -49,7 +49,18 @@ def _load():
         common = g + [C.c_uint32, C.c_uint32, C.c_int, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64]
         _lib.or_sketch_of_node.argtypes = common + [C.c_uint32, u64p, u32p, u64p]
         _lib.or_build_sketches.argtypes = common + [u64p, u32p, u64p]
-        _lib.or_skim.argtypes = common + [C.c_uint32, u32p, u64p, u32p, u64p]
+        _lib.or_skim.argtypes = common + [C.c_uint32, u32p, u64p, u32p, u64p, u64p, C.POINTER(C.c_int32)]
+        _lib.or_skim_mode.argtypes = common + [C.c_uint32, u32p, u64p, u32p, u64p, u64p, C.POINTER(C.c_int32),
+                                               C.c_int]
+        _lib.or_build_sketches_mode.argtypes = common + [u64p, u32p, u64p, C.c_int]
+        _lib.or_build_ic_sketches.argtypes = g + [C.c_uint32, C.c_int, C.c_double, C.c_uint64, C.c_uint64,
+                                                  C.c_uint64, u64p, u32p, u64p]
+        _lib.or_perm_positions.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, u64p]
+        _lib.or_ic_nodes.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, u32p]
+        _lib.or_union_estimate_mode.argtypes = [u64p, u32p, C.c_uint32, C.c_uint32, C.c_uint32, u32p, C.c_uint32,
+                                                C.c_int, C.POINTER(C.c_double)]
+        _lib.or_node_estimates.argtypes = [u64p, u32p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
+                                           C.POINTER(C.c_double)]
         _lib.or_exact_coverage.argtypes = g + [C.c_uint32, C.c_int, C.c_double, C.c_uint64, C.c_uint64,
                                                u32p, C.c_uint32, u64p]
         est = [u64p, u32p, C.c_uint32, C.c_uint32, C.c_uint32, u32p, C.c_uint32, C.POINTER(C.c_double)]
@@ -122,13 +133,39 @@ def sketch_of_node(pb: Problem, u: int):
     return x[: int(ln[0])].copy(), int(reach[0])
 
 
-def build_sketches(pb: Problem):
-    """Algorithm 2: all combined sketches. Returns (X[n,k], len[n], counters)."""
+def build_sketches(pb: Problem, rank_mode: int = 0):
+    """Algorithm 2: all combined sketches. Returns (X[n,k], len[n], counters).
+    rank_mode 0: uniform 64-bit ranks; 1: structured permutation positions."""
     x = np.zeros((pb.n, pb.k), np.uint64)
     ln = np.zeros(pb.n, np.uint32)
     cnt = np.zeros(NCOUNT, np.uint64)
-    _check(_load().or_build_sketches(*pb._common(), _p64(x), _p32(ln), _p64(cnt)), "build_sketches")
+    _check(_load().or_build_sketches_mode(*pb._common(), _p64(x), _p32(ln), _p64(cnt), rank_mode),
+           "build_sketches")
     return x, ln, dict(zip(COUNTER_NAMES, (int(c) for c in cnt)))
+
+
+def build_ic_sketches(pb: Problem):
+    """IC-model sketches (Section 3.2; pb.l is not used): X[n,k] of positions."""
+    x = np.zeros((pb.n, pb.k), np.uint64)
+    ln = np.zeros(pb.n, np.uint32)
+    cnt = np.zeros(NCOUNT, np.uint64)
+    _check(_load().or_build_ic_sketches(*pb._g(), pb.k, pb.model, pb.p, pb.coin_key, pb.rank_key, pb.prob_key,
+                                        _p64(x), _p32(ln), _p64(cnt)), "build_ic_sketches")
+    return x, ln, dict(zip(COUNTER_NAMES, (int(c) for c in cnt)))
+
+
+def perm_positions(n: int, l: int, rank_key: int) -> np.ndarray:
+    """Structured permutation (Section 3.1): position of pair (v,i) at [v*l+i]."""
+    pos = np.zeros(n * l, np.uint64)
+    _check(_load().or_perm_positions(n, l, rank_key, _p64(pos)), "perm_positions")
+    return pos
+
+
+def ic_nodes(n: int, chunks: int, rank_key: int) -> np.ndarray:
+    """Node at each IC-model position t < chunks * n."""
+    out = np.zeros(n * chunks, np.uint32)
+    _check(_load().or_ic_nodes(n, chunks, rank_key, _p32(out)), "ic_nodes")
+    return out
 
 
 def skim(pb: Problem, n_seeds: int):
@@ -137,8 +174,25 @@ def skim(pb: Problem, n_seeds: int):
     cov = np.zeros(n_seeds, np.uint64)
     size = np.zeros(pb.n, np.uint32)
     cnt = np.zeros(NCOUNT, np.uint64)
-    _check(_load().or_skim(*pb._common(), n_seeds, _p32(seeds), _p64(cov), _p32(size), _p64(cnt)), "skim")
+    _check(_load().or_skim(*pb._common(), n_seeds, _p32(seeds), _p64(cov), _p32(size), _p64(cnt), None, None), "skim")
     return seeds, cov, size, dict(zip(COUNTER_NAMES, (int(c) for c in cnt)))
+
+
+def skim_stops(pb: Problem, n_seeds: int, rank_mode: int = 0):
+    """Algorithm 1 with what each iteration's selection saw (Section 4.3.2):
+    seeds, coverages, the threshold rank tau of the search that stopped (as the
+    64-bit rank; 0 when the ranks ran out), and k', the largest sketch size
+    among the other nodes without that rank (-1 when the ranks ran out and the
+    selection used exact residual counts).  rank_mode 1 orders the pairs by
+    the structured permutation (Section 3.1); tau is then a position."""
+    seeds = np.zeros(n_seeds, np.uint32)
+    cov = np.zeros(n_seeds, np.uint64)
+    tau = np.zeros(n_seeds, np.uint64)
+    kp = np.zeros(n_seeds, np.int32)
+    cnt = np.zeros(NCOUNT, np.uint64)
+    _check(_load().or_skim_mode(*pb._common(), n_seeds, _p32(seeds), _p64(cov), None, _p64(cnt), _p64(tau),
+                                kp.ctypes.data_as(C.POINTER(C.c_int32)), rank_mode), "skim")
+    return seeds, cov, tau, kp, dict(zip(COUNTER_NAMES, (int(c) for c in cnt)))
 
 
 def exact_coverage(pb: Problem, seeds) -> np.ndarray:
@@ -150,15 +204,26 @@ def exact_coverage(pb: Problem, seeds) -> np.ndarray:
     return out[: s.shape[0]]
 
 
-def union_estimate(x: np.ndarray, ln: np.ndarray, l: int, seeds) -> float:
-    """Eq. unionest divided by l (the influence estimate)."""
+def union_estimate(x: np.ndarray, ln: np.ndarray, l: int, seeds, rank_mode: int = 0) -> float:
+    """Eq. unionest divided by l (the influence estimate); rank_mode 1/2 read
+    positions as Sections 3.1/3.2 say."""
     x = np.ascontiguousarray(x, dtype=np.uint64)
     ln = np.ascontiguousarray(ln, dtype=np.uint32)
     s = np.ascontiguousarray(seeds, dtype=np.uint32)
     out = C.c_double()
-    _check(_load().or_union_estimate(_p64(x), _p32(ln), x.shape[0], x.shape[1], l, _p32(s),
-                                     s.shape[0], C.byref(out)), "union_estimate")
+    _check(_load().or_union_estimate_mode(_p64(x), _p32(ln), x.shape[0], x.shape[1], l, _p32(s),
+                                          s.shape[0], rank_mode, C.byref(out)), "union_estimate")
     return out.value
+
+
+def node_estimates(x: np.ndarray, ln: np.ndarray, l: int, rank_mode: int = 0) -> np.ndarray:
+    """Single-node influence estimates from each node's own sketch."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    ln = np.ascontiguousarray(ln, dtype=np.uint32)
+    out = np.zeros(x.shape[0], np.float64)
+    _check(_load().or_node_estimates(_p64(x), _p32(ln), x.shape[0], x.shape[1], l, rank_mode,
+                                     out.ctypes.data_as(C.POINTER(C.c_double))), "node_estimates")
+    return out
 
 
 def bottomk_union_estimate(x: np.ndarray, ln: np.ndarray, l: int, seeds) -> float:

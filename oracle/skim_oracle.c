@@ -15,7 +15,9 @@
  *   - SKIM, Algorithm 1, step by step, with the tie rules stated at skim(),
  *   - the Cohen-Kaplan union estimator (Eq. unionest) and the bottom-k
  *     estimator of the union (Section 5.1),
- *   - exact influence by forward BFS (Eq. InfbinaryIC).
+ *   - exact influence by forward BFS (Eq. InfbinaryIC),
+ *   - structured permutation ranks (Section 3.1) for the sketches and SKIM,
+ *     IC-model sketches (Section 3.2), and their estimators.
  *
  * Parity status: every function is pinned by tests against brute force on
  * tiny graphs, closed forms or invariants; none is "parity unpinned".
@@ -79,9 +81,9 @@ static uint64_t edge_tm1(const graph_t *g, uint32_t u, uint32_t v) {
 
 /* Live-edge coin for directed edge (u,v) in instance i: the (i+1)-th output of
  * the SplitMix64 stream whose state is fmix(coin_key ^ edge_id). */
-static int live(const graph_t *g, uint32_t u, uint32_t v, uint32_t i) {
+static int live(const graph_t *g, uint32_t u, uint32_t v, uint64_t i) {
     uint64_t he = fmix(g->coin_key ^ (((uint64_t)u << 32) | v));
-    uint64_t c = fmix(he + GOLDEN * (uint64_t)(i + 1));
+    uint64_t c = fmix(he + GOLDEN * (i + 1));
     return c <= edge_tm1(g, u, v);
 }
 
@@ -217,19 +219,89 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Structured permutation ranks (Section 3.1).  Positions are 0-based (the    */
+/* paper's permutation rank T is the position plus one).  Chunk c holds        */
+/* positions c*n .. c*n + n - 1 and every node exactly once, ordered by the    */
+/* key w(v,c) = fmix(K_w + GOLDEN*(c*n + v)), K_w = fmix(rank_key ^ PERM_SALT).*/
+/* In the instance model the node's pair in chunk c is (v, sigma_v(c)), where  */
+/* sigma_v lists node v's instances by increasing r(v,i): each chunk draws an  */
+/* instance uniformly among those v has not used yet.  In the IC model         */
+/* (Section 3.2) position t has a fresh instance of its own, numbered t.       */
+/* ------------------------------------------------------------------------ */
+static const uint64_t PERM_SALT = 0x7065726d75746531ULL;
+
+static uint64_t perm_key(uint64_t rank_key) { return fmix(rank_key ^ PERM_SALT); }
+
+/* nodes of chunk c in position order */
+static void chunk_nodes(uint32_t n, uint64_t c, uint64_t kw, kv_t *buf, uint32_t *out) {
+    for (uint32_t v = 0; v < n; v++) {
+        buf[v].key = fmix(kw + GOLDEN * (c * n + v));
+        buf[v].val = v;
+    }
+    qsort(buf, n, sizeof(kv_t), cmp_kv);
+    for (uint32_t j = 0; j < n; j++) out[j] = buf[j].val;
+}
+
+/* pos_out[v*l + i] = position of pair (v,i) among all n*l */
+int or_perm_positions(uint32_t n, uint32_t l, uint64_t rank_key, uint64_t *pos_out) {
+    if (n == 0 || l == 0 || l > 255) return OR_EINVAL;
+    kv_t *buf = malloc((size_t)(n > l ? n : l) * sizeof(kv_t));
+    uint8_t *sigma = malloc((size_t)n * l);
+    uint32_t *nodes = malloc((size_t)n * sizeof(uint32_t));
+    if (!buf || !sigma || !nodes) { free(buf); free(sigma); free(nodes); return OR_ENOMEM; }
+    for (uint32_t v = 0; v < n; v++) {
+        for (uint32_t i = 0; i < l; i++) { buf[i].key = or_rank(rank_key, l, v, i); buf[i].val = i; }
+        qsort(buf, l, sizeof(kv_t), cmp_kv);
+        for (uint32_t c = 0; c < l; c++) sigma[(size_t)v * l + c] = (uint8_t)buf[c].val;
+    }
+    const uint64_t kw = perm_key(rank_key);
+    for (uint32_t c = 0; c < l; c++) {
+        chunk_nodes(n, c, kw, buf, nodes);
+        for (uint32_t j = 0; j < n; j++) {
+            uint32_t v = nodes[j];
+            pos_out[(size_t)v * l + sigma[(size_t)v * l + c]] = (uint64_t)c * n + j;
+        }
+    }
+    free(buf); free(sigma); free(nodes);
+    return OR_OK;
+}
+
+/* node_out[t] = node at IC-model position t, for t < chunks * n */
+int or_ic_nodes(uint32_t n, uint32_t chunks, uint64_t rank_key, uint32_t *node_out) {
+    if (n == 0) return OR_EINVAL;
+    kv_t *buf = malloc((size_t)n * sizeof(kv_t));
+    if (!buf) return OR_ENOMEM;
+    const uint64_t kw = perm_key(rank_key);
+    for (uint32_t c = 0; c < chunks; c++) chunk_nodes(n, c, kw, buf, node_out + (size_t)c * n);
+    free(buf);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Algorithm 2: for each instance i, process the pairs (u,i) by increasing    */
 /* rank; reverse BFS from u in G(i); a scanned node whose local sketch holds  */
 /* k ranks is pruned, otherwise the rank joins its local sketch.  After the   */
 /* instance, every local sketch is merged into the global one and trimmed to  */
 /* k, then cleared (Section 5.2).                                             */
 /* ------------------------------------------------------------------------ */
-int or_build_sketches(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
-                      uint32_t l, uint32_t k, int model, double p,
-                      uint64_t coin_key, uint64_t rank_key, uint64_t prob_key,
-                      uint64_t *x_out, uint32_t *len_out, uint64_t *counters) {
+/* rank_mode 0: uniform 64-bit ranks r(v,i); 1: structured permutation
+ * positions (every pair is processed; positions past min(k,l)*n simply never
+ * survive the merge). */
+int or_build_sketches_mode(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
+                           uint32_t l, uint32_t k, int model, double p,
+                           uint64_t coin_key, uint64_t rank_key, uint64_t prob_key,
+                           uint64_t *x_out, uint32_t *len_out, uint64_t *counters, int rank_mode) {
+    if (rank_mode != 0 && rank_mode != 1) return OR_EINVAL;
     graph_t g;
     int rc = graph_init(&g, n, m, src, dst, l, k, model, p, coin_key, rank_key, prob_key);
     if (rc) return rc;
+    uint64_t *pos = NULL;
+    if (rank_mode == 1) {
+        pos = malloc((size_t)n * l * sizeof(uint64_t));
+        if (!pos) { graph_free(&g); return OR_ENOMEM; }
+        rc = or_perm_positions(n, l, rank_key, pos);
+        if (rc) { free(pos); graph_free(&g); return rc; }
+    }
     uint64_t cnt[OR_NCOUNT] = {0};
     kv_t *order = malloc((size_t)n * sizeof(kv_t));
     uint64_t *local = malloc((size_t)n * k * sizeof(uint64_t));
@@ -242,7 +314,10 @@ int or_build_sketches(uint32_t n, uint64_t m, const uint32_t *src, const uint32_
     uint32_t bfs_id = 0;
     for (uint32_t i = 0; i < l; i++) {
         /* pairs of instance i by increasing rank */
-        for (uint32_t u = 0; u < n; u++) { order[u].key = or_rank(rank_key, l, u, i); order[u].val = u; }
+        for (uint32_t u = 0; u < n; u++) {
+            order[u].key = pos ? pos[(size_t)u * l + i] : or_rank(rank_key, l, u, i);
+            order[u].val = u;
+        }
         qsort(order, n, sizeof(kv_t), cmp_kv);
         for (uint32_t t = 0; t < n; t++) {
             uint32_t u = order[t].val;
@@ -282,7 +357,65 @@ int or_build_sketches(uint32_t n, uint64_t m, const uint32_t *src, const uint32_
     }
     if (counters) memcpy(counters, cnt, sizeof(cnt));
 done:
-    free(order); free(local); free(llen); free(stamp); free(queue); free(merged);
+    free(order); free(local); free(llen); free(stamp); free(queue); free(merged); free(pos);
+    graph_free(&g);
+    return rc;
+}
+
+int or_build_sketches(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
+                      uint32_t l, uint32_t k, int model, double p,
+                      uint64_t coin_key, uint64_t rank_key, uint64_t prob_key,
+                      uint64_t *x_out, uint32_t *len_out, uint64_t *counters) {
+    return or_build_sketches_mode(n, m, src, dst, l, k, model, p, coin_key, rank_key, prob_key,
+                                  x_out, len_out, counters, 0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* IC-model sketches (Section 3.2): the limit of infinitely many instances.   */
+/* Position t (t < k*n; every node reaches itself, so after k chunks each     */
+/* sketch is full) has its own instance G_t; its rank t joins the sketch of    */
+/* every node that reaches node(t) in G_t, while that sketch has fewer than k  */
+/* entries.  Positions arrive in increasing order, so sketches stay sorted.   */
+/* No search is pruned: a node that is full in G_t says nothing about its     */
+/* in-neighbours in G_t.                                                      */
+/* ------------------------------------------------------------------------ */
+int or_build_ic_sketches(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
+                         uint32_t k, int model, double p,
+                         uint64_t coin_key, uint64_t rank_key, uint64_t prob_key,
+                         uint64_t *x_out, uint32_t *len_out, uint64_t *counters) {
+    graph_t g;
+    int rc = graph_init(&g, n, m, src, dst, 1, k, model, p, coin_key, rank_key, prob_key);
+    if (rc) return rc;
+    uint64_t cnt[OR_NCOUNT] = {0};
+    const uint64_t npos = (uint64_t)k * n;
+    uint32_t *node = malloc(npos * sizeof(uint32_t));
+    uint32_t *stamp = calloc(n, sizeof(uint32_t));
+    uint32_t *queue = malloc((size_t)n * sizeof(uint32_t));
+    if (!node || !stamp || !queue) { rc = OR_ENOMEM; goto done; }
+    rc = or_ic_nodes(n, k, rank_key, node);
+    if (rc) goto done;
+    for (uint32_t v = 0; v < n; v++) len_out[v] = 0;
+    uint32_t bfs_id = 0;
+    for (uint64_t t = 0; t < npos; t++) {
+        cnt[5]++; cnt[6]++;
+        bfs_id++;
+        if (bfs_id == 0) { memset(stamp, 0, (size_t)n * sizeof(uint32_t)); bfs_id = 1; }
+        uint32_t head = 0, tail = 0;
+        queue[tail++] = node[t]; stamp[node[t]] = bfs_id;
+        while (head < tail) {
+            uint32_t v = queue[head++];
+            if (len_out[v] < k) { x_out[(size_t)v * k + len_out[v]++] = t; cnt[2]++; }
+            cnt[0]++;
+            cnt[1] += g.rptr[v + 1] - g.rptr[v];
+            for (uint64_t e = g.rptr[v]; e < g.rptr[v + 1]; e++) {
+                uint32_t w = g.rcol[e];
+                if (stamp[w] != bfs_id && live(&g, w, v, t)) { stamp[w] = bfs_id; queue[tail++] = w; }
+            }
+        }
+    }
+    if (counters) memcpy(counters, cnt, sizeof(cnt));
+done:
+    free(node); free(stamp); free(queue);
     graph_free(&g);
     return rc;
 }
@@ -348,11 +481,13 @@ static int cmp_kv12(const void *a, const void *b) {
 /*  - the rank cursor resumes after the rank that produced the seed.          */
 /* Outputs seeds[j] and the integer marginal coverage cov[j] = l * I_j.       */
 /* ------------------------------------------------------------------------ */
-int or_skim(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
-            uint32_t l, uint32_t k, int model, double p,
-            uint64_t coin_key, uint64_t rank_key, uint64_t prob_key,
-            uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out,
-            uint32_t *size_out, uint64_t *counters) {
+int or_skim_mode(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
+                 uint32_t l, uint32_t k, int model, double p,
+                 uint64_t coin_key, uint64_t rank_key, uint64_t prob_key,
+                 uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out,
+                 uint32_t *size_out, uint64_t *counters,
+                 uint64_t *tau_out, int32_t *kprime_out, int rank_mode) {
+    if (rank_mode != 0 && rank_mode != 1) return OR_EINVAL;
     graph_t g;
     int rc = graph_init(&g, n, m, src, dst, l, k, model, p, coin_key, rank_key, prob_key);
     if (rc) return rc;
@@ -378,10 +513,20 @@ int or_skim(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
         goto done;
     }
 
-    /* "shuffle the nl pairs": increasing rank order */
-    for (uint64_t x = 0; x < nl; x++) {
-        order[x].key = or_rank(rank_key, l, (uint32_t)(x / l), (uint32_t)(x % l));
-        order[x].val = (uint32_t)x;
+    /* "shuffle the nl pairs": increasing rank order (uniform ranks, or the
+     * structured permutation's positions, Section 3.1) */
+    if (rank_mode == 1) {
+        uint64_t *pos = malloc(nl * sizeof(uint64_t));
+        if (!pos) { rc = OR_ENOMEM; goto done; }
+        rc = or_perm_positions(n, l, rank_key, pos);
+        for (uint64_t x = 0; x < nl && !rc; x++) { order[x].key = pos[x]; order[x].val = (uint32_t)x; }
+        free(pos);
+        if (rc) goto done;
+    } else {
+        for (uint64_t x = 0; x < nl; x++) {
+            order[x].key = or_rank(rank_key, l, (uint32_t)(x / l), (uint32_t)(x % l));
+            order[x].val = (uint32_t)x;
+        }
     }
     qsort(order, nl, sizeof(kv12_t), cmp_kv12);
 
@@ -422,7 +567,27 @@ int or_skim(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
                 }
             }
         }
+        if (x >= 0) {
+            /* Section 4.3.2 (adaptive error estimation): the threshold rank of
+             * this iteration is the rank whose search stopped, and k' is the
+             * largest sketch size among the other nodes once that rank is
+             * taken out again (it is not part of any sketch for this count):
+             * size[v] minus one for every v its search visited (stamp). */
+            if (tau_out) tau_out[sidx] = order[rank - 1].key;
+            if (kprime_out) {
+                int32_t kp = 0;
+                for (uint32_t v = 0; v < n; v++) {
+                    if (v == (uint32_t)x) continue;
+                    int32_t sz = (int32_t)size[v] - (stamp[v] == bfs_id ? 1 : 0);
+                    if (sz > kp) kp = sz;
+                }
+                kprime_out[sidx] = kp;
+            }
+        }
         if (x < 0) {
+            /* selection from exact residual counts: no estimation error */
+            if (tau_out) tau_out[sidx] = 0;
+            if (kprime_out) kprime_out[sidx] = -1;
             /* ranks exhausted: node with the largest partial sketch */
             uint32_t best = 0;
             for (uint32_t v = 1; v < n; v++) if (size[v] > size[best]) best = v;
@@ -467,6 +632,16 @@ done:
     free(ix_start); free(ix_len); free(nodes);
     graph_free(&g);
     return rc;
+}
+
+int or_skim(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
+            uint32_t l, uint32_t k, int model, double p,
+            uint64_t coin_key, uint64_t rank_key, uint64_t prob_key,
+            uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out,
+            uint32_t *size_out, uint64_t *counters,
+            uint64_t *tau_out, int32_t *kprime_out) {
+    return or_skim_mode(n, m, src, dst, l, k, model, p, coin_key, rank_key, prob_key, n_seeds, seeds_out,
+                        cov_out, size_out, counters, tau_out, kprime_out, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -546,5 +721,96 @@ int or_bottomk_union_estimate(const uint64_t *x, const uint32_t *len, uint32_t n
     else est = (double)(k - 1) / ldexp((double)all[k - 1], -64);
     free(all);
     *est_out = est / (double)l;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Estimators for permutation ranks (Sections 3.1, 3.2 and 5.1).             */
+/* A sketch holds positions; a full sketch's threshold is its k-th smallest   */
+/* position, T - 1 in the paper's 1-based numbering.                          */
+/*  rank_mode 1 (D = n*l pairs): the union estimator of Eq. unionest reads    */
+/*    the threshold position q as the uniform rank q / (D - 1), so a rank      */
+/*    charged to it adds (D - 1) / q; a sketch that is not full has           */
+/*    threshold 1 and adds 1 per rank; the sum is divided by l.              */
+/*  rank_mode 2 (IC model): the limit l -> infinity of the same: a rank       */
+/*    charged to threshold q adds n / q, and one charged to a sketch that is  */
+/*    not full adds nothing.                                                  */
+/* Thresholds are compared as integers (not full = larger than any).          */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint64_t thr; uint32_t node; uint32_t pos; } qsort_t;
+static int cmp_thr_desc(const void *a, const void *b) {
+    uint64_t x = ((const qsort_t *)a)->thr, y = ((const qsort_t *)b)->thr;
+    if (x != y) return x > y ? -1 : 1;
+    uint32_t p = ((const qsort_t *)a)->pos, q = ((const qsort_t *)b)->pos;
+    return p < q ? -1 : p > q;
+}
+
+static double perm_term(uint64_t thr, int rank_mode, uint32_t n, uint32_t l) {
+    if (thr == UINT64_MAX) return rank_mode == 2 ? 0.0 : 1.0;
+    if (rank_mode == 2) return (double)n / (double)thr;
+    return (double)((uint64_t)n * l - 1) / (double)thr;
+}
+
+int or_union_estimate_mode(const uint64_t *x, const uint32_t *len, uint32_t n, uint32_t k,
+                           uint32_t l, const uint32_t *seeds, uint32_t s, int rank_mode, double *est_out) {
+    if (rank_mode == 0) return or_union_estimate(x, len, n, k, l, seeds, s, est_out);
+    if (rank_mode != 1 && rank_mode != 2) return OR_EINVAL;
+    if (s == 0) { *est_out = 0.0; return OR_OK; }
+    qsort_t *ts = malloc((size_t)s * sizeof(qsort_t));
+    uint64_t cap = 1; while (cap < 2ull * s * k + 2) cap <<= 1;
+    uint64_t *seen = calloc(cap, sizeof(uint64_t));   /* z+1, 0 empty */
+    if (!ts || !seen) { free(ts); free(seen); return OR_ENOMEM; }
+    for (uint32_t j = 0; j < s; j++) {
+        if (seeds[j] >= n) { free(ts); free(seen); return OR_EINVAL; }
+        ts[j].node = seeds[j]; ts[j].pos = j;
+        ts[j].thr = len[seeds[j]] == k ? x[(size_t)seeds[j] * k + k - 1] : UINT64_MAX;
+    }
+    qsort(ts, s, sizeof(qsort_t), cmp_thr_desc);
+    double sum = 0.0;
+    for (uint32_t j = 0; j < s; j++) {
+        uint32_t u = ts[j].node, lu = len[u];
+        const uint64_t *xu = x + (size_t)u * k;
+        uint32_t cnt = lu == k ? k - 1 : lu;
+        const double term = perm_term(ts[j].thr, rank_mode, n, l);
+        for (uint32_t t = 0; t < cnt; t++) {
+            uint64_t z = xu[t];
+            uint64_t h = fmix(z) & (cap - 1);
+            int fresh = 1;
+            while (seen[h]) {
+                if (seen[h] == z + 1) { fresh = 0; break; }
+                h = (h + 1) & (cap - 1);
+            }
+            if (fresh) { seen[h] = z + 1; sum += term; }
+        }
+    }
+    *est_out = rank_mode == 2 ? sum : sum / (double)l;
+    free(ts); free(seen);
+    return OR_OK;
+}
+
+/* Influence estimate of every single node from its own sketch:
+ *  rank_mode 0: (k - 1) / tau_u with tau_u = h * 2^-64 (Section 3), or |X_u|
+ *    when the sketch is not full; divided by l.
+ *  rank_mode 1: the unbiased permutation estimator 1 + (k-1)(D-1)/(T-1)
+ *    (Section 3.1), T - 1 = the k-th smallest position, or |X_u| when not
+ *    full; divided by l.
+ *  rank_mode 2: n (k - 1) / (T - 1) (Section 3.2); 0 when not full. */
+int or_node_estimates(const uint64_t *x, const uint32_t *len, uint32_t n, uint32_t k,
+                      uint32_t l, int rank_mode, double *out) {
+    if (rank_mode < 0 || rank_mode > 2) return OR_EINVAL;
+    for (uint32_t u = 0; u < n; u++) {
+        const uint32_t lu = len[u];
+        double e;
+        if (lu < k) {
+            e = rank_mode == 2 ? 0.0 : (double)lu / (double)l;
+        } else {
+            const uint64_t q = x[(size_t)u * k + k - 1];
+            if (rank_mode == 0) e = (double)(k - 1) / ldexp((double)q, -64) / (double)l;
+            else if (rank_mode == 1)
+                e = (1.0 + (double)(k - 1) * (double)((uint64_t)n * l - 1) / (double)q) / (double)l;
+            else e = (double)n * (double)(k - 1) / (double)q;
+        }
+        out[u] = e;
+    }
     return OR_OK;
 }

@@ -61,6 +61,8 @@ def load():
     lib.skim_sketch_pointers.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
     lib.skim_greedy.argtypes = [vp, u32, vp, vp]
     lib.skim_greedy_reset.argtypes = [vp]
+    lib.skim_greedy_ex.argtypes = [vp, u32, vp, vp, vp, vp]
+    lib.skim_discrepancy_bound.argtypes = [u32, vp, vp, vp, C.c_double, u32, u32, vp, vp, vp]
     lib.skim_oracle_query.argtypes = [vp, vp, u32, vp]
     lib.skim_oracle_query_batch.argtypes = [vp, vp, u32, vp, vp, C.c_int]
     lib.skim_get_stats.argtypes = [vp, vp, u32]
@@ -154,6 +156,34 @@ def skim_sketch_pointers(ctx: int) -> tuple[int, int]:
 
 def skim_greedy(ctx: int, n_seeds: int, seeds_out: np.ndarray, cov_out: np.ndarray):
     _check(load().skim_greedy(ctx, n_seeds, _ptr(seeds_out), _ptr(cov_out)), "skim_greedy")
+
+
+def skim_greedy_ex(ctx: int, n_seeds: int, seeds_out, cov_out, tau_out=None, kprime_out=None):
+    _check(load().skim_greedy_ex(ctx, n_seeds, _ptr(seeds_out), _ptr(cov_out),
+                                 _ptr(tau_out) if tau_out is not None else None,
+                                 _ptr(kprime_out) if kprime_out is not None else None), "skim_greedy_ex")
+
+
+def skim_discrepancy_bound(s: int, delta, tau, kprime, step: float, bins: int, n_conf: int, conf, bound_out,
+                           ccdf_out=None):
+    _check(load().skim_discrepancy_bound(s, _ptr(delta) if s else None, _ptr(tau) if s else None,
+                                         _ptr(kprime) if s else None, step, bins, n_conf,
+                                         _ptr(conf) if n_conf else None, _ptr(bound_out) if n_conf else None,
+                                         _ptr(ccdf_out) if ccdf_out is not None else None),
+           "skim_discrepancy_bound")
+
+
+def discrepancy_bound(delta, tau, kprime, step: float, bins: int = 4096, conf=(0.9, 0.95, 0.99)):
+    """Section 4.3.2 bound on the sum of discrepancies of a SKIM run (pairs):
+    returns (bounds per confidence, ccdf over the grid plus the overflow)."""
+    d = np.ascontiguousarray(delta, dtype=np.uint64)
+    t = np.ascontiguousarray(tau, dtype=np.uint64)
+    kp = np.ascontiguousarray(kprime, dtype=np.int32)
+    cf = np.ascontiguousarray(conf, dtype=np.float64)
+    out = np.zeros(max(1, cf.shape[0]), np.float64)
+    ccdf = np.zeros(bins + 1, np.float64)
+    skim_discrepancy_bound(int(d.shape[0]), d, t, kp, float(step), int(bins), int(cf.shape[0]), cf, out, ccdf)
+    return out[: cf.shape[0]], ccdf
 
 
 def skim_greedy_reset(ctx: int):
@@ -315,6 +345,14 @@ class Skim:
         cov = np.zeros(max(1, n_seeds), np.uint64)
         skim_greedy(self.ctx, n_seeds, seeds, cov)
         return seeds[:n_seeds], cov[:n_seeds]
+
+    def greedy_stops(self, n_seeds: int):
+        """greedy() plus each selection's threshold rank and k' (Section 4.3.2)."""
+        m = max(1, n_seeds)
+        seeds, cov = np.zeros(m, np.uint32), np.zeros(m, np.uint64)
+        tau, kp = np.zeros(m, np.uint64), np.zeros(m, np.int32)
+        skim_greedy_ex(self.ctx, n_seeds, seeds, cov, tau, kp)
+        return seeds[:n_seeds], cov[:n_seeds], tau[:n_seeds], kp[:n_seeds]
 
     def greedy_reset(self):
         skim_greedy_reset(self.ctx)

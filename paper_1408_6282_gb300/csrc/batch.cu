@@ -191,6 +191,26 @@ __global__ void k_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, u
     }
 }
 
+// Section 4.3.2: add delta to the size of every node in the committed index
+// list of lane p (each node appears once in a lane's list).
+__global__ void k_lane_size_add(const uint32_t *idx_nodes, uint64_t idx_base, const uint64_t *lane_off,
+                                const uint64_t *lane_cnt, uint32_t p, uint32_t *size, int delta) {
+    const uint64_t off = idx_base + lane_off[p], cnt = lane_cnt[p];
+    for (uint64_t j = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; j < cnt;
+         j += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        size[idx_nodes[off + j]] += static_cast<uint32_t>(delta);
+}
+
+// k' of Section 4.3.2: the largest size among nodes other than x.
+__global__ void k_max_size_except(const uint32_t *size, uint32_t n, uint32_t x, uint32_t *out) {
+    uint32_t best = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (v != x) best = max(best, size[v]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_down_sync(kFull, best, o));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
+}
+
 __global__ void k_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl) {
     unsigned long long best = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
@@ -280,6 +300,19 @@ cudaError_t launch_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, 
 cudaError_t launch_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl, cudaStream_t s) {
     note_launch();
     k_argmax_size<<<grid_for(n, 256), 256, 0, s>>>(size, n, ctl);
+    return cudaGetLastError();
+}
+cudaError_t launch_second_size(const uint32_t *idx_nodes, uint64_t idx_base, const uint64_t *lane_off,
+                               const uint64_t *lane_cnt, uint32_t p, uint32_t *size, uint32_t n, uint32_t x,
+                               uint32_t *out, cudaStream_t s) {
+    // the stop lane's list holds at most n nodes (its length is on the device)
+    const unsigned g = grid_for(n, 256, 1024);
+    note_launch();
+    k_lane_size_add<<<g, 256, 0, s>>>(idx_nodes, idx_base, lane_off, lane_cnt, p, size, -1);
+    note_launch();
+    k_max_size_except<<<grid_for(n, 256), 256, 0, s>>>(size, n, x, out);
+    note_launch();
+    k_lane_size_add<<<g, 256, 0, s>>>(idx_nodes, idx_base, lane_off, lane_cnt, p, size, 1);
     return cudaGetLastError();
 }
 cudaError_t launch_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl, cudaStream_t s) {

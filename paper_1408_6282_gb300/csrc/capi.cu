@@ -83,6 +83,11 @@ struct skim_ctx {
     uint64_t since_stop = 0, last_gap = 0;
     double vpl_est = 0;  // visit records per lane of the last SKIM batch
     uint32_t last_B = 0;
+    // Section 4.3.2 records of the current skim_greedy_ex call (device):
+    // per seed the threshold rank and k'; null when not asked for
+    uint64_t *rec_tau = nullptr;
+    uint32_t *rec_kp = nullptr;
+    uint32_t rec_j = 0;
     // queries
     uint64_t *qk = nullptr, *qv = nullptr;
     uint64_t qtcap = 0;
@@ -447,7 +452,14 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
             if (best != ~0ull) {
                 const uint32_t p = static_cast<uint32_t>(best >> 32);
                 const uint32_t x = static_cast<uint32_t>(best & 0xffffffffu);
+                const uint64_t idx_base = c->idx_used;
                 RC(commit_lanes(c, c->blo, p));
+                if (c->rec_tau) {
+                    CK(c, cudaMemcpyAsync(c->rec_tau + c->rec_j, c->srank + c->bp0 + p, sizeof(uint64_t),
+                                          cudaMemcpyDeviceToDevice, c->st));
+                    CK(c, launch_second_size(c->idx, idx_base, c->lane_off, c->lane_cnt, p, c->size, c->n, x,
+                                             c->rec_kp + c->rec_j, c->st));
+                }
                 RC(residual(c, x, cov_out));
                 {
                     const uint64_t after = c->bB - 1 - p;  // batch lanes not yet consumed
@@ -513,6 +525,10 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
             CK(c, launch_min_unchosen(c->chosen, c->n, c->ctl, c->st));
             RC(sync_ctl(c));
             x = static_cast<uint32_t>(c->hctl->best);
+        }
+        if (c->rec_tau) {  // exact residual counts: recorded as k' = -1, tau = 0
+            CK(c, cudaMemsetAsync(c->rec_kp + c->rec_j, 0xff, sizeof(uint32_t), c->st));
+            CK(c, cudaMemsetAsync(c->rec_tau + c->rec_j, 0, sizeof(uint64_t), c->st));
         }
         RC(residual(c, x, cov_out));
         *x_out = x;
@@ -605,6 +621,7 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->lcnt); dfree(c->full); dfree(c->X); dfree(c->xlen);
     dfree(c->covered); dfree(c->seg_start); dfree(c->pend_trav); dfree(c->pend_erase);
     dfree(c->size); dfree(c->seg_len); dfree(c->idx); dfree(c->chosen);
+    dfree(c->rec_tau); dfree(c->rec_kp);
     dfree(c->qk); dfree(c->qv); dfree(c->qseeds); dfree(c->qoff); dfree(c->qout);
     dfree(c->qtop); dfree(c->qtopu);
     if (c->qpart) cudaFree(c->qpart);
@@ -1006,20 +1023,54 @@ int skim_greedy_reset(skim_ctx *c) {
     return skim_state_init(c);
 }
 
-int skim_greedy(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out) {
+namespace {
+
+int greedy_loop(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out) {
+    for (uint32_t j = 0; j < n_seeds; j++) {
+        uint32_t x = 0;
+        uint64_t cov = 0;
+        c->rec_j = j;
+        RC(next_seed(c, &x, &cov));
+        seeds_out[j] = x;
+        cov_out[j] = cov;
+        c->nseeds++;
+    }
+    return SKIM_OK;
+}
+
+}  // namespace
+
+int skim_greedy_ex(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out, uint64_t *tau_out,
+                   int32_t *kprime_out) {
     if (!c || (n_seeds && (!seeds_out || !cov_out))) return SKIM_EINVAL;
     if (c->batch_count) return SKIM_EINVAL;  // a batch of graphs has no single seed sequence
     if (c->broken) return SKIM_ECUDA;
     if (!c->sk_init) RC(skim_state_init(c));
     if (static_cast<uint64_t>(c->nseeds) + n_seeds > c->n) return SKIM_EINVAL;
     RC(reset_stats(c));
-    for (uint32_t j = 0; j < n_seeds; j++) {
-        uint32_t x = 0;
-        uint64_t cov = 0;
-        RC(next_seed(c, &x, &cov));
-        seeds_out[j] = x;
-        cov_out[j] = cov;
-        c->nseeds++;
+    if ((tau_out || kprime_out) && n_seeds) {
+        RC(dalloc(c, &c->rec_tau, n_seeds));
+        int rc = dalloc(c, &c->rec_kp, n_seeds);
+        if (rc == SKIM_OK) {
+            CK(c, cudaMemsetAsync(c->rec_kp, 0, n_seeds * sizeof(uint32_t), c->st));
+            rc = greedy_loop(c, n_seeds, seeds_out, cov_out);
+        }
+        if (rc == SKIM_OK) {
+            std::vector<uint64_t> t(n_seeds);
+            std::vector<uint32_t> kp(n_seeds);
+            CK(c, cudaMemcpyAsync(t.data(), c->rec_tau, n_seeds * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->st));
+            CK(c, cudaMemcpyAsync(kp.data(), c->rec_kp, n_seeds * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+            CK(c, cudaStreamSynchronize(c->st));
+            for (uint32_t j = 0; j < n_seeds; j++) {
+                if (tau_out) tau_out[j] = t[j];
+                if (kprime_out) kprime_out[j] = static_cast<int32_t>(kp[j]);
+            }
+        }
+        dfree(c->rec_tau);
+        dfree(c->rec_kp);
+        RC(rc);
+    } else {
+        RC(greedy_loop(c, n_seeds, seeds_out, cov_out));
     }
     uint64_t keep[3] = {c->hstats[SKIM_STAT_BATCHES], c->hstats[SKIM_STAT_RANKS], c->hstats[SKIM_STAT_RETRIES]};
     RC(pull_stats(c));
@@ -1027,6 +1078,10 @@ int skim_greedy(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *co
     c->hstats[SKIM_STAT_RANKS] = keep[1];
     c->hstats[SKIM_STAT_RETRIES] = keep[2];
     return SKIM_OK;
+}
+
+int skim_greedy(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out) {
+    return skim_greedy_ex(c, n_seeds, seeds_out, cov_out, nullptr, nullptr);
 }
 
 int skim_oracle_query_batch(skim_ctx *c, const uint64_t *offsets, uint32_t q, const uint32_t *seeds, double *est_out,
@@ -1093,6 +1148,14 @@ int skim_kernel_launches(uint64_t *out) {
 int skim_set_timing(skim_ctx *c, int on) {
     if (!c) return SKIM_EINVAL;
     c->timing = on != 0;
+    // create the events up front: creating them inside a timed bracket would
+    // leave the GPU waiting on the host there
+    const size_t want = 2048;
+    while (c->timing && c->kpool.size() + c->kpend.size() * 2 < want) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return fail_cuda(c, cudaGetLastError());
+        c->kpool.push_back(e);
+    }
     return SKIM_OK;
 }
 

@@ -129,6 +129,11 @@ cudaError_t launch_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, 
                             uint64_t *alive, cudaStream_t s);
 cudaError_t launch_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl, cudaStream_t s);
 cudaError_t launch_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl, cudaStream_t s);
+// Section 4.3.2: k' = max size over v != x with the stop lane p taken out
+// (sizes are restored); atomicMax into *out, which the caller zeroes.
+cudaError_t launch_second_size(const uint32_t *idx_nodes, uint64_t idx_base, const uint64_t *lane_off,
+                               const uint64_t *lane_cnt, uint32_t p, uint32_t *size, uint32_t n, uint32_t x,
+                               uint32_t *out, cudaStream_t s);
 
 // query.cu
 // Scratch of the multi-block query path: hash tables (total_slots keys and

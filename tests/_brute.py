@@ -127,3 +127,33 @@ def union_estimate_exact(sketches: list[list[int]], k: int) -> Fraction:
             if z not in best or t > best[z]:
                 best[z] = t
     return sum((1 / t for t in best.values()), Fraction(0))
+
+
+# ---- structured permutation ranks (Section 3.1) and IC-model positions ------
+
+PERM_SALT = 0x7065726d75746531
+
+
+def _chunk_order(n: int, c: int, kw: int) -> list[int]:
+    return sorted(range(n), key=lambda v: fmix(kw + G * (c * n + v)))
+
+
+def perm_positions(n: int, l: int, rank_key: int) -> dict[tuple[int, int], int]:
+    """Position of every pair (v, i): chunk c lists each node once, in the order
+    of its key for that chunk, paired with the node's c-th instance in the
+    order of the pair ranks r(v, i)."""
+    kw = fmix(rank_key ^ PERM_SALT)
+    sigma = {v: sorted(range(l), key=lambda i: rank(rank_key, l, v, i)) for v in range(n)}
+    pos = {}
+    for c in range(l):
+        for j, v in enumerate(_chunk_order(n, c, kw)):
+            pos[(v, sigma[v][c])] = c * n + j
+    return pos
+
+
+def ic_nodes(n: int, chunks: int, rank_key: int) -> list[int]:
+    kw = fmix(rank_key ^ PERM_SALT)
+    out = []
+    for c in range(chunks):
+        out += _chunk_order(n, c, kw)
+    return out

@@ -4,7 +4,8 @@ For a named workload this runs the oracle once and stores, in
 ``tests/golden/<workload>.json``:
   - the sha256 of the generated graph (so a changed generator is caught),
   - the sha256 of all combined sketches (Algorithm 2) and a few sampled rows,
-  - the SKIM seed sequence and integer marginal coverages (Algorithm 1),
+  - the SKIM seed sequence and integer marginal coverages (Algorithm 1), with
+    each selection's threshold rank and k' (Section 4.3.2),
   - influence-oracle estimates (Eq. unionest) for seeded uniform query sets,
   - the oracle's sequential work counters (edge-instance traversals).
 No value here comes from the GPU path.
@@ -85,9 +86,10 @@ def main():
         s = args.seeds if args.seeds is not None else w.seeds
         if s:
             t = time.time()
-            seeds, cov, _, cnt = oracle.skim(pb, s)
+            seeds, cov, tau, kp, cnt = oracle.skim_stops(pb, s)
             dt = time.time() - t
             res["skim"] = {"n_seeds": s, "seeds": seeds.tolist(), "cov": [int(c) for c in cov],
+                           "tau": [str(int(x)) for x in tau], "kprime": [int(x) for x in kp],
                            "counters": cnt, "oracle_seconds": dt}
             print(f"[{w.name}] skim {s} seeds {dt:.1f}s {cnt}", flush=True)
     json.dump(res, open(out_path + ".tmp", "w"), indent=1)

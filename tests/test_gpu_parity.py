@@ -77,10 +77,11 @@ def test_small_graphs_sketches_skim_queries(pkg, name, mk, l, k, model, p, bl):
         assert np.array_equal(ln, oln)
         assert np.array_equal(x, ox)
         s = min(g.n, 25)
-        seeds, cov = sk.greedy(s)
-        os_, oc, _, _ = oracle.skim(pb, s)
+        seeds, cov, tau, kp = sk.greedy_stops(s)
+        os_, oc, otau, okp, _ = oracle.skim_stops(pb, s)
         assert np.array_equal(seeds, os_), (seeds, os_)
         assert np.array_equal(cov, oc)
+        assert np.array_equal(tau, otau) and np.array_equal(kp, okp)  # Section 4.3.2 records
         rng = np.random.default_rng(5)
         sets = [[], [0], list(seeds[:3]), rng.integers(0, g.n, 10).tolist(), list(range(g.n))]
         single = [sk.query(q) for q in sets]
@@ -96,12 +97,14 @@ def test_skim_full_permutation_and_resume(pkg, bl):
     pb, sk = _both(pkg, g, 8, 6, 1, 0.0, 21, bl)
     with sk:
         a, ca = sk.greedy(7)
-        b, cb = sk.greedy(g.n - 7)  # continues the sequence to exhaustion
+        b, cb, tb, kb = sk.greedy_stops(g.n - 7)  # continues the sequence to exhaustion
         seeds = np.concatenate([a, b])
         cov = np.concatenate([ca, cb])
-        os_, oc, _, _ = oracle.skim(pb, g.n)
+        os_, oc, otau, okp, _ = oracle.skim_stops(pb, g.n)
         assert np.array_equal(seeds, os_)
         assert np.array_equal(cov, oc)
+        assert np.array_equal(tb, otau[7:]) and np.array_equal(kb, okp[7:])
+        assert okp[-1] == -1  # the tail comes from exact residual counts
         assert sorted(seeds.tolist()) == list(range(g.n))
         sk.greedy_reset()
         c, cc = sk.greedy(10)
@@ -118,9 +121,7 @@ def test_er4096_workload(pkg):
         sk.build_sketches()
         x, ln = sk.sketches()
         assert _digest(x, ln) == gold["sketches"]["sha256"]
-        seeds, cov = sk.greedy(w.seeds)
-        assert seeds.tolist() == gold["skim"]["seeds"]
-        assert [int(c) for c in cov] == gold["skim"]["cov"]
+        _check_skim(sk, gold["skim"], w.seeds)
         for q in gold["queries"]:
             assert _close(sk.query(q["seeds"]), q["estimate"])
 
@@ -135,9 +136,10 @@ def test_rmat_midsize(pkg, scale, model, p):
         x, ln = sk.sketches()
         ox, oln, _ = oracle.build_sketches(pb)
         assert np.array_equal(ln, oln) and np.array_equal(x, ox)
-        seeds, cov = sk.greedy(40)
-        os_, oc, _, _ = oracle.skim(pb, 40)
+        seeds, cov, tau, kp = sk.greedy_stops(40)
+        os_, oc, otau, okp, _ = oracle.skim_stops(pb, 40)
         assert np.array_equal(seeds, os_) and np.array_equal(cov, oc)
+        assert np.array_equal(tau, otau) and np.array_equal(kp, okp)
         pre = oracle.exact_coverage(pb, seeds)
         assert np.array_equal(np.cumsum(cov), pre)
 
@@ -176,9 +178,17 @@ def test_rmat20_wc_full_size(pkg):
         est = sk.query_batch([q["seeds"] for q in gold["queries"]])
         for q, e in zip(gold["queries"], est):
             assert _close(float(e), q["estimate"])
-        seeds, cov = sk.greedy(w.seeds)
-        assert seeds.tolist() == gold["skim"]["seeds"]
-        assert [int(c) for c in cov] == gold["skim"]["cov"]
+        _check_skim(sk, gold["skim"], w.seeds)
+
+
+def _check_skim(sk, gs, s):
+    """Seeds and coverages, and the Section 4.3.2 records where stored."""
+    seeds, cov, tau, kp = sk.greedy_stops(s)
+    assert seeds.tolist() == gs["seeds"]
+    assert [int(c) for c in cov] == gs["cov"]
+    if "tau" in gs:
+        assert [str(int(t)) for t in tau] == gs["tau"]
+        assert [int(x) for x in kp] == gs["kprime"]
 
 
 def test_rmat22_wc_sketches_full_size(pkg):
@@ -209,9 +219,7 @@ def test_rmat24_p01_skim_full_size(pkg):
     assert g.digest() == gold["graph_sha256"]
     ks = w.keys()
     with pkg.Skim(g.n, g.src, g.dst, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob) as sk:
-        seeds, cov = sk.greedy(w.seeds)
-        assert seeds.tolist() == gold["skim"]["seeds"]
-        assert [int(c) for c in cov] == gold["skim"]["cov"]
+        _check_skim(sk, gold["skim"], w.seeds)
 
 
 def test_query_sum_is_correctly_rounded(pkg):
