@@ -68,7 +68,22 @@ typedef struct {
  *   rank_key   rank of pair (v,i) is fmix(rank_key + (v*l+i)*G), read as
  *              a real in [0,1) after scaling by 2^-64 (ranks never tie);
  *   prob_key   trivalency class of edge (u,v): fmix(prob_key ^ (u<<32|v)) % 3;
- *   batch_lanes  ranks per batched search, 0 = automatic. */
+ *   batch_lanes  ranks per batched search, 0 = automatic;
+ *   rank_mode  SKIM_RANKS_*: how the pairs are ordered and what a sketch holds.
+ *     SKIM_RANKS_UNIFORM (0): the uniform 64-bit ranks above.
+ *     SKIM_RANKS_PERMUTATION (1): structured permutation ranks (Section 3.1).
+ *       Positions 0..n*l-1 (the paper's T is the position plus one) come in
+ *       l chunks of n; chunk c lists every node once, ordered by
+ *       w(v,c) = fmix(K_w + (c*n+v)*G), K_w = fmix(rank_key ^ 0x7065726d75746531),
+ *       and pairs node v with its (c+1)-th instance in the order of the ranks
+ *       r(v,i) above.  Sketches hold positions; Algorithm 2 processes only the
+ *       first min(k,l)*n positions (no later one can enter a sketch).
+ *     SKIM_RANKS_IC_MODEL (2): IC-model sketches (Section 3.2), the limit of
+ *       infinitely many instances: requires l = 1; position t < k*n (same
+ *       chunk order, k chunks) has a fresh instance of its own whose coins use
+ *       t in place of i; searches are not pruned.  SKIM is not available.
+ *   Queries read a position threshold q as the uniform rank q/(n*l-1)
+ *   (mode 1) or estimate n/q per rank (mode 2); see skim_oracle_query. */
 typedef struct {
     uint32_t l;
     uint32_t k;
@@ -78,7 +93,12 @@ typedef struct {
     uint64_t rank_key;
     uint64_t prob_key;
     uint32_t batch_lanes;
+    uint32_t rank_mode;
 } skim_params;
+
+#define SKIM_RANKS_UNIFORM 0
+#define SKIM_RANKS_PERMUTATION 1
+#define SKIM_RANKS_IC_MODEL 2
 
 typedef struct skim_ctx skim_ctx;
 
@@ -177,8 +197,23 @@ int skim_greedy_reset(skim_ctx *ctx);
  * estimator): estimate of Inf(S) = |union of R_u, u in S| / l from the
  * sketches of S.  seeds (host), n_seeds >= 0; duplicates allowed; the empty
  * set gives 0.  The sum is formed exactly in fixed point and rounded once, so
- * the result does not depend on summation order.  est_out (host). */
+ * the result does not depend on summation order.  est_out (host).
+ * With SKIM_RANKS_PERMUTATION a threshold position q (k-th smallest of a full
+ * sketch) reads as the uniform rank q/(n*l-1), so each rank charged to it adds
+ * (n*l-1)/q (Section 5.1's permutation version); with SKIM_RANKS_IC_MODEL the
+ * estimate is the l -> infinity limit: n/q per rank, nothing for a rank whose
+ * largest threshold belongs to a sketch that is not full, no division by l. */
 int skim_oracle_query(skim_ctx *ctx, const uint32_t *seeds, uint32_t n_seeds, double *est_out);
+
+/* Influence estimate of every single node from its own sketch (out[v], n
+ * doubles; host memory, or device memory if out_on_device):
+ *   SKIM_RANKS_UNIFORM: (k-1)/tau_v / l, tau_v = h * 2^-64 (Section 3);
+ *   SKIM_RANKS_PERMUTATION: (1 + (k-1)(n*l-1)/q) / l, the estimator of
+ *     Section 3.1 with T - 1 = q the k-th smallest position;
+ *   SKIM_RANKS_IC_MODEL: n (k-1) / q (Section 3.2);
+ * and |X_v| / l (0 in the IC model) when the sketch is not full.
+ * Errors: SKIM_EINVAL, SKIM_ENOTBUILT. */
+int skim_node_estimates(skim_ctx *ctx, double *out, int out_on_device);
 
 /* Batched form of skim_oracle_query: q queries given in CSR form.
  * offsets[q+1] (host), seeds[offsets[q]] (host|device per on_device),

@@ -20,6 +20,7 @@ SKIM_OK = 0
 _ERR = {-1: "SKIM_EINVAL", -2: "SKIM_ENOMEM", -3: "SKIM_ENOTBUILT", -4: "SKIM_ETIMEOUT", -5: "SKIM_ECUDA",
         -6: "SKIM_EGRAPH", -7: "SKIM_ERANGE"}
 PROB_UNIFORM, PROB_WC, PROB_TRIVALENCY = 0, 1, 2
+RANKS_UNIFORM, RANKS_PERMUTATION, RANKS_IC_MODEL = 0, 1, 2
 KERNEL_NAMES = ("rev_search", "fwd_search", "accept", "record_sort", "skim_step", "rank_order", "query", "setup")
 STAT_NAMES = ("rev_visits", "rev_coins", "insertions", "fwd_visits", "fwd_coins", "batches", "ranks", "retries",
               "rev_edges", "fwd_edges")
@@ -39,7 +40,7 @@ class skim_graph(C.Structure):
 class skim_params(C.Structure):
     _fields_ = [("l", C.c_uint32), ("k", C.c_uint32), ("prob_model", C.c_int), ("p", C.c_double),
                 ("coin_key", C.c_uint64), ("rank_key", C.c_uint64), ("prob_key", C.c_uint64),
-                ("batch_lanes", C.c_uint32)]
+                ("batch_lanes", C.c_uint32), ("rank_mode", C.c_uint32)]
 
 
 _lib = None
@@ -62,6 +63,7 @@ def load():
     lib.skim_greedy.argtypes = [vp, u32, vp, vp]
     lib.skim_greedy_reset.argtypes = [vp]
     lib.skim_greedy_ex.argtypes = [vp, u32, vp, vp, vp, vp]
+    lib.skim_node_estimates.argtypes = [vp, vp, C.c_int]
     lib.skim_discrepancy_bound.argtypes = [u32, vp, vp, vp, C.c_double, u32, u32, vp, vp, vp]
     lib.skim_oracle_query.argtypes = [vp, vp, u32, vp]
     lib.skim_oracle_query_batch.argtypes = [vp, vp, u32, vp, vp, C.c_int]
@@ -186,6 +188,10 @@ def discrepancy_bound(delta, tau, kprime, step: float, bins: int = 4096, conf=(0
     return out[: cf.shape[0]], ccdf
 
 
+def skim_node_estimates(ctx: int, out, out_on_device: int = 0):
+    _check(load().skim_node_estimates(ctx, _ptr(out), out_on_device), "skim_node_estimates")
+
+
 def skim_greedy_reset(ctx: int):
     _check(load().skim_greedy_reset(ctx), "skim_greedy_reset")
 
@@ -277,7 +283,8 @@ class Skim:
     """
 
     def __init__(self, n: int, src, dst, l: int, k: int, prob_model: int = PROB_UNIFORM, p: float = 0.1,
-                 coin_key: int = 0, rank_key: int = 0, prob_key: int = 0, batch_lanes: int = 0, stream: int = 0):
+                 coin_key: int = 0, rank_key: int = 0, prob_key: int = 0, batch_lanes: int = 0, stream: int = 0,
+                 rank_mode: int = 0):
         on_device = not isinstance(src, np.ndarray)
         if not on_device:
             src = np.ascontiguousarray(src, dtype=np.uint32)
@@ -286,8 +293,8 @@ class Skim:
         m = int(src.shape[0])
         g = skim_graph(n, m, _ptr(src) if m else None, _ptr(dst) if m else None, 1 if on_device else 0)
         prm = skim_params(l, k, prob_model, p, coin_key & (2**64 - 1), rank_key & (2**64 - 1),
-                          prob_key & (2**64 - 1), batch_lanes)
-        self.n, self.m, self.l, self.k = n, m, l, k
+                          prob_key & (2**64 - 1), batch_lanes, rank_mode)
+        self.n, self.m, self.l, self.k, self.rank_mode = n, m, l, k, rank_mode
         self.ctx = skim_create(g, prm, stream)
         self._keep = None
 
@@ -356,6 +363,12 @@ class Skim:
 
     def greedy_reset(self):
         skim_greedy_reset(self.ctx)
+
+    def node_estimates(self) -> np.ndarray:
+        """Single-node influence estimates from every node's own sketch."""
+        out = np.zeros(self.n, np.float64)
+        skim_node_estimates(self.ctx, out, 0)
+        return out
 
     def query(self, seeds) -> float:
         s = np.ascontiguousarray(seeds, dtype=np.uint32)

@@ -29,8 +29,16 @@ inline unsigned grid_for(size_t n, int threads, unsigned cap = 152 * 32) {
 }
 
 // Instance of every lane and the offset of its coin stream, (i + 1) * G.
-__global__ void k_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, uint64_t *lane_g) {
+// Instance and coin-stream offset of every lane: instance i = pair % l, or in
+// the IC model (lane_rank given) a fresh instance numbered by the position.
+__global__ void k_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_rank, uint32_t B, uint32_t l,
+                            uint8_t *lane_inst, uint64_t *lane_g) {
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < B; j += gridDim.x * blockDim.x) {
+        if (lane_rank) {
+            lane_inst[j] = 0;
+            lane_g[j] = kGolden * (lane_rank[j] + 1);
+            continue;
+        }
         const uint32_t i = lane_pair[j] % l;
         lane_inst[j] = static_cast<uint8_t>(i);
         lane_g[j] = kGolden * static_cast<uint64_t>(i + 1);
@@ -233,10 +241,10 @@ __global__ void k_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl) {
 
 }  // namespace
 
-cudaError_t launch_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, uint64_t *lane_g,
-                             cudaStream_t s) {
+cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_rank, uint32_t B, uint32_t l,
+                             uint8_t *lane_inst, uint64_t *lane_g, cudaStream_t s) {
     note_launch();
-    k_lane_inst<<<grid_for(B, 256), 256, 0, s>>>(lane_pair, B, l, lane_inst, lane_g);
+    k_lane_inst<<<grid_for(B, 256), 256, 0, s>>>(lane_pair, lane_rank, B, l, lane_inst, lane_g);
     return cudaGetLastError();
 }
 cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,

@@ -34,6 +34,10 @@ struct skim_ctx {
     uint64_t *srank = nullptr;
     uint32_t *spair = nullptr;
     void *rank_ws = nullptr;
+    // rank order: SKIM_RANKS_* mode, positions in the order, and how many of
+    // them the sketch build processes
+    int rank_mode = 0;
+    uint64_t npos = 0, nbuild = 0;
     uint64_t rank_key = 0;
     // graphs of a batch (skim_create_batch): per-node rank bases, per-edge
     // thresholds, node offsets of the graphs
@@ -296,11 +300,13 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     const uint32_t T = (B + 63) / 64;
     const uint32_t tbits = bitlen(T - 1);
     RC(reset_ctl(c));
-    CK(c, launch_lane_inst(c->spair + p0, B, c->l, c->lane_inst, c->lane_g, c->st));
+    CK(c, launch_lane_inst(c->spair + p0, c->rank_mode == SKIM_RANKS_IC_MODEL ? c->srank + p0 : nullptr, B, c->l,
+                           c->lane_inst, c->lane_g, c->st));
     if (!mode_build) CK(c, cudaMemsetAsync(c->alive, 0, T * sizeof(uint64_t), c->st));
     TravArgs a = base_args(c, false);
     a.tbits = tbits;
-    a.prune = mode_build ? 1 : 0;
+    // IC-model searches are never pruned: every lane is its own instance
+    a.prune = mode_build && c->rank_mode != SKIM_RANKS_IC_MODEL ? 1 : 0;
     CK(c, launch_rev_sources(a, c->spair + p0, B, c->l, mode_build ? nullptr : c->covered,
                              mode_build ? nullptr : c->alive, c->st));
     uint64_t R = 0;
@@ -539,7 +545,11 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
 int rank_order(skim_ctx *c) {
     {
         KTimer kt(c, SKIM_K_RANKS);
-        CK(c, rank_sort(c->rank_key, c->rbase, c->l, c->nl, c->srank, c->spair, c->rank_ws, c->st));
+        if (c->rank_mode == SKIM_RANKS_UNIFORM)
+            CK(c, rank_sort(c->rank_key, c->rbase, c->l, c->nl, c->srank, c->spair, c->rank_ws, c->st));
+        else
+            CK(c, perm_sort(c->rank_key, c->n, c->l, static_cast<uint32_t>(c->npos / c->n),
+                            c->rank_mode == SKIM_RANKS_IC_MODEL, c->srank, c->spair, c->rank_ws, c->st));
     }
     CK(c, cudaStreamSynchronize(c->st));
     resolve_timers(c);
@@ -587,6 +597,13 @@ int ensure_query_space(skim_ctx *c, uint64_t seeds, uint64_t q, uint64_t table, 
 uint64_t query_table(uint64_t s, uint32_t k) { return pow2_at_least(std::max<uint64_t>(64, 2 * s * (k - 1) + 2)); }
 
 }  // namespace
+
+QueryTerms skim::query_terms_of(const skim_ctx *c) {
+    if (c->rank_mode == SKIM_RANKS_PERMUTATION)
+        return QueryTerms{1, static_cast<double>(c->nl - 1), static_cast<double>(c->l)};
+    if (c->rank_mode == SKIM_RANKS_IC_MODEL) return QueryTerms{2, static_cast<double>(c->n), 1.0};
+    return QueryTerms{0, 0.0, static_cast<double>(c->l)};
+}
 
 extern "C" {
 
@@ -640,8 +657,17 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
     if (prm->prob_model == 0 && prm->p < 1.0 && static_cast<uint64_t>(std::ldexp(prm->p, 64)) == 0) return SKIM_EINVAL;
     if (g->m && (!g->src || !g->dst)) return SKIM_EINVAL;
     if (g->m >= (1ull << 32)) return SKIM_ERANGE;
+    if (prm->rank_mode > SKIM_RANKS_IC_MODEL) return SKIM_EINVAL;
+    if (prm->rank_mode == SKIM_RANKS_IC_MODEL && prm->l != 1) return SKIM_EINVAL;
     const uint64_t nl = static_cast<uint64_t>(g->n) * prm->l;
     if (nl > 0xffffffffull) return SKIM_ERANGE;
+    // positions of the rank order, and those the sketch build needs (with
+    // permutation ranks every node owns one position per chunk, so no position
+    // past min(k, l) chunks can enter a sketch)
+    uint64_t npos = nl, nbuild = nl;
+    if (prm->rank_mode == SKIM_RANKS_PERMUTATION) nbuild = static_cast<uint64_t>(std::min(prm->k, prm->l)) * g->n;
+    if (prm->rank_mode == SKIM_RANKS_IC_MODEL) npos = nbuild = static_cast<uint64_t>(prm->k) * g->n;
+    if (npos > 0xffffffffull) return SKIM_ERANGE;
 
     skim_ctx *c = new (std::nothrow) skim_ctx();
     if (!c) return SKIM_ENOMEM;
@@ -652,6 +678,9 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
     c->l = prm->l;
     c->k = prm->k;
     c->nl = nl;
+    c->rank_mode = static_cast<int>(prm->rank_mode);
+    c->npos = npos;
+    c->nbuild = nbuild;
     c->batch_cfg = prm->batch_lanes;
     c->cm.model = prm->prob_model;
     c->cm.tm1_uniform = prm->prob_model == 0 ? tm1_of(prm->p) : 0;
@@ -708,7 +737,7 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         // workspace for scans and sorts
         // visit records per batch: a few per lane; sized generously so that
         // re-running a batch with fewer lanes stays rare
-        const uint64_t lanes_max = std::min<uint64_t>(nl, prm->batch_lanes ? prm->batch_lanes : (1u << 21));
+        const uint64_t lanes_max = std::min<uint64_t>(npos, prm->batch_lanes ? prm->batch_lanes : (1u << 21));
         const uint64_t rcap = std::min<uint64_t>(std::max<uint64_t>(16ull * lanes_max, 1u << 20), 1ull << 26);
         size_t ws = std::max({scan_workspace_bytes(static_cast<size_t>(n) + 1), radix_workspace_bytes(m),
                               radix_workspace_bytes(rcap), scan_workspace_bytes(static_cast<size_t>(kMaxWords) * 64)});
@@ -767,13 +796,16 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         }
         c->cm.thr_wc = c->thr_wc;
         // rank order of the n*l pairs
-        TRY(dalloc(c, &c->srank, nl));
-        TRY(dalloc(c, &c->spair, nl));
-        TRYC(cudaMalloc(&c->rank_ws, rank_sort_workspace_bytes(nl)));
+        TRY(dalloc(c, &c->srank, npos));
+        TRY(dalloc(c, &c->spair, npos));
+        TRYC(cudaMalloc(&c->rank_ws, c->rank_mode == SKIM_RANKS_UNIFORM
+                                         ? rank_sort_workspace_bytes(nl)
+                                         : perm_sort_workspace_bytes(n, c->l, static_cast<uint32_t>(npos / n),
+                                                                     c->rank_mode == SKIM_RANKS_IC_MODEL)));
         c->rank_key = prm->rank_key;
         TRY(rank_order(c));
         // traversal scratch
-        c->lane_cap = static_cast<uint32_t>(std::min<uint64_t>(pow2_at_least(std::min<uint64_t>(nl, kMaxWords * 64ull)),
+        c->lane_cap = static_cast<uint32_t>(std::min<uint64_t>(pow2_at_least(std::min<uint64_t>(npos, kMaxWords * 64ull)),
                                                                kMaxWords * 64ull));
         if (c->lane_cap < 64) c->lane_cap = 64;
         c->rcap = rcap;
@@ -824,6 +856,7 @@ int skim_create_batch(const skim_graph *graphs, const skim_params *prm, uint32_t
         const skim_params &p = prm[g];
         if (graphs[g].on_device) return SKIM_EINVAL;  // host edge lists only
         if (graphs[g].n == 0 || p.l != l || p.k != k) return SKIM_EINVAL;
+        if (p.rank_mode != SKIM_RANKS_UNIFORM) return SKIM_EINVAL;  // per-graph rank bases are uniform ranks
         if (p.prob_model < 0 || p.prob_model > 2) return SKIM_EINVAL;
         if (p.prob_model == 0 && !(p.p > 0.0 && p.p <= 1.0)) return SKIM_EINVAL;
         if (graphs[g].m && (!graphs[g].src || !graphs[g].dst)) return SKIM_EINVAL;
@@ -965,8 +998,8 @@ int skim_build_sketches(skim_ctx *c) {
     const uint32_t Bmax = default_lanes(c);
     uint32_t B = std::min<uint32_t>(Bmax, 1u << 12);
     uint64_t p0 = 0;
-    while (p0 < c->nl) {
-        uint32_t b = static_cast<uint32_t>(std::min<uint64_t>(B, c->nl - p0));
+    while (p0 < c->nbuild) {
+        uint32_t b = static_cast<uint32_t>(std::min<uint64_t>(B, c->nbuild - p0));
         bool retry = false;
         RC(rev_batch(c, p0, b, true, &retry));
         if (retry) {
@@ -1044,6 +1077,7 @@ int skim_greedy_ex(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t 
                    int32_t *kprime_out) {
     if (!c || (n_seeds && (!seeds_out || !cov_out))) return SKIM_EINVAL;
     if (c->batch_count) return SKIM_EINVAL;  // a batch of graphs has no single seed sequence
+    if (c->rank_mode == SKIM_RANKS_IC_MODEL) return SKIM_EINVAL;  // IC-model SKIM is not built
     if (c->broken) return SKIM_ECUDA;
     if (!c->sk_init) RC(skim_state_init(c));
     if (static_cast<uint64_t>(c->nseeds) + n_seeds > c->n) return SKIM_EINVAL;
@@ -1121,7 +1155,7 @@ int skim_oracle_query_batch(skim_ctx *c, const uint64_t *offsets, uint32_t q, co
     {
         KTimer kt(c, SKIM_K_QUERY);
         QueryScratch qs{c->qk, c->qv, c->qtop, c->qtopu, c->qpart, c->dflag};
-        CK(c, launch_query_multi(c->X, c->xlen, c->n, c->k, c->l, dseeds, d_off, d_toff, d_coff, q, toff[q], total,
+        CK(c, launch_query_multi(c->X, c->xlen, c->n, c->k, query_terms_of(c), dseeds, d_off, d_toff, d_coff, q, toff[q], total,
                                  static_cast<uint32_t>(coff[q]), qs, dout, c->st));
     }
     unsigned bad = 0;
@@ -1143,6 +1177,22 @@ int skim_kernel_launches(uint64_t *out) {
     if (!out) return SKIM_EINVAL;
     *out = g_kernel_launches.load();
     return SKIM_OK;
+}
+
+int skim_node_estimates(skim_ctx *c, double *out, int out_on_device) {
+    if (!c || !out) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    if (!c->built) return SKIM_ENOTBUILT;
+    double *d = out;
+    if (!out_on_device) RC(dalloc(c, &d, c->n));
+    int rc = SKIM_OK;
+    if (launch_node_estimates(c->X, c->xlen, c->n, c->k, c->l, c->rank_mode, d, c->st) != cudaSuccess ||
+        (!out_on_device &&
+         cudaMemcpyAsync(out, d, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess) ||
+        cudaStreamSynchronize(c->st) != cudaSuccess)
+        rc = fail_cuda(c, cudaGetLastError());
+    if (!out_on_device) dfree(d);
+    return rc;
 }
 
 int skim_set_timing(skim_ctx *c, int on) {

@@ -22,6 +22,8 @@ inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_rel
 
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kEmptyKey = ~0ull;
+// key of the within-chunk node order of permutation ranks: fmix(rank_key ^ salt)
+constexpr uint64_t kPermSalt = 0x7065726d75746531ull;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Work items are cut so that one item costs about kTargetCoins coin

@@ -92,33 +92,66 @@ SKIM_DEV uint64_t rank_of(uint64_t rank_key, const uint64_t *rbase, uint32_t l, 
     return rbase ? fmix(rbase[x / l] + kGolden * (x % l)) : pair_rank(rank_key, x);
 }
 
-__global__ void k_rank_count(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t nl, int bb,
-                             unsigned long long *cnt) {
-    for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < nl;
-         x += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        uint64_t r = rank_of(rank_key, rbase, l, x);
-        uint64_t b = bb ? (r >> (64 - bb)) : 0;
-        atomicAdd(&cnt[b], 1ull);
+// Sort keys of the rank order.  An element x is sorted by key(x) inside
+// bucket(x); buckets are laid out in the order of the result.
+//  UniformKeys: x = v*l + i, the uniform rank r(v,i) (Section 3); the output
+//    rank is the key itself.
+//  ChunkKeys: structured permutation (Section 3.1) and IC-model positions
+//    (Section 3.2): x = c*n + v, chunk c first, then w(v,c) = fmix(K_w + G x);
+//    the output rank is the position, the output pair (v, sigma_v(c)) or, in
+//    the IC model (sigma null), the node v.
+struct UniformKeys {
+    uint64_t rank_key;
+    const uint64_t *rbase;
+    uint32_t l;
+    int bb;
+    SKIM_DEV uint64_t key(uint64_t x) const { return rank_of(rank_key, rbase, l, x); }
+    SKIM_DEV uint64_t bucket(uint64_t, uint64_t key) const { return bb ? (key >> (64 - bb)) : 0; }
+    SKIM_DEV uint64_t out_rank(uint64_t, uint64_t key) const { return key; }
+    SKIM_DEV uint32_t out_pair(uint64_t x) const { return static_cast<uint32_t>(x); }
+};
+
+struct ChunkKeys {
+    uint64_t kw;
+    uint32_t n, l;
+    int bb;                // bucket bits per chunk
+    const uint8_t *sigma;  // sigma[v*l + c]: node v's instance in chunk c (null: IC model)
+    SKIM_DEV uint64_t key(uint64_t x) const { return fmix(kw + kGolden * x); }
+    SKIM_DEV uint64_t bucket(uint64_t x, uint64_t key) const {
+        return ((x / n) << bb) | (bb ? (key >> (64 - bb)) : 0);
     }
+    SKIM_DEV uint64_t out_rank(uint64_t pos, uint64_t) const { return pos; }
+    SKIM_DEV uint32_t out_pair(uint64_t x) const {
+        const uint32_t v = static_cast<uint32_t>(x % n);
+        if (!sigma) return v;
+        const uint64_t c = x / n;
+        return v * l + sigma[static_cast<uint64_t>(v) * l + c];
+    }
+};
+
+template <class K>
+__global__ void k_rank_count(K kf, uint64_t total, unsigned long long *cnt) {
+    for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        atomicAdd(&cnt[kf.bucket(x, kf.key(x))], 1ull);
 }
 
-__global__ void k_rank_scatter(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t nl, int bb,
-                               const uint64_t *off, unsigned *fill, uint32_t *tmp) {
-    for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < nl;
+template <class K>
+__global__ void k_rank_scatter(K kf, uint64_t total, const uint64_t *off, unsigned *fill, uint32_t *tmp) {
+    for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < total;
          x += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        uint64_t r = rank_of(rank_key, rbase, l, x);
-        uint64_t b = bb ? (r >> (64 - bb)) : 0;
+        const uint64_t b = kf.bucket(x, kf.key(x));
         unsigned p = atomicAdd(&fill[b], 1u);
         tmp[off[b] + p] = static_cast<uint32_t>(x);
     }
 }
 
-// Sort one bucket by rank.  Ranks are distinct (the pair -> rank map is a
-// bijection), so a bucket larger than the shared-memory capacity can be
-// placed by counting smaller keys; that path is correct for any size and
-// only its speed depends on the (uniform) bucket sizes.
-__global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(uint64_t rank_key, const uint64_t *rbase, uint32_t l,
-                                                                const uint64_t *off, const uint32_t *tmp,
+// Sort one bucket by key.  Keys are distinct (each key map is a bijection of
+// x), so a bucket larger than the shared-memory capacity can be placed by
+// counting smaller keys; that path is correct for any size and only its speed
+// depends on the (uniform) bucket sizes.
+template <class K>
+__global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(K kf, const uint64_t *off, const uint32_t *tmp,
                                                                 uint64_t *sorted_rank, uint32_t *sorted_pair) {
     __shared__ uint64_t key[kBucketCap];
     __shared__ uint32_t val[kBucketCap];
@@ -132,7 +165,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(uint64_t rank_ke
             if (i < s) {
                 uint32_t x = tmp[b0 + i];
                 val[i] = x;
-                key[i] = rank_of(rank_key, rbase, l, x);
+                key[i] = kf.key(x);
             } else {
                 key[i] = ~0ull;
                 val[i] = 0;
@@ -156,13 +189,13 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(uint64_t rank_ke
             }
         }
         for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) {
-            sorted_rank[b0 + i] = key[i];
-            sorted_pair[b0 + i] = val[i];
+            sorted_rank[b0 + i] = kf.out_rank(b0 + i, key[i]);
+            sorted_pair[b0 + i] = kf.out_pair(val[i]);
         }
         return;
     }
-    // oversize bucket: ranks to the output rank slots, then place pairs by count
-    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) sorted_rank[b0 + i] = rank_of(rank_key, rbase, l, tmp[b0 + i]);
+    // oversize bucket: keys to the output rank slots, then place elements by count
+    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) sorted_rank[b0 + i] = kf.key(tmp[b0 + i]);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) {
         uint64_t r = sorted_rank[b0 + i];
@@ -171,8 +204,32 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(uint64_t rank_ke
         sorted_pair[b0 + pos] = tmp[b0 + i];
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x)
-        sorted_rank[b0 + i] = rank_of(rank_key, rbase, l, sorted_pair[b0 + i]);
+    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) {
+        const uint32_t x = sorted_pair[b0 + i];
+        sorted_rank[b0 + i] = kf.out_rank(b0 + i, kf.key(x));
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) sorted_pair[b0 + i] = kf.out_pair(sorted_pair[b0 + i]);
+}
+
+// Section 3.1: sigma[v*l + c] = the instance of node v with the (c+1)-th
+// smallest rank r(v,i); one warp per node, l <= 64 keys in two registers.
+__global__ void k_perm_sigma(uint64_t rank_key, uint32_t n, uint32_t l, uint8_t *sigma) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t v = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5; v < n; v += warps) {
+        const uint64_t base = v * l;
+        const uint64_t k0 = lane < l ? pair_rank(rank_key, base + lane) : ~0ull;
+        const uint64_t k1 = lane + 32 < l ? pair_rank(rank_key, base + lane + 32) : ~0ull;
+        uint32_t c0 = 0, c1 = 0;
+        for (uint32_t j = 0; j < l; j++) {
+            const uint64_t kj = __shfl_sync(kFull, j < 32 ? k0 : k1, j & 31);
+            c0 += kj < k0;
+            c1 += kj < k1;
+        }
+        if (lane < l) sigma[base + c0] = static_cast<uint8_t>(lane);
+        if (lane + 32 < l) sigma[base + c1] = static_cast<uint8_t>(lane + 32);
+    }
 }
 
 // ---- graphs of a batch -----------------------------------------------------
@@ -302,38 +359,86 @@ cudaError_t launch_rank_bases(const BatchDesc &b, uint32_t n, uint32_t l, uint64
     return cudaGetLastError();
 }
 
-size_t rank_sort_workspace_bytes(uint64_t nl) {
-    uint64_t nb = 1ull << bucket_bits(nl);
-    size_t b = (nb + 1) * sizeof(uint64_t) * 2 + nb * sizeof(unsigned) + nl * sizeof(uint32_t);
+namespace {
+
+struct SortSpace {
+    uint64_t *cnt, *off;
+    unsigned *fill;
+    uint32_t *tmp;
+    void *scan;
+};
+
+size_t sort_space_bytes(uint64_t nb, uint64_t total) {
+    size_t b = (nb + 1) * sizeof(uint64_t) * 2 + nb * sizeof(unsigned) + total * sizeof(uint32_t);
     return b + scan_workspace_bytes(nb + 1) + 1024;
 }
+
+SortSpace carve(void *ws, uint64_t nb, uint64_t total) {
+    SortSpace sp;
+    char *p = static_cast<char *>(ws);
+    sp.cnt = reinterpret_cast<uint64_t *>(p); p += (nb + 1) * sizeof(uint64_t);
+    sp.off = reinterpret_cast<uint64_t *>(p); p += (nb + 1) * sizeof(uint64_t);
+    sp.fill = reinterpret_cast<unsigned *>(p); p += nb * sizeof(unsigned);
+    sp.tmp = reinterpret_cast<uint32_t *>(p); p += total * sizeof(uint32_t);
+    sp.scan = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(p) + 255) & ~static_cast<uintptr_t>(255));
+    return sp;
+}
+
+template <class K>
+cudaError_t bucket_sort_all(const K &kf, uint64_t total, uint64_t nb, const SortSpace &sp, uint64_t *sorted_rank,
+                            uint32_t *sorted_pair, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(sp.cnt, 0, (nb + 1) * sizeof(uint64_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sp.fill, 0, nb * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_rank_count<<<grid_for(total, 256), 256, 0, s>>>(kf, total, reinterpret_cast<unsigned long long *>(sp.cnt));
+    // off[b] = exclusive prefix; off[nb] = total (scan over nb+1 entries with cnt[nb] = 0)
+    e = exclusive_scan_u64(sp.cnt, sp.off, nb + 1, nullptr, sp.scan, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_rank_scatter<<<grid_for(total, 256), 256, 0, s>>>(kf, total, sp.off, sp.fill, sp.tmp);
+    note_launch();
+    k_bucket_sort<<<static_cast<unsigned>(nb), kBucketThreads, 0, s>>>(kf, sp.off, sp.tmp, sorted_rank, sorted_pair);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t rank_sort_workspace_bytes(uint64_t nl) { return sort_space_bytes(1ull << bucket_bits(nl), nl); }
 
 cudaError_t rank_sort(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t nl, uint64_t *sorted_rank,
                       uint32_t *sorted_pair, void *ws, cudaStream_t s) {
     if (nl == 0) return cudaSuccess;
     const int bb = bucket_bits(nl);
     const uint64_t nb = 1ull << bb;
-    char *p = static_cast<char *>(ws);
-    uint64_t *cnt = reinterpret_cast<uint64_t *>(p); p += (nb + 1) * sizeof(uint64_t);
-    uint64_t *off = reinterpret_cast<uint64_t *>(p); p += (nb + 1) * sizeof(uint64_t);
-    unsigned *fill = reinterpret_cast<unsigned *>(p); p += nb * sizeof(unsigned);
-    uint32_t *tmp = reinterpret_cast<uint32_t *>(p); p += nl * sizeof(uint32_t);
-    p = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(p) + 255) & ~static_cast<uintptr_t>(255));
-    void *sws = p;
-    cudaError_t e = cudaMemsetAsync(cnt, 0, (nb + 1) * sizeof(uint64_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(fill, 0, nb * sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    k_rank_count<<<grid_for(nl, 256), 256, 0, s>>>(rank_key, rbase, l, nl, bb, reinterpret_cast<unsigned long long *>(cnt));
-    // off[b] = exclusive prefix; off[nb] = nl (scan over nb+1 entries with cnt[nb] = 0)
-    e = exclusive_scan_u64(cnt, off, nb + 1, nullptr, sws, s);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    k_rank_scatter<<<grid_for(nl, 256), 256, 0, s>>>(rank_key, rbase, l, nl, bb, off, fill, tmp);
-    note_launch();
-    k_bucket_sort<<<static_cast<unsigned>(nb), kBucketThreads, 0, s>>>(rank_key, rbase, l, off, tmp, sorted_rank,
-                                                                   sorted_pair);
-    return cudaGetLastError();
+    UniformKeys kf{rank_key, rbase, l, bb};
+    return bucket_sort_all(kf, nl, nb, carve(ws, nb, nl), sorted_rank, sorted_pair, s);
+}
+
+uint64_t perm_key(uint64_t rank_key) { return fmix(rank_key ^ kPermSalt); }
+
+size_t perm_sort_workspace_bytes(uint32_t n, uint32_t l, uint32_t chunks, bool ic) {
+    const uint64_t nb = static_cast<uint64_t>(chunks) << bucket_bits(n);
+    const uint64_t total = static_cast<uint64_t>(chunks) * n;
+    return sort_space_bytes(nb, total) + (ic ? 0 : static_cast<size_t>(n) * l) + 256;
+}
+
+cudaError_t perm_sort(uint64_t rank_key, uint32_t n, uint32_t l, uint32_t chunks, bool ic, uint64_t *sorted_rank,
+                      uint32_t *sorted_pair, void *ws, cudaStream_t s) {
+    const uint64_t total = static_cast<uint64_t>(chunks) * n;
+    if (total == 0) return cudaSuccess;
+    const int bb = bucket_bits(n);
+    const uint64_t nb = static_cast<uint64_t>(chunks) << bb;
+    uint8_t *sigma = nullptr;
+    char *rest = static_cast<char *>(ws);
+    if (!ic) {
+        sigma = reinterpret_cast<uint8_t *>(rest);
+        rest += (static_cast<size_t>(n) * l + 255) & ~static_cast<size_t>(255);
+        note_launch();
+        k_perm_sigma<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(rank_key, n, l, sigma);
+    }
+    ChunkKeys kf{perm_key(rank_key), n, l, bb, sigma};
+    return bucket_sort_all(kf, total, nb, carve(rest, nb, total), sorted_rank, sorted_pair, s);
 }
 
 }  // namespace skim

@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 
+struct skim_ctx;  // the C ABI's opaque context (capi.cu)
+
 namespace skim {
 
 // Live-edge threshold model (Section 6: uniform p, weighted cascade 1/indeg,
@@ -74,6 +76,13 @@ cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long lon
 // rank of pair x = v*l+i is fmix(rank_key + G*x), or fmix(rbase[v] + G*i)
 // when a per-node base is given (graphs of a batch, each with its own key).
 size_t rank_sort_workspace_bytes(uint64_t nl);
+// Structured permutation (Section 3.1; ic = false: pairs (v, sigma_v(c))) or
+// IC-model positions (Section 3.2; ic = true: nodes) for the first `chunks`
+// chunks of n positions: sorted_rank[t] = t, sorted_pair[t] = pair or node.
+uint64_t perm_key(uint64_t rank_key);
+size_t perm_sort_workspace_bytes(uint32_t n, uint32_t l, uint32_t chunks, bool ic);
+cudaError_t perm_sort(uint64_t rank_key, uint32_t n, uint32_t l, uint32_t chunks, bool ic, uint64_t *sorted_rank,
+                      uint32_t *sorted_pair, void *ws, cudaStream_t s);
 cudaError_t rank_sort(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t nl, uint64_t *sorted_rank,
                       uint32_t *sorted_pair, void *ws, cudaStream_t s);
 
@@ -105,8 +114,8 @@ cudaError_t launch_respill_fwd(const TravArgs &a, uint32_t n, cudaStream_t s);
 int traverse_grid(bool forward);  // resident blocks for the persistent traversal
 
 // batch.cu
-cudaError_t launch_lane_inst(const uint32_t *lane_pair, uint32_t B, uint32_t l, uint8_t *lane_inst, uint64_t *lane_g,
-                             cudaStream_t s);
+cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_rank, uint32_t B, uint32_t l,
+                             uint8_t *lane_inst, uint64_t *lane_g, cudaStream_t s);
 cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                           const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
                           uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
@@ -148,7 +157,21 @@ struct QueryScratch {
 };
 uint32_t query_chunks(uint64_t table_slots);  // chunks of one query's table
 size_t query_partial_bytes();                  // bytes per chunk partial
-cudaError_t launch_query_multi(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
+// How a threshold becomes a term of Eq. unionest, and the final divisor:
+//  mode 0 (uniform 64-bit ranks): 1 / (h * 2^-64), divided by l;
+//  mode 1 (structured permutation, Section 3.1): num / h with num = n*l - 1,
+//          1 for a sketch that is not full, divided by l;
+//  mode 2 (IC model, Section 3.2): num / h with num = n, 0 for a sketch that
+//          is not full, divided by 1.
+struct QueryTerms {
+    int mode;
+    double num;
+    double div;
+};
+QueryTerms query_terms_of(const skim_ctx *c);
+cudaError_t launch_node_estimates(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
+                                  int mode, double *out, cudaStream_t s);
+cudaError_t launch_query_multi(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, const QueryTerms &terms,
                                const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off,
                                const uint64_t *chunk_off, uint32_t q, uint64_t total_slots, uint64_t total_seeds,
                                uint32_t total_chunks, const QueryScratch &qs, double *out, cudaStream_t s);

@@ -13,6 +13,12 @@
 // with a 53-bit significand) and the total is rounded to double once, to
 // nearest-even.  The result therefore does not depend on the order in which
 // ranks are visited, and a query gives the same bits alone or in a batch.
+// With permutation ranks (Sections 3.1, 3.2) a sketch holds positions and a
+// threshold q becomes the term (n*l - 1)/q, or n/q in the IC model, each
+// formed as one double division (terms are at least 1/k >= 2^-8, so 64
+// fraction bits still hold them exactly).
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace skim {
@@ -43,7 +49,14 @@ SKIM_DEV double inv_tau(uint64_t h) {
     return 1.0 / tau;
 }
 
-// exact fixed-point image (value * 2^64) of a double in [1, 2^64]
+// term of a threshold h under the context's rank reading (QueryTerms)
+SKIM_DEV double term_of(const QueryTerms &t, uint64_t h) {
+    if (t.mode == 0) return inv_tau(h);
+    if (h == ~0ull) return t.mode == 2 ? 0.0 : 1.0;
+    return t.num / __ull2double_rn(h);
+}
+
+// exact fixed-point image (value * 2^64) of a double in [2^-12, 2^64]
 SKIM_DEV U192 to_fixed(double v) {
     uint64_t bits = static_cast<uint64_t>(__double_as_longlong(v));
     int e = static_cast<int>((bits >> 52) & 0x7ff) - 1023;
@@ -169,7 +182,7 @@ __global__ void k_q_insert(const uint64_t *X, const uint32_t *xlen, uint32_t n, 
 __global__ void __launch_bounds__(256) k_q_sum(const uint64_t *hkeys, const uint64_t *hvals, const uint64_t *table_off,
                                                const uint64_t *chunk_off, uint32_t q,
                                                const unsigned long long *top_tau, const unsigned *top_used,
-                                               U192 *partial) {
+                                               QueryTerms terms, U192 *partial) {
     __shared__ U192 wsum[8];
     const uint32_t c = blockIdx.x;
     const uint32_t qi = upper_bound_u64(chunk_off + 1, q, c);
@@ -178,8 +191,14 @@ __global__ void __launch_bounds__(256) k_q_sum(const uint64_t *hkeys, const uint
     const uint64_t hi = min(lo + kQChunk, table_off[qi + 1]);
     U192 acc{{0, 0, 0}};
     for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        if (hkeys[i] != kEmptyKey) add192(acc, to_fixed(inv_tau(hvals[i])));
-    if (c == first && threadIdx.x == 0 && top_used[qi]) add192(acc, to_fixed(inv_tau(top_tau[qi])));
+        if (hkeys[i] != kEmptyKey) {
+            const double v = term_of(terms, hvals[i]);
+            if (v != 0.0) add192(acc, to_fixed(v));
+        }
+    if (c == first && threadIdx.x == 0 && top_used[qi]) {
+        const double v = term_of(terms, top_tau[qi]);
+        if (v != 0.0) add192(acc, to_fixed(v));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         U192 other;
@@ -195,11 +214,34 @@ __global__ void __launch_bounds__(256) k_q_sum(const uint64_t *hkeys, const uint
     }
 }
 
-__global__ void k_q_final(const U192 *partial, const uint64_t *chunk_off, uint32_t q, uint32_t l, double *out) {
+__global__ void k_q_final(const U192 *partial, const uint64_t *chunk_off, uint32_t q, double div, double *out) {
     for (uint32_t qi = blockIdx.x * blockDim.x + threadIdx.x; qi < q; qi += gridDim.x * blockDim.x) {
         U192 tot{{0, 0, 0}};
         for (uint64_t c = chunk_off[qi]; c < chunk_off[qi + 1]; c++) add192(tot, partial[c]);
-        out[qi] = fixed_to_double(tot) / static_cast<double>(l);
+        out[qi] = fixed_to_double(tot) / div;
+    }
+}
+
+// Single-node influence estimates from each node's own sketch: the bottom-k
+// estimator (k-1)/tau of Section 3 (mode 0), the permutation estimator
+// 1 + (k-1)(D-1)/(T-1) of Section 3.1 (mode 1) and n(k-1)/(T-1) of Section 3.2
+// (mode 2); |X_v| (mode 0, 1) or 0 (mode 2) for a sketch that is not full.
+__global__ void k_node_estimates(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
+                                 int mode, double *out) {
+    const double dl = static_cast<double>(l), k1 = static_cast<double>(k - 1);
+    const double d1 = static_cast<double>(static_cast<uint64_t>(n) * l - 1);
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint32_t lv = xlen[v];
+        double e;
+        if (lv < k) {
+            e = mode == 2 ? 0.0 : static_cast<double>(lv) / dl;
+        } else {
+            const double q = __ull2double_rn(X[static_cast<uint64_t>(v) * k + k - 1]);
+            if (mode == 0) e = k1 / ldexp(q, -64) / dl;
+            else if (mode == 1) e = (1.0 + k1 * d1 / q) / dl;
+            else e = static_cast<double>(n) * k1 / q;
+        }
+        out[v] = e;
     }
 }
 
@@ -209,7 +251,15 @@ uint32_t query_chunks(uint64_t table_slots) { return static_cast<uint32_t>((tabl
 
 size_t query_partial_bytes() { return sizeof(U192); }
 
-cudaError_t launch_query_multi(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
+cudaError_t launch_node_estimates(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, uint32_t l,
+                                  int mode, double *out, cudaStream_t s) {
+    note_launch();
+    const unsigned g = static_cast<unsigned>(std::min<uint64_t>((n + 255) / 256, 152 * 16));
+    k_node_estimates<<<g ? g : 1, 256, 0, s>>>(X, xlen, n, k, l, mode, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_multi(const uint64_t *X, const uint32_t *xlen, uint32_t n, uint32_t k, const QueryTerms &terms,
                                const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off,
                                const uint64_t *chunk_off, uint32_t q, uint64_t total_slots, uint64_t total_seeds,
                                uint32_t total_chunks, const QueryScratch &qs, double *out, cudaStream_t s) {
@@ -225,10 +275,10 @@ cudaError_t launch_query_multi(const uint64_t *X, const uint32_t *xlen, uint32_t
     k_q_insert<<<grid(total_seeds * k), 256, 0, s>>>(X, xlen, n, k, seeds, offsets, table_off, q, qs.hkeys, qs.hvals,
                                                      top_tau, qs.top_used, qs.err);
     note_launch();
-    k_q_sum<<<total_chunks, 256, 0, s>>>(qs.hkeys, qs.hvals, table_off, chunk_off, q, top_tau, qs.top_used,
+    k_q_sum<<<total_chunks, 256, 0, s>>>(qs.hkeys, qs.hvals, table_off, chunk_off, q, top_tau, qs.top_used, terms,
                                          static_cast<U192 *>(qs.partial));
     note_launch();
-    k_q_final<<<grid(q), 256, 0, s>>>(static_cast<const U192 *>(qs.partial), chunk_off, q, l, out);
+    k_q_final<<<grid(q), 256, 0, s>>>(static_cast<const U192 *>(qs.partial), chunk_off, q, terms.div, out);
     return cudaGetLastError();
 }
 

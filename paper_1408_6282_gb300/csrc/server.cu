@@ -67,6 +67,7 @@ struct skim_server {
     const uint64_t *X = nullptr;
     const uint32_t *xlen = nullptr;
     uint32_t n = 0, k = 0, l = 0;
+    QueryTerms terms{0, 0.0, 1.0};
     uint32_t max_inflight = 0;
     std::vector<Lane> lanes;
     std::mutex mu;
@@ -165,7 +166,7 @@ bool admit(skim_server *s) {
     ok &= cudaMemcpyAsync(ln->d_meta, ln->h_meta, 3 * g1 * sizeof(uint64_t), cudaMemcpyHostToDevice, ln->st) ==
           cudaSuccess;
     QueryScratch qs{ln->hk, ln->hv, ln->d_top, ln->d_topu, ln->d_part, ln->d_err};
-    ok &= launch_query_multi(s->X, s->xlen, s->n, s->k, s->l, ln->d_seeds, ln->d_meta, ln->d_meta + g1,
+    ok &= launch_query_multi(s->X, s->xlen, s->n, s->k, s->terms, ln->d_seeds, ln->d_meta, ln->d_meta + g1,
                              ln->d_meta + 2 * g1, cnt, used, nseeds, static_cast<uint32_t>(chunks), qs, ln->d_out,
                              ln->st) == cudaSuccess;
     ok &= cudaMemcpyAsync(ln->h_out, ln->d_out, cnt * sizeof(double), cudaMemcpyDeviceToHost, ln->st) == cudaSuccess;
@@ -216,6 +217,7 @@ int skim_server_start(skim_ctx *ctx, uint32_t max_inflight, uint64_t scratch_slo
     s->n = n;
     s->k = k;
     s->l = l;
+    s->terms = query_terms_of(ctx);
     s->max_inflight = max_inflight;
     s->lanes.resize(streams);
     const uint64_t arena = std::max<uint64_t>(scratch_slots / streams, 64);

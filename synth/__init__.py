@@ -259,6 +259,65 @@ def uniform_seed_set(n: int, size: int, key: int, qid: int) -> np.ndarray:
     return np.asarray(out, dtype=np.uint32)
 
 
+class Neighborhoods:
+    """The neighbourhood query generator of Section 6.2 over one graph: a root
+    drawn with probability proportional to its degree (a uniformly random end
+    of a uniformly random edge: in- plus out-degree), then the smallest radius
+    d whose ball (all nodes within d hops, edges taken in either direction)
+    holds at least `size` nodes, and `size` distinct nodes drawn uniformly from
+    that ball.  A component smaller than `size` gives all of its nodes."""
+
+    def __init__(self, n: int, src: np.ndarray, dst: np.ndarray):
+        src = np.asarray(src, dtype=np.int64)
+        dst = np.asarray(dst, dtype=np.int64)
+        self.n, self.m = n, src.shape[0]
+        self.src, self.dst = src, dst
+        both_u = np.concatenate([src, dst])
+        order = np.argsort(both_u, kind="stable")
+        self.adj = np.concatenate([dst, src])[order]
+        ptr = np.zeros(n + 1, np.int64)
+        np.add.at(ptr, both_u + 1, 1)
+        self.ptr = np.cumsum(ptr)
+
+    def draw(self, size: int, key: int, qid: int) -> tuple[np.ndarray, int]:
+        """Seed set (uint32) and the radius of its ball."""
+        base = _fmix_int((key ^ 0x4E45494748424F52) + (qid + 1) * GOLDEN)
+        h = int(stream(base, 1)[0])
+        if self.m == 0:
+            root = ((h >> 32) * self.n) >> 32
+        else:
+            e = ((h >> 32) * (2 * self.m)) >> 32
+            root = int(self.src[e] if e < self.m else self.dst[e - self.m])
+        seen = {root}
+        ball = [root]
+        frontier = [root]
+        radius = 0
+        while len(ball) < size and frontier:
+            nxt = []
+            for a in frontier:
+                for b in self.adj[self.ptr[a]:self.ptr[a + 1]].tolist():
+                    if b not in seen:
+                        seen.add(b)
+                        nxt.append(b)
+            if not nxt:
+                break
+            radius += 1
+            ball += nxt
+            frontier = nxt
+        take = min(size, len(ball))
+        # partial Fisher-Yates over the ball with the query's stream
+        r = stream(base, take, start=2)
+        for i in range(take):
+            j = i + ((int(r[i]) >> 32) * (len(ball) - i) >> 32)
+            ball[i], ball[j] = ball[j], ball[i]
+        return np.asarray(ball[:take], dtype=np.uint32), radius
+
+
+def neighborhood_seed_set(n: int, src: np.ndarray, dst: np.ndarray, size: int, key: int, qid: int):
+    """One draw of the neighbourhood generator (see Neighborhoods)."""
+    return Neighborhoods(n, src, dst).draw(size, key, qid)
+
+
 def poisson_arrivals(count: int, rate_per_s: float, key: int) -> np.ndarray:
     """Arrival times (s) of a Poisson process: exponential gaps by inversion."""
     h = stream(key ^ 0x5A5A5A5A5A5A5A5A, count)

@@ -46,12 +46,13 @@ def test_strerror_and_argument_errors_without_gpu():
     assert lib.skim_build_sketches(None) == -1
     out = ctypes.c_void_p()
     g = pkg.skim_graph(0, 0, None, None, 0)
-    p = pkg.skim_params(4, 4, 0, 0.1, 0, 0, 0, 0)
+    p = pkg.skim_params(4, 4, 0, 0.1, 0, 0, 0, 0, 0)
     assert lib.skim_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(out)) == -1  # n == 0
     g = pkg.skim_graph(4, 0, None, None, 0)
-    for bad in (pkg.skim_params(0, 4, 0, 0.1, 0, 0, 0, 0), pkg.skim_params(65, 4, 0, 0.1, 0, 0, 0, 0),
-                pkg.skim_params(4, 1, 0, 0.1, 0, 0, 0, 0), pkg.skim_params(4, 4, 0, 0.0, 0, 0, 0, 0),
-                pkg.skim_params(4, 4, 3, 0.1, 0, 0, 0, 0)):
+    for bad in (pkg.skim_params(0, 4, 0, 0.1, 0, 0, 0, 0, 0), pkg.skim_params(65, 4, 0, 0.1, 0, 0, 0, 0, 0),
+                pkg.skim_params(4, 1, 0, 0.1, 0, 0, 0, 0, 0), pkg.skim_params(4, 4, 0, 0.0, 0, 0, 0, 0, 0),
+                pkg.skim_params(4, 4, 3, 0.1, 0, 0, 0, 0, 0), pkg.skim_params(4, 4, 0, 0.1, 0, 0, 0, 0, 3),
+                pkg.skim_params(4, 4, 0, 0.1, 0, 0, 0, 0, 2)):  # bad rank mode; IC model needs l = 1
         assert lib.skim_create(ctypes.byref(g), ctypes.byref(bad), None, ctypes.byref(out)) == -1
 
 
