@@ -51,7 +51,8 @@ SMS = 152
 def workload_desc(w: synth.Workload, g) -> str:
     model = {0: f"uniform p={w.p}", 1: "weighted cascade", 2: "trivalency"}[w.prob_model]
     return (f"{w.name}: R-MAT scale {w.n_or_scale} edge factor {w.m_or_ef} ({g.m} edges after dedup), "
-            f"{model}, l={w.l}, k={w.k}; rank order + all sketches + {w.seeds} SKIM seeds + queries")
+            f"{model}, l={w.l}, k={w.k}; live-edge instances + rank order + all sketches + {w.seeds} SKIM seeds "
+            "+ queries")
 
 
 def step_traversals(gold: dict) -> int:
@@ -126,6 +127,52 @@ def traffic_record(kernel: str):
     return rec
 
 
+def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms):
+    """Roofline of one kernel group of the step, from its CUDA-event time and
+    the algorithmic work of one step (the oracle's counts, so redundant GPU
+    work is not credited).
+
+    rev_search  (memory): 16 B per reverse expansion (the two row bounds of
+                (v, i)) + 20 B per live in-edge (4 B neighbour id, 8 B read and
+                8 B write of its visited word).
+    fwd_search  (memory): 8 B per forward expansion (row bounds) + 12 B per
+                out-edge scanned (4 B id + 8 B live mask) + 16 B per live
+                out-edge (covered word read and write).
+    instances   (integer ALU): 2 m l coins (both CSR orders) x 27 int32 ops.
+    """
+    ms, launches = kt[kname]
+    sec = ms / 1000.0 / steps
+    sk, sm = gold["sketches"]["counters"], gold["skim"]["counters"]
+    common = {"kernel": kname, "avg_launch_ms": ms / max(1, launches), "launches_per_step": launches / steps,
+              "share_of_kernel_time": ms / total_ms if total_ms else None}
+    if kname == "instances":
+        ops = 2 * m * l * OPS_PER_COIN
+        peak = SMS * INT32_OPS_PER_SM_CLK * sm_max * 1e6 / 1e12
+        achieved = ops / sec / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)", "frac": achieved / peak,
+                "traffic": None, "peak_note": "derived: 152 SMs x 64 int32 ops/clk x max SM clock",
+                "algorithmic_units": f"2 x {m} edges x {l} instances coins x {OPS_PER_COIN} ops", **common}
+    if kname == "rev_search":
+        E = sk["rev_expansions"] + sm["rev_expansions"]
+        L = sk.get("rev_live_edges", 0) + sm.get("rev_live_edges", 0)
+        byts = 16 * E + 20 * L
+        units = f"{E} reverse expansions x 16 B + {L} live in-edges x 20 B per step"
+        key = "k_traverse_rev"
+    else:
+        E, S, L = sm["fwd_expansions"], sm["fwd_edge_scans"], sm.get("fwd_live_edges", 0)
+        byts = 8 * E + 12 * S + 16 * L
+        units = f"{E} forward expansions x 8 B + {S} out-edges x 12 B + {L} live out-edges x 16 B per step"
+        key = "k_traverse_fwd"
+    achieved = byts / sec / 1e9
+    trb = traffic_record(key)
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": trb["dram_bytes_per_launch"] if trb else None,
+            "traffic_note": (f"DRAM bytes per launch ({trb['launch']}), from profiles/traffic.json") if trb
+            else "no capture of the current source",
+            "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_units": units, **common}
+
+
 def max_over_ranks(elapsed: float, dist=None, device="cpu") -> float:
     """The slowest rank's time (the job's time); identity on one process."""
     if dist is None:
@@ -190,6 +237,8 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[50000.0, 200000.0, 500000.0])
     ap.add_argument("--batched-graphs", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--neighborhood-queries", type=int, default=300)
+    ap.add_argument("--no-rank-modes", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -227,22 +276,25 @@ def main():
     sk = pkg.Skim(g.n, src_d, dst_d, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob,
                   stream=stream.cuda_stream)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    part = {"ranks": [], "build": [], "greedy": [], "query": []}
+    part = {"instances": [], "ranks": [], "build": [], "greedy": [], "query": []}
 
     def step(record):
-        e = [ev() for _ in range(5)]
+        e = [ev() for _ in range(6)]
         e[0].record(stream)
-        sk.rank_order()
+        sk.instances()
         e[1].record(stream)
-        sk.build_sketches()
+        sk.rank_order()
         e[2].record(stream)
-        seeds, cov = sk.greedy(w.seeds)
+        sk.build_sketches()
         e[3].record(stream)
-        pkg.skim_oracle_query_batch(sk.ctx, q_off, len(qs), q_flat_d, q_out_d, 1)
+        seeds, cov = sk.greedy(w.seeds)
         e[4].record(stream)
+        pkg.skim_oracle_query_batch(sk.ctx, q_off, len(qs), q_flat_d, q_out_d, 1)
+        e[5].record(stream)
         if record:
             stream.synchronize()
-            for key, a, b in (("ranks", 0, 1), ("build", 1, 2), ("greedy", 2, 3), ("query", 3, 4)):
+            for key, a, b in (("instances", 0, 1), ("ranks", 1, 2), ("build", 2, 3), ("greedy", 3, 4),
+                              ("query", 4, 5)):
                 part[key].append(e[a].elapsed_time(e[b]) / 1000.0)
         return seeds, cov
 
@@ -302,6 +354,49 @@ def main():
                 "relative_to_seed_set": [float(b) / tot for b in bnd],
                 "exact_selections": int((skp < 0).sum()), "greedy_with_records_s": t_stops,
                 "bound_host_s": time.perf_counter() - a}
+
+    # the second query distribution of Section 6.2: neighbourhood seed sets
+    # (degree-proportional root, smallest ball with |S| nodes), one device batch
+    nb = synth.Neighborhoods(g.n, g.src, g.dst)
+    nsizes = synth.query_sizes(args.neighborhood_queries, ks.query ^ 0x4E42)
+    nqs = [nb.draw(int(z), ks.query ^ 0x4E42, q)[0] for q, z in enumerate(nsizes)]
+    n_off = np.zeros(len(nqs) + 1, np.uint64)
+    n_off[1:] = np.cumsum([len(q) for q in nqs])
+    n_flat_d = torch.from_numpy(np.concatenate(nqs).view(np.int32)).cuda()
+    n_out_d = torch.zeros(len(nqs), dtype=torch.float64, device="cuda")
+    nt = []
+    for i in range(4):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        pkg.skim_oracle_query_batch(sk.ctx, n_off, len(nqs), n_flat_d, n_out_d, 1)
+        e1.record(stream)
+        stream.synchronize()
+        if i:
+            nt.append(e0.elapsed_time(e1) / 1000.0)
+    neighborhood = {"queries": len(nqs), "seeds": int(n_off[-1]), "qps": len(nqs) / statistics.median(nt)}
+
+    # the other rank readings of the same workload (untimed, once each):
+    # structured permutation ranks (Section 3.1) with SKIM, and IC-model
+    # sketches (Section 3.2, l -> infinity, k*n positions, unpruned searches)
+    rank_modes = {}
+    if not args.no_rank_modes:
+        for name, mode, lm in (("permutation", pkg.RANKS_PERMUTATION, w.l), ("ic_model", pkg.RANKS_IC_MODEL, 1)):
+            with pkg.Skim(g.n, src_d, dst_d, lm, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob,
+                          stream=stream.cuda_stream, rank_mode=mode) as s3:
+                torch.cuda.synchronize()
+                a = time.perf_counter()
+                s3.build_sketches()
+                torch.cuda.synchronize()
+                tb = time.perf_counter() - a
+                st = s3.stats()
+                rec = {"l": lm, "k": w.k, "build_s": tb, "positions": st["ranks"], "coins": st["rev_coins"],
+                       "coins_per_s": st["rev_coins"] / tb}
+                if mode == pkg.RANKS_PERMUTATION:
+                    a = time.perf_counter()
+                    s3.greedy(w.seeds)
+                    torch.cuda.synchronize()
+                    rec["s_to_50_seeds"] = time.perf_counter() - a
+                rank_modes[name] = rec
 
     # serving: Poisson query streams replayed through the continuous-batching
     # server on the same resident sketches, against the one-query-at-a-time form
@@ -374,27 +469,14 @@ def main():
     e2e_t = max_over_ranks(statistics.median(e2e_times), dist, device="cuda")
     e2e_value = job_value(world, 1, t_alg, e2e_t)
 
-    # roofline of the dominant kernel: the batched reverse search (integer ALU bound)
-    rev_ms, rev_launches = kt["rev_search"]
-    coins_alg = (gold["sketches"]["counters"]["rev_edge_scans"] + gold["skim"]["counters"]["rev_edge_scans"])
-    rev_s_per_step = rev_ms / 1000.0 / args.steps
-    achieved = coins_alg * OPS_PER_COIN / rev_s_per_step / 1e12
+    # roofline of the dominant kernel group (largest device time per step)
     sm_max = (clk or {}).get("sm_max_mhz")
     if not sm_max:
         sm_max = json.load(open(PEAKS)).get("sm_max_mhz", 2070.0) if os.path.exists(PEAKS) else 2070.0
-    peak = SMS * INT32_OPS_PER_SM_CLK * sm_max * 1e6 / 1e12
-    trb = traffic_record("k_traverse_rev")
-    per_launch_traffic = trb["dram_bytes_per_launch"] if trb else None
+    hbm_peak = json.load(open(PEAKS)).get("hbm_gbs", 6800.0) if os.path.exists(PEAKS) else 6800.0
     total_ms = sum(v[0] for v in kt.values())
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)",
-                "frac": achieved / peak, "traffic": per_launch_traffic,
-                "traffic_note": (f"DRAM bytes of one ncu-captured launch ({trb['launch']}, {trb['duration_ms']} ms), "
-                                 "from profiles/traffic.json") if trb else "no capture of the current source",
-                "kernel": "k_traverse<reverse> (batched reverse search)",
-                "avg_launch_ms": rev_ms / max(1, rev_launches), "launches_per_step": rev_launches / args.steps,
-                "share_of_kernel_time": rev_ms / total_ms if total_ms else None,
-                "peak_note": "derived: 152 SMs x 64 int32 ops/clk x max SM clock (no measured int peak)",
-                "algorithmic_units": f"{coins_alg} oracle coin evaluations per step x {OPS_PER_COIN} ops"}
+    dominant = max(("rev_search", "fwd_search", "instances"), key=lambda kname: kt[kname][0])
+    roofline = kernel_roofline(dominant, kt, gold, g.m, w.l, args.steps, sm_max, hbm_peak, total_ms)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1000.0, "higher_is_better": True,
@@ -406,12 +488,15 @@ def main():
             "s_to_50_seeds": statistics.median(part["greedy"]),
             "sketch_build_s": statistics.median(part["build"]),
             "rank_order_s": statistics.median(part["ranks"]),
+            "instances_s": statistics.median(part["instances"]),
             "oracle_qps": len(qs) / statistics.median(part["query"]),
             "query_p50_ms": lat[len(lat) // 2], "query_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "single_query_qps": 1000.0 / (sum(lat) / len(lat)),
             "serving": serving,
             "batched": batched,
             "adaptive_error": adaptive,
+            "neighborhood_queries": neighborhood,
+            "rank_modes": rank_modes,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -131,6 +131,21 @@ int skim_autotune_batch_lanes(skim_ctx *ctx, const uint32_t *candidates, uint32_
  * sketches are unaffected (the ranks themselves do not change). */
 int skim_rank_order(skim_ctx *ctx);
 
+/* Generate the l live-edge instances (Section 2; Algorithms 1 and 2 take a set
+ * of instances): every edge's coin in every instance is drawn once (the coin
+ * above), giving a 64-bit live mask per edge in both CSR orders and, per
+ * (node v, instance i), the list of v's live in-neighbours.  Searches then
+ * walk live edges only.  Done by skim_create; exposed so that a caller can
+ * time it.  Restarts SKIM (as skim_greedy_reset); sketches are unaffected (the
+ * coins do not change).  The IC model (SKIM_RANKS_IC_MODEL) has an instance
+ * per rank position and draws coins during the searches instead, as does a
+ * context with 2^32 or more live (edge, instance) pairs. */
+int skim_instances(skim_ctx *ctx);
+
+/* live_pairs: live (edge, instance) pairs of the last skim_instances;
+ * materialised: 1 if searches use the materialised instances (host outputs). */
+int skim_instance_stats(skim_ctx *ctx, uint64_t *live_pairs, int *materialised);
+
 /* Algorithm 2 (Section 5.2): combined bottom-k reachability sketches X_v of
  * all nodes (Eq. combinedrs), computed by rank-batched pruned reverse
  * searches; the result equals the definition exactly.  Sketches stay in
@@ -247,6 +262,7 @@ int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
  *   SKIM_K_RANKS rank order of the n*l pairs
  *   SKIM_K_QUERY union-estimator queries
  *   SKIM_K_SETUP CSR construction and validation
+ *   SKIM_K_INSTANCES generation of the live-edge instances (skim_instances)
  * Turning timing on creates a pool of 2048 CUDA events at once (so that no
  * event is created inside a timed bracket).  A bracket that holds a host
  * synchronisation (SKIM_K_STEP) also counts the host's share of that wait. */
@@ -258,7 +274,8 @@ int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
 #define SKIM_K_RANKS 5
 #define SKIM_K_QUERY 6
 #define SKIM_K_SETUP 7
-#define SKIM_K_COUNT 8
+#define SKIM_K_INSTANCES 8
+#define SKIM_K_COUNT 9
 int skim_set_timing(skim_ctx *ctx, int on);
 
 /* Number of kernels this library has launched in the calling process since it

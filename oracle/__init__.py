@@ -22,9 +22,10 @@ _SRC = os.path.join(_HERE, "skim_oracle.c")
 _LIB = os.path.join(_HERE, "libskim_oracle.so")
 _lib = None
 
-NCOUNT = 8
+NCOUNT = 10
 COUNTER_NAMES = ("rev_expansions", "rev_edge_scans", "insertions", "fwd_expansions",
-                 "fwd_edge_scans", "ranks_processed", "ranks_consumed", "index_erased")
+                 "fwd_edge_scans", "ranks_processed", "ranks_consumed", "index_erased",
+                 "rev_live_edges", "fwd_live_edges")
 
 
 def build(force: bool = False) -> str:

@@ -169,8 +169,11 @@ static int cmp_kv(const void *a, const void *b) {
  *  [4] forward edge scans
  *  [5] ranks processed (BFS sources not skipped)
  *  [6] ranks consumed (rank cursor advance, skipped ones included)
- *  [7] index entries erased */
-#define OR_NCOUNT 8
+ *  [7] index entries erased
+ *  [8] live reverse edges: over the reverse expansions, the in-edges that are
+ *      live in the expansion's instance (whether or not their tail is new)
+ *  [9] live forward edges: the same over the forward expansions */
+#define OR_NCOUNT 10
 
 /* ------------------------------------------------------------------------ */
 /* Eq. combinedrs by definition: X_u = bottom-k of the ranks of R_u, R_u    */
@@ -337,7 +340,9 @@ int or_build_sketches_mode(uint32_t n, uint64_t m, const uint32_t *src, const ui
                 cnt[1] += g.rptr[v + 1] - g.rptr[v];
                 for (uint64_t e = g.rptr[v]; e < g.rptr[v + 1]; e++) {
                     uint32_t w = g.rcol[e];                 /* in-edge w -> v */
-                    if (stamp[w] != bfs_id && live(&g, w, v, i)) { stamp[w] = bfs_id; queue[tail++] = w; }
+                    if (!live(&g, w, v, i)) continue;
+                    cnt[8]++;
+                    if (stamp[w] != bfs_id) { stamp[w] = bfs_id; queue[tail++] = w; }
                 }
             }
             if (any) cnt[5]++;
@@ -409,7 +414,9 @@ int or_build_ic_sketches(uint32_t n, uint64_t m, const uint32_t *src, const uint
             cnt[1] += g.rptr[v + 1] - g.rptr[v];
             for (uint64_t e = g.rptr[v]; e < g.rptr[v + 1]; e++) {
                 uint32_t w = g.rcol[e];
-                if (stamp[w] != bfs_id && live(&g, w, v, t)) { stamp[w] = bfs_id; queue[tail++] = w; }
+                if (!live(&g, w, v, t)) continue;
+                cnt[8]++;
+                if (stamp[w] != bfs_id) { stamp[w] = bfs_id; queue[tail++] = w; }
             }
         }
     }
@@ -563,7 +570,9 @@ int or_skim_mode(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *ds
                 cnt[1] += g.rptr[v + 1] - g.rptr[v];
                 for (uint64_t e = g.rptr[v]; e < g.rptr[v + 1]; e++) {
                     uint32_t w = g.rcol[e];
-                    if (stamp[w] != bfs_id && live(&g, w, v, i)) { stamp[w] = bfs_id; queue[tail++] = w; }
+                    if (!live(&g, w, v, i)) continue;
+                    cnt[8]++;
+                    if (stamp[w] != bfs_id) { stamp[w] = bfs_id; queue[tail++] = w; }
                 }
             }
         }
@@ -617,7 +626,9 @@ int or_skim_mode(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *ds
                 for (uint64_t e = g.fptr[v]; e < g.fptr[v + 1]; e++) {
                     uint32_t w = g.fcol[e];
                     uint64_t pw = (uint64_t)w * l + i;
-                    if (!covered[pw] && live(&g, v, w, i)) { covered[pw] = 1; queue[tail++] = w; }
+                    if (!live(&g, v, w, i)) continue;
+                    cnt[9]++;
+                    if (!covered[pw]) { covered[pw] = 1; queue[tail++] = w; }
                 }
             }
         }

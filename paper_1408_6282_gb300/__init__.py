@@ -21,7 +21,8 @@ _ERR = {-1: "SKIM_EINVAL", -2: "SKIM_ENOMEM", -3: "SKIM_ENOTBUILT", -4: "SKIM_ET
         -6: "SKIM_EGRAPH", -7: "SKIM_ERANGE"}
 PROB_UNIFORM, PROB_WC, PROB_TRIVALENCY = 0, 1, 2
 RANKS_UNIFORM, RANKS_PERMUTATION, RANKS_IC_MODEL = 0, 1, 2
-KERNEL_NAMES = ("rev_search", "fwd_search", "accept", "record_sort", "skim_step", "rank_order", "query", "setup")
+KERNEL_NAMES = ("rev_search", "fwd_search", "accept", "record_sort", "skim_step", "rank_order", "query", "setup",
+                "instances")
 STAT_NAMES = ("rev_visits", "rev_coins", "insertions", "fwd_visits", "fwd_coins", "batches", "ranks", "retries",
               "rev_edges", "fwd_edges")
 
@@ -70,6 +71,8 @@ def load():
     lib.skim_get_stats.argtypes = [vp, vp, u32]
     lib.skim_destroy.argtypes = [vp]
     lib.skim_rank_order.argtypes = [vp]
+    lib.skim_instances.argtypes = [vp]
+    lib.skim_instance_stats.argtypes = [vp, vp, vp]
     lib.skim_set_timing.argtypes = [vp, C.c_int]
     lib.skim_kernel_times.argtypes = [vp, vp, vp, u32, C.c_int]
     lib.skim_kernel_launches.argtypes = [vp]
@@ -190,6 +193,10 @@ def discrepancy_bound(delta, tau, kprime, step: float, bins: int = 4096, conf=(0
 
 def skim_node_estimates(ctx: int, out, out_on_device: int = 0):
     _check(load().skim_node_estimates(ctx, _ptr(out), out_on_device), "skim_node_estimates")
+
+
+def skim_instances(ctx: int):
+    _check(load().skim_instances(ctx), "skim_instances")
 
 
 def skim_greedy_reset(ctx: int):
@@ -363,6 +370,17 @@ class Skim:
 
     def greedy_reset(self):
         skim_greedy_reset(self.ctx)
+
+    def instances(self):
+        """Regenerate the live-edge instances (done at creation)."""
+        skim_instances(self.ctx)
+
+    def instance_stats(self) -> tuple[int, bool]:
+        """(live edge-instance pairs, whether searches use them)."""
+        lp = np.zeros(1, np.uint64)
+        mt = np.zeros(1, np.int32)
+        _check(load().skim_instance_stats(self.ctx, _ptr(lp), _ptr(mt)), "skim_instance_stats")
+        return int(lp[0]), bool(mt[0])
 
     def node_estimates(self) -> np.ndarray:
         """Single-node influence estimates from every node's own sketch."""

@@ -38,6 +38,13 @@ struct skim_ctx {
     // them the sketch build processes
     int rank_mode = 0;
     uint64_t npos = 0, nbuild = 0;
+    // materialised instances (Section 2): per-edge live masks in both CSR
+    // orders and the node-major live in-neighbour rows of every (v, i)
+    bool mat = false;
+    uint64_t *rmask = nullptr, *fmask = nullptr, *loff = nullptr;
+    uint32_t *rlive = nullptr;
+    uint32_t *rrow = nullptr, *rev2fwd = nullptr;  // per reverse CSR edge: head, forward position
+    uint64_t rlive_cap = 0, live_total = 0;
     uint64_t rank_key = 0;
     // graphs of a batch (skim_create_batch): per-node rank bases, per-edge
     // thresholds, node offsets of the graphs
@@ -239,7 +246,10 @@ int reset_queue(skim_ctx *c, uint64_t used) {
 TravArgs base_args(skim_ctx *c, bool forward) {
     TravArgs a{};
     a.ptr = forward ? c->fptr : c->rptr;
-    a.col = forward ? c->fcol : c->rcol;
+    a.col = forward ? c->fcol : (c->mat ? c->rlive : c->rcol);
+    a.mat = c->mat ? 1 : 0;
+    a.loff = c->loff;
+    a.lmask = forward ? c->fmask : nullptr;
     a.cm = c->cm;
     a.q = c->q;
     a.qcap = c->qcap;
@@ -542,6 +552,39 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
     }
 }
 
+// Materialise the l live-edge instances (Section 2: Algorithms 1 and 2 take a
+// set of instances): every edge's coins once per instance, then the live
+// in-neighbour rows.  The IC model has an instance per position and keeps
+// drawing coins during the searches; so does a context whose live pairs would
+// not fit 32-bit row offsets.
+int make_instances(skim_ctx *c) {
+    c->mat = false;
+    if (c->rank_mode == SKIM_RANKS_IC_MODEL) return SKIM_OK;
+    KTimer kt(c, SKIM_K_INSTANCES);
+    if (!c->loff) {
+        RC(dalloc(c, &c->rmask, std::max<uint64_t>(c->m, 1)));
+        RC(dalloc(c, &c->fmask, std::max<uint64_t>(c->m, 1)));
+        RC(dalloc(c, &c->loff, c->nl + 1));
+    }
+    CK(c, launch_live_masks(c->rrow, c->rcol, c->rhe, c->rtm1, c->rev2fwd, c->cm, c->m, c->l, c->rmask, c->fmask,
+                            c->st));
+    CK(c, launch_live_count(c->rptr, c->rmask, c->n, c->l, c->loff, c->st));
+    CK(c, cudaMemsetAsync(c->loff + c->nl, 0, sizeof(uint64_t), c->st));
+    CK(c, exclusive_scan_u64(c->loff, c->loff, c->nl + 1, nullptr, c->ws, c->st));
+    CK(c, cudaMemcpyAsync(&c->live_total, c->loff + c->nl, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    if (c->live_total >= (1ull << 32)) return SKIM_OK;
+    if (c->live_total > c->rlive_cap) {
+        dfree(c->rlive);
+        c->rlive_cap = 0;
+        RC(dalloc(c, &c->rlive, c->live_total));
+        c->rlive_cap = c->live_total;
+    }
+    CK(c, launch_live_fill(c->rptr, c->rcol, c->rmask, c->n, c->l, c->loff, c->rlive ? c->rlive : nullptr, c->st));
+    c->mat = true;
+    return SKIM_OK;
+}
+
 int rank_order(skim_ctx *c) {
     {
         KTimer kt(c, SKIM_K_RANKS);
@@ -639,6 +682,7 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->covered); dfree(c->seg_start); dfree(c->pend_trav); dfree(c->pend_erase);
     dfree(c->size); dfree(c->seg_len); dfree(c->idx); dfree(c->chosen);
     dfree(c->rec_tau); dfree(c->rec_kp);
+    dfree(c->rmask); dfree(c->fmask); dfree(c->loff); dfree(c->rlive); dfree(c->rrow); dfree(c->rev2fwd);
     dfree(c->qk); dfree(c->qv); dfree(c->qseeds); dfree(c->qoff); dfree(c->qout);
     dfree(c->qtop); dfree(c->qtopu);
     if (c->qpart) cudaFree(c->qpart);
@@ -739,7 +783,8 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         // re-running a batch with fewer lanes stays rare
         const uint64_t lanes_max = std::min<uint64_t>(npos, prm->batch_lanes ? prm->batch_lanes : (1u << 21));
         const uint64_t rcap = std::min<uint64_t>(std::max<uint64_t>(16ull * lanes_max, 1u << 20), 1ull << 26);
-        size_t ws = std::max({scan_workspace_bytes(static_cast<size_t>(n) + 1), radix_workspace_bytes(m),
+        size_t ws = std::max({scan_workspace_bytes(static_cast<size_t>(n) + 1), scan_workspace_bytes(nl + 1),
+                              radix_workspace_bytes(m),
                               radix_workspace_bytes(rcap), scan_workspace_bytes(static_cast<size_t>(kMaxWords) * 64)});
         c->ws_bytes = ws;
         TRYC(cudaMalloc(&c->ws, ws));
@@ -769,7 +814,9 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
             TRY(dalloc(c, &v2, m));
             TRYC(launch_make_rev_keys(dsrc, ddst, m, k1, v1, c->st));
             TRYC(radix_sort_pairs(k1, v1, k2, v2, m, 32 + bitlen(n - 1), c->ws, c->st));
-            TRYC(launch_split_rev(k1, m, c->rcol, c->st));
+            TRY(dalloc(c, &c->rrow, m));
+            TRY(dalloc(c, &c->rev2fwd, m));
+            TRYC(launch_split_rev(k1, v1, m, c->rcol, c->rrow, c->rev2fwd, c->st));
             TRYC(cudaStreamSynchronize(c->st));
             dfree(k1); dfree(k2); dfree(v1); dfree(v2);
         }
@@ -795,6 +842,7 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
             TRYC(launch_wc_thresholds(c->rptr, n, c->thr_wc, c->st));
         }
         c->cm.thr_wc = c->thr_wc;
+        TRY(make_instances(c));
         // rank order of the n*l pairs
         TRY(dalloc(c, &c->srank, npos));
         TRY(dalloc(c, &c->spair, npos));
@@ -929,6 +977,7 @@ int skim_create_batch(const skim_graph *graphs, const skim_params *prm, uint32_t
     if (!ok) return fail(fail_cuda(c, cudaGetLastError()));
     c->cm.model = 3;
     c->batch_count = count;
+    if ((rc = make_instances(c))) return fail(rc);
     if ((rc = rank_order(c))) return fail(rc);
     *out = c;
     return SKIM_OK;
@@ -972,6 +1021,25 @@ int skim_rank_order(skim_ctx *c) {
     }
     RC(rank_order(c));
     c->sk_init = false;
+    return SKIM_OK;
+}
+
+int skim_instances(skim_ctx *c) {
+    if (!c) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    if (c->batch_active) {
+        RC(clear_batch(c));
+        c->batch_active = false;
+    }
+    RC(make_instances(c));
+    c->sk_init = false;
+    return SKIM_OK;
+}
+
+int skim_instance_stats(skim_ctx *c, uint64_t *live_pairs, int *materialised) {
+    if (!c || !live_pairs || !materialised) return SKIM_EINVAL;
+    *live_pairs = c->live_total;
+    *materialised = c->mat ? 1 : 0;
     return SKIM_OK;
 }
 

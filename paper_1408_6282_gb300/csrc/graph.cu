@@ -45,14 +45,20 @@ __global__ void k_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint64
     for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < m;
          e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         key[e] = (static_cast<uint64_t>(dst[e]) << 32) | src[e];
-        val[e] = 0;
+        val[e] = static_cast<uint32_t>(e);  // forward CSR position (the input is sorted by (src, dst))
     }
 }
 
-__global__ void k_split_rev(const uint64_t *key, uint64_t m, uint32_t *rcol) {
+// reverse CSR from the (dst, src)-sorted keys: column (src), row (dst) and the
+// edge's forward CSR position
+__global__ void k_split_rev(const uint64_t *key, const uint32_t *val, uint64_t m, uint32_t *rcol, uint32_t *rrow,
+                            uint32_t *rev2fwd) {
     for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < m;
-         e += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+         e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         rcol[e] = static_cast<uint32_t>(key[e]);
+        rrow[e] = static_cast<uint32_t>(key[e] >> 32);
+        rev2fwd[e] = val[e];
+    }
 }
 
 __global__ void k_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr) {
@@ -70,6 +76,98 @@ __global__ void k_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_t
         for (uint32_t e = ptr[v] + lane; e < ptr[v + 1]; e += 32) {
             const uint32_t c = col[e];
             he[e] = reverse ? edge_state(coin_key, c, v) : edge_state(coin_key, v, c);
+        }
+    }
+}
+
+// ---- materialised instances ------------------------------------------------
+// Live threshold of CSR edge e in row r with other end x (the head of the edge
+// is r in the reverse CSR and x in the forward one).
+SKIM_DEV uint64_t row_edge_tm1(const CoinModel &cm, const uint64_t *tm1e, uint64_t e, uint32_t r, uint32_t x,
+                               int reverse) {
+    const uint32_t head = reverse ? r : x, tail = reverse ? x : r;
+    if (cm.model == 3) return tm1e[e];
+    if (cm.model == 0) return cm.tm1_uniform;
+    if (cm.model == 1) return cm.thr_wc[head];
+    return cm.tm1_class[fmix(cm.prob_key ^ ((static_cast<uint64_t>(tail) << 32) | head)) % 3u];
+}
+
+// One thread per edge (reverse CSR order): bit i of the mask is the coin of
+// the edge in instance i, fmix(he + (i+1) G) <= tm1 (two independent chains
+// per step).  The mask is stored at the edge's reverse and forward positions.
+__global__ void k_live_masks(const uint32_t *rrow, const uint32_t *rcol, const uint64_t *rhe, const uint64_t *rtm1,
+                             const uint32_t *rev2fwd, CoinModel cm, uint64_t m, uint32_t l, uint64_t *rmask,
+                             uint64_t *fmask) {
+    for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < m;
+         e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t t1 = row_edge_tm1(cm, rtm1, e, rrow[e], rcol[e], 1);
+        const uint64_t h = rhe[e];
+        uint64_t mk = 0;
+        uint32_t i = 0;
+        for (; i + 1 < l; i += 2) {
+            const uint64_t c0 = fmix(h + kGolden * (i + 1)), c1 = fmix(h + kGolden * (i + 2));
+            mk |= (static_cast<uint64_t>(c0 <= t1) << i) | (static_cast<uint64_t>(c1 <= t1) << (i + 1));
+        }
+        if (i < l) mk |= static_cast<uint64_t>(fmix(h + kGolden * (i + 1)) <= t1) << i;
+        rmask[e] = mk;
+        fmask[rev2fwd[e]] = mk;
+    }
+}
+
+// One warp per node v, tiles of 32 in-edges (one per lane): for instance b
+// the tile holds popc(ballot(bit b)) live in-edges; lane b % 32 keeps the
+// counts of instances b < 32 and b >= 32.
+__global__ void k_live_count(const uint32_t *rptr, const uint64_t *rmask, uint32_t n, uint32_t l, uint64_t *off) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
+        uint64_t c0 = 0, c1 = 0;
+        const uint32_t e1 = rptr[v + 1];
+        for (uint32_t e0 = rptr[v]; e0 < e1; e0 += 32) {
+            const uint64_t mk = e0 + lane < e1 ? rmask[e0 + lane] : 0;
+            uint64_t any = mk;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(kFull, any, o);
+            for (uint64_t bits = any; bits; bits &= bits - 1) {
+                const uint32_t b = __ffsll(bits) - 1;
+                const uint32_t c = __popc(__ballot_sync(kFull, (mk >> b) & 1ull));
+                if (lane == (b & 31)) {
+                    if (b < 32) c0 += c;
+                    else c1 += c;
+                }
+            }
+        }
+        const uint64_t base = static_cast<uint64_t>(v) * l;
+        if (lane < l) off[base + lane] = c0;
+        if (lane + 32 < l) off[base + lane + 32] = c1;
+    }
+}
+
+// Same tiles: the live in-neighbours of (v, b) are written in row order from
+// off[v*l + b] on; lane b % 32 keeps the write cursors of instances b, b + 32.
+__global__ void k_live_fill(const uint32_t *rptr, const uint32_t *rcol, const uint64_t *rmask, uint32_t n,
+                            uint32_t l, const uint64_t *off, uint32_t *live) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
+        const uint64_t base = static_cast<uint64_t>(v) * l;
+        uint64_t p0 = lane < l ? off[base + lane] : 0, p1 = lane + 32 < l ? off[base + lane + 32] : 0;
+        const uint32_t e1 = rptr[v + 1];
+        for (uint32_t e0 = rptr[v]; e0 < e1; e0 += 32) {
+            const bool in = e0 + lane < e1;
+            const uint64_t mk = in ? rmask[e0 + lane] : 0;
+            const uint32_t w = in ? rcol[e0 + lane] : 0;
+            uint64_t any = mk;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(kFull, any, o);
+            for (uint64_t bits = any; bits; bits &= bits - 1) {
+                const uint32_t b = __ffsll(bits) - 1;
+                const unsigned bb = __ballot_sync(kFull, (mk >> b) & 1ull);
+                const uint64_t cur = __shfl_sync(kFull, b < 32 ? p0 : p1, b & 31);
+                if ((mk >> b) & 1ull) live[cur + __popc(bb & lanemask_lt())] = w;
+                if (lane == (b & 31)) {
+                    if (b < 32) p0 += __popc(bb);
+                    else p1 += __popc(bb);
+                }
+            }
         }
     }
 }
@@ -312,10 +410,11 @@ cudaError_t launch_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint6
     k_make_rev_keys<<<grid_for(m, 256), 256, 0, s>>>(src, dst, m, key, val);
     return cudaGetLastError();
 }
-cudaError_t launch_split_rev(const uint64_t *key, uint64_t m, uint32_t *rcol, cudaStream_t s) {
+cudaError_t launch_split_rev(const uint64_t *key, const uint32_t *val, uint64_t m, uint32_t *rcol, uint32_t *rrow,
+                             uint32_t *rev2fwd, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
     note_launch();
-    k_split_rev<<<grid_for(m, 256), 256, 0, s>>>(key, m, rcol);
+    k_split_rev<<<grid_for(m, 256), 256, 0, s>>>(key, val, m, rcol, rrow, rev2fwd);
     return cudaGetLastError();
 }
 cudaError_t launch_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr, cudaStream_t s) {
@@ -327,6 +426,27 @@ cudaError_t launch_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_
                                uint64_t *he, cudaStream_t s) {
     note_launch();
     k_edge_states<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(ptr, col, n, coin_key, reverse, he);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_live_masks(const uint32_t *rrow, const uint32_t *rcol, const uint64_t *rhe, const uint64_t *rtm1,
+                              const uint32_t *rev2fwd, const CoinModel &cm, uint64_t m, uint32_t l, uint64_t *rmask,
+                              uint64_t *fmask, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    note_launch();
+    k_live_masks<<<grid_for(m, 256), 256, 0, s>>>(rrow, rcol, rhe, rtm1, rev2fwd, cm, m, l, rmask, fmask);
+    return cudaGetLastError();
+}
+cudaError_t launch_live_count(const uint32_t *rptr, const uint64_t *rmask, uint32_t n, uint32_t l, uint64_t *off,
+                              cudaStream_t s) {
+    note_launch();
+    k_live_count<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(rptr, rmask, n, l, off);
+    return cudaGetLastError();
+}
+cudaError_t launch_live_fill(const uint32_t *rptr, const uint32_t *rcol, const uint64_t *rmask, uint32_t n, uint32_t l,
+                             const uint64_t *off, uint32_t *live, cudaStream_t s) {
+    note_launch();
+    k_live_fill<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(rptr, rcol, rmask, n, l, off, live);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,12 @@ struct TravArgs {
     uint32_t l;
     uint64_t *pend_trav;        // per node: instances whose expansion was spilled
     uint64_t *pend_erase;       // per node: instances whose index erasure was spilled
+    // materialised instances (mat != 0): reverse searches walk the live
+    // in-neighbours of (node v, instance i), col[loff[v*l+i] .. loff[v*l+i+1]);
+    // forward searches test the per-edge live masks lmask (bit i = live in i)
+    int mat;
+    const uint64_t *loff;
+    const uint64_t *lmask;
 };
 
 // graph.cu
@@ -64,10 +70,22 @@ cudaError_t launch_degree_count(const uint32_t *idx, uint64_t m, uint64_t *deg, 
 cudaError_t launch_u64_to_u32(const uint64_t *in, uint32_t *out, size_t n, cudaStream_t s);
 cudaError_t launch_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint64_t m, uint64_t *key, uint32_t *val,
                                  cudaStream_t s);
-cudaError_t launch_split_rev(const uint64_t *key, uint64_t m, uint32_t *rcol, cudaStream_t s);
+cudaError_t launch_split_rev(const uint64_t *key, const uint32_t *val, uint64_t m, uint32_t *rcol, uint32_t *rrow,
+                             uint32_t *rev2fwd, cudaStream_t s);
 cudaError_t launch_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr, cudaStream_t s);
 // Per-edge coin-stream states of a CSR: he[e] for edge (row node, col[e]);
 // reverse = 1 when rows are heads (edge col[e] -> row).
+// Materialised instances (Section 2: the l live-edge graphs): live masks of
+// every CSR edge (bit i = coin of instance i), and the node-major lists of live
+// in-neighbours: counts per (v, i) into off[v*l + i], then (after an exclusive
+// scan of off) the sources themselves.
+cudaError_t launch_live_masks(const uint32_t *rrow, const uint32_t *rcol, const uint64_t *rhe, const uint64_t *rtm1,
+                              const uint32_t *rev2fwd, const CoinModel &cm, uint64_t m, uint32_t l, uint64_t *rmask,
+                              uint64_t *fmask, cudaStream_t s);
+cudaError_t launch_live_count(const uint32_t *rptr, const uint64_t *rmask, uint32_t n, uint32_t l, uint64_t *off,
+                              cudaStream_t s);
+cudaError_t launch_live_fill(const uint32_t *rptr, const uint32_t *rcol, const uint64_t *rmask, uint32_t n, uint32_t l,
+                             const uint64_t *off, uint32_t *live, cudaStream_t s);
 cudaError_t launch_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_t n, uint64_t coin_key, int reverse,
                                uint64_t *he, cudaStream_t s);
 cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out, cudaStream_t s);

@@ -141,21 +141,43 @@ SKIM_DEV bool spill_if_full(const TravArgs &A, unsigned long long s, uint32_t ni
     return true;
 }
 
+// Live in-neighbour row of (u, lane j of word t) in the materialised instances.
+SKIM_DEV uint32_t live_row_len(const TravArgs &A, uint32_t u, uint32_t t, int j) {
+    const uint64_t r = static_cast<uint64_t>(u) * A.l + A.lane_inst[static_cast<size_t>(t) * 64 + j];
+    return static_cast<uint32_t>(A.loff[r + 1] - A.loff[r]);
+}
+
 // Warp-collective: queue the expansion of lane bits `nb` of entry (u, t)
-// (table slot `slot`).
+// (table slot `slot`).  With materialised instances each lane gets items of
+// its own (its row of live in-neighbours; none if the row is empty).
+template <bool MAT>
 SKIM_DEV void push_rev(const TravArgs &A, Acc &acc, uint32_t u, uint32_t t, uint64_t nb, uint64_t slot) {
     uint32_t ni = 0;
-    if (nb) ni = n_chunks(A.ptr[u + 1] - A.ptr[u], nb);
+    if (MAT) {
+        for (uint64_t m = nb; m; m &= m - 1) ni += n_chunks(live_row_len(A, u, t, __ffsll(m) - 1));
+    } else if (nb) {
+        ni = n_chunks(A.ptr[u + 1] - A.ptr[u], nb);
+    }
     if (!__any_sync(kFull, ni != 0)) return;
     unsigned long long s = reserve_slots(A, acc, ni);
     if (ni && spill_if_full(A, s, ni)) {
         atomicOr(reinterpret_cast<unsigned long long *>(&A.pend[slot]), nb);
         return;
     }
-    for (uint32_t c = 0; c < ni; c++) write_item(A, s + c, u, (t << kChunkBits) | c, nb);
+    if (MAT) {
+        uint32_t c = 0;
+        for (uint64_t m = nb; m; m &= m - 1) {
+            const int j = __ffsll(m) - 1;
+            const uint32_t nc = n_chunks(live_row_len(A, u, t, j));
+            for (uint32_t q = 0; q < nc; q++, c++) write_item(A, s + c, u, (t << kChunkBits) | q, 1ull << j);
+        }
+    } else {
+        for (uint32_t c = 0; c < ni; c++) write_item(A, s + c, u, (t << kChunkBits) | c, nb);
+    }
 }
 
 // Warp-collective: lanes with `act` visit node u with lane bits `bits` in word t.
+template <bool MAT>
 SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32_t t, uint64_t bits) {
     if (!__any_sync(kFull, act && bits)) return;
     uint64_t nb = 0;
@@ -189,7 +211,7 @@ SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32
         }
     }
     acc.visits += __popcll(nb);
-    push_rev(A, acc, u, t, nb, slot);
+    push_rev<MAT>(A, acc, u, t, nb, slot);
 }
 
 // Warp-collective: queue the expansion of node w in instances `trav` and the
@@ -280,6 +302,7 @@ struct Desc {
     bool erase, single;
 };
 
+template <bool FWD, bool MAT>
 SKIM_DEV Desc describe(const TravArgs &A, bool have, const Item &it) {
     Desc d{};
     if (!have || it.w == kNopTag) return d;
@@ -293,6 +316,14 @@ SKIM_DEV Desc describe(const TravArgs &A, bool have, const Item &it) {
         return d;
     }
     const uint32_t chunk = it.w & ((1u << kChunkBits) - 1);
+    if (MAT && !FWD) {  // one lane: its row of live in-neighbours
+        const uint32_t t = it.w >> kChunkBits;
+        const uint64_t r = static_cast<uint64_t>(it.v) * A.l + A.lane_inst[static_cast<size_t>(t) * 64 + (__ffsll(it.mask) - 1)];
+        const uint32_t e0 = static_cast<uint32_t>(A.loff[r]), e1 = static_cast<uint32_t>(A.loff[r + 1]);
+        d.begin = e0 + chunk * kChunk;
+        d.cnt = min(kChunk, e1 - d.begin);
+        return d;
+    }
     const uint32_t e0 = A.ptr[it.v], e1 = A.ptr[it.v + 1];
     const uint32_t ce = chunk_edges(e1 - e0, it.mask);
     d.begin = e0 + chunk * ce;
@@ -331,9 +362,12 @@ constexpr int kUnroll = SKIM_UNROLL;  // edges per lane per step: independent ha
 #define SKIM_PREFETCH 1
 #endif
 
-// Coin-stream state of CSR edge idx whose other end is x.
-template <bool FWD>
+// Per-edge value the live test needs: the coin-stream state of CSR edge idx
+// (other end x), or with materialised instances its live mask (forward; the
+// reverse live rows need nothing).
+template <bool FWD, bool MAT>
 SKIM_DEV uint64_t edge_key(const TravArgs &A, const Desc &d, uint32_t idx, uint32_t x) {
+    if (MAT) return FWD ? A.lmask[idx] : 0;
 #if SKIM_HE_TABLE
     return A.he[idx];
 #else
@@ -343,20 +377,22 @@ SKIM_DEV uint64_t edge_key(const TravArgs &A, const Desc &d, uint32_t idx, uint3
 
 // Live lanes (reverse) or instances (forward) of an edge with other end x
 // and coin-stream state he.
-template <bool FWD>
+template <bool FWD, bool MAT>
 SKIM_DEV uint64_t edge_live_xh(const TravArgs &A, const Desc &d, uint32_t idx, uint32_t x, uint64_t he,
                                const uint64_t *ginst) {
+    if (MAT) return FWD ? (d.mask & he) : d.mask;
     if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A, idx, d.v, x), ginst);
     const uint64_t t1 = edge_tm1_rev(A, idx, x, d.v, d.tm1);
     if (d.single) return fmix(he + d.g1) <= t1 ? d.mask : 0;
     return live_lanes(he, d.mask, t1, A.lane_g + static_cast<size_t>(d.w >> kChunkBits) * 64);
 }
 
-template <bool FWD>
+template <bool FWD, bool MAT>
 SKIM_DEV uint64_t edge_live(const TravArgs &A, const Desc &d, uint32_t idx, uint32_t *tgt, const uint64_t *ginst) {
     const uint32_t x = A.col[idx];
-    const uint64_t he = edge_key<FWD>(A, d, idx, x);
+    const uint64_t he = edge_key<FWD, MAT>(A, d, idx, x);
     *tgt = x;
+    if (MAT) return FWD ? (d.mask & he) : d.mask;
     if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A, idx, d.v, x), ginst);
     const uint64_t t1 = edge_tm1_rev(A, idx, x, d.v, d.tm1);
     if (d.single) return fmix(he + d.g1) <= t1 ? d.mask : 0;
@@ -376,7 +412,7 @@ SKIM_DEV uint64_t prune_full(const TravArgs &A, const Desc &d, uint32_t u, uint6
 }
 
 // Hand the live results of one step to the emitters (warp-collective).
-template <bool FWD>
+template <bool FWD, bool MAT>
 SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, const Desc &d, const uint64_t *lv, const uint32_t *tg) {
 #pragma unroll
     for (int q = 0; q < kUnroll; q++) {
@@ -385,7 +421,7 @@ SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, const Desc &d, const uint64
             emit_fwd(A, acc, live != 0, tg[q], live);
         } else {
             if (live && A.prune) live = prune_full(A, d, tg[q], live);
-            emit_rev(A, acc, live != 0, tg[q], d.w >> kChunkBits, live);
+            emit_rev<MAT>(A, acc, live != 0, tg[q], d.w >> kChunkBits, live);
         }
     }
 }
@@ -393,7 +429,7 @@ SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, const Desc &d, const uint64
 // Expand entries [k0, k0 + kUnroll*stride) of item d, entry k at index
 // begin + k for k < cnt (stride = 32 when the warp shares the item, 1 when
 // the lane owns it).  Warp-collective.
-template <bool FWD>
+template <bool FWD, bool MAT>
 SKIM_DEV void expand_step(const TravArgs &A, Acc &acc, const Desc &d, uint32_t k0, uint32_t stride, bool own,
                           const uint64_t *ginst) {
     uint64_t lv[kUnroll];
@@ -407,26 +443,26 @@ SKIM_DEV void expand_step(const TravArgs &A, Acc &acc, const Desc &d, uint32_t k
             if (FWD && d.erase)
                 atomicSub(&A.size[A.idx_nodes[(d.mask - 1) + d.begin + k]], 1u);
             else
-                lv[q] = edge_live<FWD>(A, d, d.begin + k, &tg[q], ginst);
+                lv[q] = edge_live<FWD, MAT>(A, d, d.begin + k, &tg[q], ginst);
         }
     }
     uint64_t anyl = 0;
 #pragma unroll
     for (int q = 0; q < kUnroll; q++) anyl |= lv[q];
-    if (__any_sync(kFull, anyl != 0)) emit_step<FWD>(A, acc, d, lv, tg);
+    if (__any_sync(kFull, anyl != 0)) emit_step<FWD, MAT>(A, acc, d, lv, tg);
 }
 
 // Expand the items held by the lanes with `have`: an item of 32 or more
 // entries is swept by the whole warp (lane = entry), smaller items by their
 // own lane.
-template <bool FWD>
+template <bool FWD, bool MAT>
 SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &it, const uint64_t *ginst) {
     const int lane = threadIdx.x & 31;
-    Desc d = describe(A, have, it);
+    Desc d = describe<FWD, MAT>(A, have, it);
     if (d.cnt && !d.erase) {
         acc.edges += d.cnt;
-        acc.coins += static_cast<unsigned long long>(d.cnt) * __popcll(d.mask);
-        if (!FWD) {
+        if (!MAT) acc.coins += static_cast<unsigned long long>(d.cnt) * __popcll(d.mask);
+        if (!FWD && !MAT) {
             d.tm1 = A.cm.model == 1 ? A.cm.thr_wc[d.v] : A.cm.tm1_uniform;
             d.single = (d.mask & (d.mask - 1)) == 0;
             if (d.single) d.g1 = A.lane_g[static_cast<size_t>(d.w >> kChunkBits) * 64 + (__ffsll(d.mask) - 1)];
@@ -439,7 +475,7 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
         const Desc b = shfl_desc(d, src);
 #if SKIM_PREFETCH
         if (FWD && b.erase) {  // index-erase items
-            for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD>(A, acc, b, k0 + lane, 32, true, ginst);
+            for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD, MAT>(A, acc, b, k0 + lane, 32, true, ginst);
         } else {
             // one step ahead: the next edge's column and key are in flight
             // while the current coin is computed
@@ -447,7 +483,7 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
             uint64_t h = 0;
             if (lane < b.cnt) {
                 x = A.col[b.begin + lane];
-                h = edge_key<FWD>(A, b, b.begin + lane, x);
+                h = edge_key<FWD, MAT>(A, b, b.begin + lane, x);
             }
             for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32) {
                 const uint32_t k = k0 + lane;
@@ -455,31 +491,31 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
                 uint64_t hn = 0;
                 if (k + 32 < b.cnt) {
                     xn = A.col[b.begin + k + 32];
-                    hn = edge_key<FWD>(A, b, b.begin + k + 32, xn);
+                    hn = edge_key<FWD, MAT>(A, b, b.begin + k + 32, xn);
                 }
                 uint64_t lv[kUnroll] = {0};
                 uint32_t tg[kUnroll] = {0};
                 if (k < b.cnt) {
-                    lv[0] = edge_live_xh<FWD>(A, b, b.begin + k, x, h, ginst);
+                    lv[0] = edge_live_xh<FWD, MAT>(A, b, b.begin + k, x, h, ginst);
                     tg[0] = x;
                 }
-                if (__any_sync(kFull, lv[0] != 0)) emit_step<FWD>(A, acc, b, lv, tg);
+                if (__any_sync(kFull, lv[0] != 0)) emit_step<FWD, MAT>(A, acc, b, lv, tg);
                 x = xn;
                 h = hn;
             }
         }
 #else
-        for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD>(A, acc, b, k0 + lane, 32, true, ginst);
+        for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD, MAT>(A, acc, b, k0 + lane, 32, true, ginst);
 #endif
     }
     const uint32_t mine = d.cnt < 32 ? d.cnt : 0;
     uint32_t steps = (mine + kUnroll - 1) / kUnroll;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) steps = max(steps, __shfl_xor_sync(kFull, steps, o));
-    for (uint32_t st = 0; st < steps; st++) expand_step<FWD>(A, acc, d, st * kUnroll, 1, mine != 0, ginst);
+    for (uint32_t st = 0; st < steps; st++) expand_step<FWD, MAT>(A, acc, d, st * kUnroll, 1, mine != 0, ginst);
 }
 
-template <bool FWD>
+template <bool FWD, bool MAT>
 __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse(TravArgs A) {
     __shared__ uint64_t ginst[64];  // (i + 1) * G for instance i (residual searches)
     if (threadIdx.x < 64) ginst[threadIdx.x] = kGolden * static_cast<uint64_t>(threadIdx.x + 1);
@@ -512,7 +548,7 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
             }
             const unsigned hb = __ballot_sync(kFull, have);
             if (hb) {
-                process_items<FWD>(A, acc, have, it, ginst);
+                process_items<FWD, MAT>(A, acc, have, it, ginst);
                 // slots reserved while processing must be visible before the
                 // items count as done (the drain test reads done, then tail)
                 const bool fence = __any_sync(kFull, acc.pushed);
@@ -580,17 +616,24 @@ int traverse_grid(bool forward) {
     // SM keeps the idle warps (which poll) few.  Reverse searches of a batch
     // fill the machine: as many blocks as fit.
     if (forward) return sms;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_traverse<false>, kTravThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_traverse<false, false>, kTravThreads, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
 
 cudaError_t launch_traverse(const TravArgs &a, bool forward, int grid, cudaStream_t s) {
     note_launch();
-    if (forward)
-        k_traverse<true><<<grid, kTravThreads, 0, s>>>(a);
-    else
-        k_traverse<false><<<grid, kTravThreads, 0, s>>>(a);
+    if (forward) {
+        if (a.mat)
+            k_traverse<true, true><<<grid, kTravThreads, 0, s>>>(a);
+        else
+            k_traverse<true, false><<<grid, kTravThreads, 0, s>>>(a);
+    } else {
+        if (a.mat)
+            k_traverse<false, true><<<grid, kTravThreads, 0, s>>>(a);
+        else
+            k_traverse<false, false><<<grid, kTravThreads, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -622,7 +665,10 @@ __global__ void k_rev_sources(TravArgs A, const uint32_t *lane_pair, uint32_t B,
                 atomicOr(reinterpret_cast<unsigned long long *>(&alive[w >> 1]), bits);
             }
         }
-        emit_rev(A, acc, act, u, j >> 6, 1ull << (j & 63));
+        if (A.mat)
+            emit_rev<true>(A, acc, act, u, j >> 6, 1ull << (j & 63));
+        else
+            emit_rev<false>(A, acc, act, u, j >> 6, 1ull << (j & 63));
     }
     flush_acc(A, acc, false);
 }
@@ -640,7 +686,10 @@ __global__ void k_respill_rev(TravArgs A, uint64_t R) {
             p = atomicExch(reinterpret_cast<unsigned long long *>(&A.pend[slot]), 0ull);
         }
         Acc acc;
-        push_rev(A, acc, static_cast<uint32_t>(key >> A.tbits), static_cast<uint32_t>(key & tmask), p, slot);
+        if (A.mat)
+            push_rev<true>(A, acc, static_cast<uint32_t>(key >> A.tbits), static_cast<uint32_t>(key & tmask), p, slot);
+        else
+            push_rev<false>(A, acc, static_cast<uint32_t>(key >> A.tbits), static_cast<uint32_t>(key & tmask), p, slot);
     }
 }
 

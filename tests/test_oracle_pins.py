@@ -344,3 +344,26 @@ def test_estimator_unbiased_and_cv_bound():
     if exact_u * l > k:
         cv = np.std(eu) / exact_u
         assert cv <= 1.25 / math.sqrt(k - 2)
+
+
+@pytest.mark.parametrize("name,mk", TINY[:6])
+def test_work_counters_without_pruning_match_brute_force(name, mk):
+    # With k > n*l no local sketch fills, so the reverse search of every pair
+    # (u,i) expands each v that reaches u in instance i: expansions =
+    # sum over (v,i) of |R(G_i, v)|, live reverse edges = the same weighted by
+    # v's live in-degree in instance i.
+    g = mk()
+    l = 3
+    pb = _problem(g, l, g.n * l + 1, 0, 0.4)
+    inst = _inst(pb)
+    indeg_live = [[0] * g.n for _ in range(l)]
+    for i in range(l):
+        for u in range(g.n):
+            for v in inst.out[i][u]:
+                indeg_live[i][v] += 1
+    reach = [[len(inst.reach(v, i)) for i in range(l)] for v in range(g.n)]
+    _, _, cnt = oracle.build_sketches(pb)
+    assert cnt["rev_expansions"] == sum(reach[v][i] for v in range(g.n) for i in range(l))
+    assert cnt["rev_live_edges"] == sum(reach[v][i] * indeg_live[i][v] for v in range(g.n) for i in range(l))
+    indeg = np.bincount(g.dst, minlength=g.n) if g.m else np.zeros(g.n, int)
+    assert cnt["rev_edge_scans"] == sum(reach[v][i] * int(indeg[v]) for v in range(g.n) for i in range(l))
