@@ -64,7 +64,7 @@ __global__ void k_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint6
         const uint64_t tmask = (1ull << tbits) - 1;
         for (uint64_t rr = r; rr < R && (rec_key[rr] >> tbits) == v; rr++) {
             const uint64_t t = rec_key[rr] & tmask;
-            uint64_t m = hvals[rec_val[rr]];
+            uint64_t m = hvals[2ull * rec_val[rr]];
             while (m) {
                 int j = __ffsll(m) - 1;
                 m &= m - 1;
@@ -89,8 +89,8 @@ __global__ void k_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hke
     for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
          r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         uint32_t s = rec_val[r];
-        hkeys[s] = kEmptyKey;
-        hvals[s] = 0;
+        hkeys[2ull * s] = kEmptyKey;  // key and bits of a slot share 16 bytes
+        hvals[2ull * s] = 0;
     }
 }
 
@@ -116,7 +116,7 @@ __global__ void k_candidates(const uint64_t *rec_key, const uint32_t *rec_val, u
         uint32_t cum = 0;
         for (uint64_t rr = r; rr < R && (rec_key[rr] >> tbits) == v; rr++) {
             const uint64_t t = rec_key[rr] & tmask;
-            uint64_t m = hvals[rec_val[rr]] & alive[t] & range_mask(t, lo, 0xffffffffu);
+            uint64_t m = hvals[2ull * rec_val[rr]] & alive[t] & range_mask(t, lo, 0xffffffffu);
             uint32_t c = __popcll(m);
             if (cum + c >= need) {
                 uint64_t p = t * 64 + nth_set_bit(m, static_cast<int>(need - cum - 1));
@@ -140,7 +140,7 @@ __global__ void k_commit_count(const uint64_t *rec_key, const uint32_t *rec_val,
         uint32_t add = 0;
         for (uint64_t rr = r; rr < R && (rec_key[rr] >> tbits) == v; rr++) {
             const uint64_t t = rec_key[rr] & tmask;
-            uint64_t m = hvals[rec_val[rr]] & alive[t] & range_mask(t, lo, hi);
+            uint64_t m = hvals[2ull * rec_val[rr]] & alive[t] & range_mask(t, lo, hi);
             add += __popcll(m);
             while (m) {
                 int j = __ffsll(m) - 1;
@@ -163,7 +163,7 @@ __global__ void k_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_va
          r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         const uint64_t v = rec_key[r] >> tbits;
         const uint64_t t = rec_key[r] & tmask;
-        uint64_t m = hvals[rec_val[r]] & alive[t] & range_mask(t, lo, hi);
+        uint64_t m = hvals[2ull * rec_val[r]] & alive[t] & range_mask(t, lo, hi);
         while (m) {
             int j = __ffsll(m) - 1;
             m &= m - 1;

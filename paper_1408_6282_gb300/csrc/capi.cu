@@ -234,6 +234,13 @@ int reset_ctl(skim_ctx *c) {
     return SKIM_OK;
 }
 
+// every visited-table slot empty: keys all ones, lane bits zero
+cudaError_t clear_table(skim_ctx *c) {
+    cudaError_t e = cudaMemset2DAsync(c->hkeys, 16, 0xff, 8, c->hcap, c->st);
+    if (e == cudaSuccess) e = cudaMemset2DAsync(c->hvals, 16, 0, 8, c->hcap, c->st);
+    return e;
+}
+
 // empty the work queue (cursors and slots) before another traversal round
 int reset_queue(skim_ctx *c, uint64_t used) {
     uint64_t u = std::min(used, c->qcap);
@@ -304,8 +311,11 @@ int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out) {
 
 // Reverse search of the batch of ranks [p0, p0+B).  mode_build: Algorithm 2
 // (pruned by local counts); otherwise SKIM (covered sources skipped).
+// est_per_lane: expected visit records per lane (0 = unknown).  The visited
+// table used is a power of two of about 8 slots per expected record (all of
+// it when unknown), so that a batch's table stays small enough for L2.
 // Returns SKIM_OK with *retry set if the batch overflowed its tables.
-int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry) {
+int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry, double est_per_lane) {
     *retry = false;
     const uint32_t T = (B + 63) / 64;
     const uint32_t tbits = bitlen(T - 1);
@@ -315,6 +325,11 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     if (!mode_build) CK(c, cudaMemsetAsync(c->alive, 0, T * sizeof(uint64_t), c->st));
     TravArgs a = base_args(c, false);
     a.tbits = tbits;
+    if (est_per_lane > 0) {
+        const uint64_t want = pow2_at_least(std::max<uint64_t>(
+            1ull << 16, static_cast<uint64_t>(8.0 * est_per_lane * static_cast<double>(B))));
+        a.hmask = std::min(want, c->hcap) - 1;
+    }
     // IC-model searches are never pruned: every lane is its own instance
     a.prune = mode_build && c->rank_mode != SKIM_RANKS_IC_MODEL ? 1 : 0;
     CK(c, launch_rev_sources(a, c->spair + p0, B, c->l, mode_build ? nullptr : c->covered,
@@ -325,8 +340,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     if (h.err & kErrRetryable) {
         *retry = true;
         RC(reset_queue(c, h.q_tail.v));
-        CK(c, cudaMemsetAsync(c->hkeys, 0xff, c->hcap * sizeof(uint64_t), c->st));
-        CK(c, cudaMemsetAsync(c->hvals, 0, c->hcap * sizeof(uint64_t), c->st));
+        CK(c, clear_table(c));
         CK(c, cudaMemsetAsync(c->pend, 0, c->hcap * sizeof(uint64_t), c->st));
         c->hstats[SKIM_STAT_RETRIES]++;
         return SKIM_OK;
@@ -513,9 +527,10 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
             want = std::min<uint64_t>(want, default_lanes(c));
             uint32_t B = static_cast<uint32_t>(std::min<uint64_t>(want, c->nl - c->cursor));
             bool retry = false;
-            RC(rev_batch(c, c->cursor, B, false, &retry));
+            RC(rev_batch(c, c->cursor, B, false, &retry, c->vpl_est));
             if (retry) {
                 c->skim_B = std::max<uint32_t>(64, B / 2);
+                c->vpl_est *= 4;  // more records than expected: a larger table too
                 continue;
             }
             c->skim_B = 0;
@@ -674,7 +689,8 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->rbase); dfree(c->rtm1); dfree(c->ftm1);
     dfree(c->ctl); dfree(c->dflag);
     if (c->hctl) cudaFreeHost(c->hctl);
-    dfree(c->q); dfree(c->hkeys); dfree(c->hvals); dfree(c->pend);
+    dfree(c->q); dfree(c->hkeys); dfree(c->pend);
+    c->hvals = nullptr;
     dfree(c->rkey); dfree(c->rkey2); dfree(c->rval); dfree(c->rval2);
     if (c->ws) cudaFree(c->ws);
     dfree(c->lane_inst); dfree(c->lane_g); dfree(c->alive); dfree(c->lane_cnt); dfree(c->lane_off); dfree(c->lane_fill);
@@ -861,11 +877,11 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         c->qcap = std::max<uint64_t>(rcap, 1u << 22);
         TRY(dalloc(c, &c->q, c->qcap));
         TRYC(cudaMemsetAsync(c->q, 0, c->qcap * sizeof(Item), c->st));
-        TRY(dalloc(c, &c->hkeys, c->hcap));
-        TRY(dalloc(c, &c->hvals, c->hcap));
+        // one array of 16-byte slots: key at [2h], lane bits at [2h + 1]
+        TRY(dalloc(c, &c->hkeys, 2 * c->hcap));
+        c->hvals = c->hkeys + 1;
         TRY(dalloc(c, &c->pend, c->hcap));
-        TRYC(cudaMemsetAsync(c->hkeys, 0xff, c->hcap * sizeof(uint64_t), c->st));
-        TRYC(cudaMemsetAsync(c->hvals, 0, c->hcap * sizeof(uint64_t), c->st));
+        TRYC(clear_table(c));
         TRYC(cudaMemsetAsync(c->pend, 0, c->hcap * sizeof(uint64_t), c->st));
         TRY(dalloc(c, &c->rkey, c->rcap));
         TRY(dalloc(c, &c->rkey2, c->rcap));
@@ -1066,12 +1082,14 @@ int skim_build_sketches(skim_ctx *c) {
     const uint32_t Bmax = default_lanes(c);
     uint32_t B = std::min<uint32_t>(Bmax, 1u << 12);
     uint64_t p0 = 0;
+    double rpl = 0;  // records per lane of the last batch (0: unknown)
     while (p0 < c->nbuild) {
         uint32_t b = static_cast<uint32_t>(std::min<uint64_t>(B, c->nbuild - p0));
         bool retry = false;
-        RC(rev_batch(c, p0, b, true, &retry));
+        RC(rev_batch(c, p0, b, true, &retry, rpl));
         if (retry) {
             B = std::max<uint32_t>(64, b / 4);
+            rpl = 0;  // the whole table for the re-run
             continue;
         }
         {
@@ -1086,6 +1104,7 @@ int skim_build_sketches(skim_ctx *c) {
         // next batch: double, but keep the visit records near a quarter of
         // the table (dense instances can give thousands of records per lane)
         const double per_lane = static_cast<double>(recs ? recs : 1) / b;
+        rpl = per_lane;
         const uint64_t fit = static_cast<uint64_t>(static_cast<double>(c->rcap) / 4.0 / per_lane);
         B = static_cast<uint32_t>(std::max<uint64_t>(64, std::min<uint64_t>({Bmax, 2ull * B, fit})));
     }

@@ -47,20 +47,21 @@ SKIM_DEV uint64_t edge_tm1_fwd(const TravArgs &A, uint32_t idx, uint32_t u, uint
 
 // Insert-or-merge of (key, bits) into the visited table.  Returns false if the
 // probe limit is hit.  *old = bits present before, *slot = table slot,
-// *first = this call created the entry.
+// *first = this call created the entry.  Slot h keeps its key at hkeys[2h] and
+// its bits at hvals[2h] (hvals = hkeys + 1): both in one 16-byte sector.
 SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t key, uint64_t bits, uint64_t *old,
                       uint64_t *slot, bool *first) {
     uint64_t h = fmix(key) & hmask;
     for (int p = 0; p < kMaxProbe; p++) {
-        uint64_t k = *reinterpret_cast<volatile uint64_t *>(&hkeys[h]);
+        uint64_t k = *reinterpret_cast<volatile uint64_t *>(&hkeys[2 * h]);
         if (k == kEmptyKey) {
-            unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long *>(&hkeys[h]),
+            unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long *>(&hkeys[2 * h]),
                                                 static_cast<unsigned long long>(kEmptyKey),
                                                 static_cast<unsigned long long>(key));
             if (prev == kEmptyKey) {
                 *first = true;
                 *slot = h;
-                *old = atomicOr(reinterpret_cast<unsigned long long *>(&hvals[h]), bits);
+                *old = atomicOr(reinterpret_cast<unsigned long long *>(&hvals[2 * h]), bits);
                 return true;
             }
             k = prev;
@@ -68,7 +69,7 @@ SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t
         if (k == key) {
             *first = false;
             *slot = h;
-            *old = atomicOr(reinterpret_cast<unsigned long long *>(&hvals[h]), bits);
+            *old = atomicOr(reinterpret_cast<unsigned long long *>(&hvals[2 * h]), bits);
             return true;
         }
         h = (h + 1) & hmask;
@@ -147,6 +148,15 @@ SKIM_DEV uint32_t live_row_len(const TravArgs &A, uint32_t u, uint32_t t, int j)
     return static_cast<uint32_t>(A.loff[r + 1] - A.loff[r]);
 }
 
+// A materialised reverse item names its row directly: v = first entry of the
+// chunk, w = (word << 6 | lane bit), mask = entries in the chunk (1..kChunk),
+// so that the consumer needs no lookup before it reads the row.
+SKIM_DEV void write_row_items(const TravArgs &A, unsigned long long s, uint64_t b0, uint64_t b1, uint32_t t, int j) {
+    for (uint64_t e = b0, q = 0; e < b1; e += kChunk, q++)
+        write_item(A, s + q, static_cast<uint32_t>(e), (t << 6) | static_cast<uint32_t>(j),
+                   b1 - e < kChunk ? b1 - e : static_cast<uint64_t>(kChunk));
+}
+
 // Warp-collective: queue the expansion of lane bits `nb` of entry (u, t)
 // (table slot `slot`).  With materialised instances each lane gets items of
 // its own (its row of live in-neighbours; none if the row is empty).
@@ -168,8 +178,10 @@ SKIM_DEV void push_rev(const TravArgs &A, Acc &acc, uint32_t u, uint32_t t, uint
         uint32_t c = 0;
         for (uint64_t m = nb; m; m &= m - 1) {
             const int j = __ffsll(m) - 1;
-            const uint32_t nc = n_chunks(live_row_len(A, u, t, j));
-            for (uint32_t q = 0; q < nc; q++, c++) write_item(A, s + c, u, (t << kChunkBits) | q, 1ull << j);
+            const uint64_t r = static_cast<uint64_t>(u) * A.l + A.lane_inst[static_cast<size_t>(t) * 64 + j];
+            const uint64_t b0 = A.loff[r], b1 = A.loff[r + 1];
+            write_row_items(A, s + c, b0, b1, t, j);
+            c += n_chunks(static_cast<uint32_t>(b1 - b0));
         }
     } else {
         for (uint32_t c = 0; c < ni; c++) write_item(A, s + c, u, (t << kChunkBits) | c, nb);
@@ -212,6 +224,57 @@ SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32
     }
     acc.visits += __popcll(nb);
     push_rev<MAT>(A, acc, u, t, nb, slot);
+}
+
+// Warp-collective, materialised reverse searches: lanes with `act` reach node
+// u for lane j of word t (instance inst).  The row bounds of (u, inst) and the
+// pruning word are loaded together, before the visited-table update.
+SKIM_DEV void emit_rev_mat(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32_t t, int j, uint32_t inst) {
+    if (!__any_sync(kFull, act)) return;
+    uint64_t b0 = 0, b1 = 0;
+    if (act) {
+        const uint64_t r = static_cast<uint64_t>(u) * A.l + inst;
+        b0 = A.loff[r];
+        b1 = A.loff[r + 1];
+        if (A.prune && ((A.full[u] >> inst) & 1ull)) act = false;  // Algorithm 2: local sketch full
+    }
+    const uint64_t bit = 1ull << j;
+    bool fresh = false, first = false;
+    uint64_t slot = 0;
+    if (act) {
+        uint64_t old;
+        const uint64_t key = (static_cast<uint64_t>(u) << A.tbits) | t;
+        if (hash_or(A.hkeys, A.hvals, A.hmask, key, bit, &old, &slot, &first))
+            fresh = !(old & bit);
+        else
+            atomicOr(&A.ctl->err, kErrHash);
+    }
+    {
+        unsigned ball = __ballot_sync(kFull, first);
+        if (ball) {
+            unsigned long long base = 0;
+            if ((threadIdx.x & 31) == 0) base = atomicAdd(&A.ctl->rec_count.v, static_cast<unsigned long long>(__popc(ball)));
+            base = __shfl_sync(kFull, base, 0);
+            if (first) {
+                unsigned long long r = base + __popc(ball & lanemask_lt());
+                if (r < A.rcap) {
+                    A.rec_key[r] = (static_cast<uint64_t>(u) << A.tbits) | t;
+                    A.rec_val[r] = static_cast<uint32_t>(slot);
+                } else {
+                    atomicOr(&A.ctl->err, kErrRecords);
+                }
+            }
+        }
+    }
+    acc.visits += fresh ? 1 : 0;
+    const uint32_t ni = fresh ? n_chunks(static_cast<uint32_t>(b1 - b0)) : 0;
+    if (!__any_sync(kFull, ni != 0)) return;
+    unsigned long long s = reserve_slots(A, acc, ni);
+    if (ni && spill_if_full(A, s, ni)) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&A.pend[slot]), bit);
+        return;
+    }
+    if (ni) write_row_items(A, s, b0, b1, t, j);
 }
 
 // Warp-collective: queue the expansion of node w in instances `trav` and the
@@ -300,6 +363,7 @@ struct Desc {
     uint32_t v, w, begin, cnt;
     uint64_t mask, tm1, g1;  // g1: stream offset when the item has a single lane
     bool erase, single;
+    uint32_t inst;           // materialised reverse items: the lane's instance
 };
 
 template <bool FWD, bool MAT>
@@ -316,12 +380,13 @@ SKIM_DEV Desc describe(const TravArgs &A, bool have, const Item &it) {
         return d;
     }
     const uint32_t chunk = it.w & ((1u << kChunkBits) - 1);
-    if (MAT && !FWD) {  // one lane: its row of live in-neighbours
-        const uint32_t t = it.w >> kChunkBits;
-        const uint64_t r = static_cast<uint64_t>(it.v) * A.l + A.lane_inst[static_cast<size_t>(t) * 64 + (__ffsll(it.mask) - 1)];
-        const uint32_t e0 = static_cast<uint32_t>(A.loff[r]), e1 = static_cast<uint32_t>(A.loff[r + 1]);
-        d.begin = e0 + chunk * kChunk;
-        d.cnt = min(kChunk, e1 - d.begin);
+    if (MAT && !FWD) {  // one lane and a chunk of its row (write_row_items)
+        const uint32_t t = it.w >> 6, j = it.w & 63u;
+        d.begin = it.v;
+        d.cnt = static_cast<uint32_t>(it.mask);
+        d.mask = 1ull << j;
+        d.w = t << kChunkBits;
+        d.inst = A.lane_inst[static_cast<size_t>(t) * 64 + j];
         return d;
     }
     const uint32_t e0 = A.ptr[it.v], e1 = A.ptr[it.v + 1];
@@ -342,6 +407,7 @@ SKIM_DEV Desc shfl_desc(const Desc &d, int src) {
     o.g1 = __shfl_sync(kFull, d.g1, src);
     o.erase = __shfl_sync(kFull, d.erase, src);
     o.single = __shfl_sync(kFull, d.single, src);
+    o.inst = __shfl_sync(kFull, d.inst, src);
     return o;
 }
 
@@ -419,6 +485,8 @@ SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, const Desc &d, const uint64
         uint64_t live = lv[q];
         if (FWD) {
             emit_fwd(A, acc, live != 0, tg[q], live);
+        } else if (MAT) {
+            emit_rev_mat(A, acc, live != 0, tg[q], d.w >> kChunkBits, __ffsll(d.mask) - 1, d.inst);
         } else {
             if (live && A.prune) live = prune_full(A, d, tg[q], live);
             emit_rev<MAT>(A, acc, live != 0, tg[q], d.w >> kChunkBits, live);
@@ -549,14 +617,15 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
             const unsigned hb = __ballot_sync(kFull, have);
             if (hb) {
                 process_items<FWD, MAT>(A, acc, have, it, ginst);
-                // slots reserved while processing must be visible before the
-                // items count as done (the drain test reads done, then tail)
-                const bool fence = __any_sync(kFull, acc.pushed);
+                // The drain test reads done, then tail, so the slots reserved
+                // while processing must be counted in tail before these items
+                // count as done.  No fence is needed: lane 0 made every
+                // reservation of this warp with an atomic whose result it has
+                // already used, so that atomic has been performed at the point
+                // of coherence before this one is issued.  (Items themselves are
+                // found by their non-zero fields, not by ordering.)
                 acc.pushed = false;
-                if (lane == 0) {
-                    if (fence) __threadfence();
-                    atomicAdd(&C->q_done.v, static_cast<unsigned long long>(__popc(hb)));
-                }
+                if (lane == 0) atomicAdd(&C->q_done.v, static_cast<unsigned long long>(__popc(hb)));
                 t_progress = globaltimer();
                 backoff = 32;
                 polls = 0;
@@ -666,7 +735,7 @@ __global__ void k_rev_sources(TravArgs A, const uint32_t *lane_pair, uint32_t B,
             }
         }
         if (A.mat)
-            emit_rev<true>(A, acc, act, u, j >> 6, 1ull << (j & 63));
+            emit_rev_mat(A, acc, act, u, j >> 6, static_cast<int>(j & 63), i);
         else
             emit_rev<false>(A, acc, act, u, j >> 6, 1ull << (j & 63));
     }

@@ -268,3 +268,20 @@ def test_error_codes(pkg):
     with pytest.raises(pkg.SkimError) as e:
         pkg.Skim(3, np.array([1], np.uint32), np.array([1], np.uint32), 4, 4)  # self-loop
     assert e.value.code == -6
+
+
+def test_long_path_graph(pkg):
+    """A 200000-node path, every edge live: reverse searches are long chains
+    of single successors (the local-continuation limit and the progress
+    watchdog must both hold)."""
+    g = synth.chain(200000)
+    pb, sk = _both(pkg, g, 4, 4, 0, 1.0, 5)
+    with sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        ox, oln, _ = oracle.build_sketches(pb)
+        assert np.array_equal(ln, oln) and np.array_equal(x, ox)
+        seeds, cov, tau, kp = sk.greedy_stops(5)
+        os_, oc, otau, okp, _ = oracle.skim_stops(pb, 5)
+        assert np.array_equal(seeds, os_) and np.array_equal(cov, oc)
+        assert np.array_equal(tau, otau) and np.array_equal(kp, okp)
