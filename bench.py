@@ -135,9 +135,9 @@ def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms):
     rev_search  (memory): 16 B per reverse expansion (the two row bounds of
                 (v, i)) + 20 B per live in-edge (4 B neighbour id, 8 B read and
                 8 B write of its visited word).
-    fwd_search  (memory): 8 B per forward expansion (row bounds) + 12 B per
-                out-edge scanned (4 B id + 8 B live mask) + 16 B per live
-                out-edge (covered word read and write).
+    fwd_search  (memory): 16 B per forward expansion (the two row bounds of
+                (v, i)) + 20 B per live out-edge (4 B neighbour id, covered word
+                read and write) + 8 B per index entry erased (node id, size).
     instances   (integer ALU): 2 m l coins (both CSR orders) x 27 int32 ops.
     """
     ms, launches = kt[kname]
@@ -159,9 +159,9 @@ def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms):
         units = f"{E} reverse expansions x 16 B + {L} live in-edges x 20 B per step"
         key = "k_traverse_rev"
     else:
-        E, S, L = sm["fwd_expansions"], sm["fwd_edge_scans"], sm.get("fwd_live_edges", 0)
-        byts = 8 * E + 12 * S + 16 * L
-        units = f"{E} forward expansions x 8 B + {S} out-edges x 12 B + {L} live out-edges x 16 B per step"
+        E, L, X = sm["fwd_expansions"], sm.get("fwd_live_edges", 0), sm["index_erased"]
+        byts = 16 * E + 20 * L + 8 * X
+        units = f"{E} forward expansions x 16 B + {L} live out-edges x 20 B + {X} index entries x 8 B per step"
         key = "k_traverse_fwd"
     achieved = byts / sec / 1e9
     trb = traffic_record(key)

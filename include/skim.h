@@ -254,10 +254,10 @@ int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
 /* Kernel timing with CUDA events on the context's stream (off by default).
  * When on, the device time of each launch group below is accumulated until
  * the next call with reset != 0.  Kinds (index into ms_out / launches_out):
- *   SKIM_K_REV   reverse searches (Algorithms 1 and 2, the batched BFS)
+ *   SKIM_K_REV   reverse searches (Algorithms 1 and 2, the batched BFS, sources included)
  *   SKIM_K_FWD   residual forward searches (Algorithm 1)
  *   SKIM_K_ACCEPT Algorithm 2 acceptance into the sketches
- *   SKIM_K_SORT  grouping of visit records by node (radix sort)
+ *   SKIM_K_SORT  grouping of visit records by node (radix sort), emptying their table slots
  *   SKIM_K_STEP  SKIM per-node steps (first-to-k candidates, commits)
  *   SKIM_K_RANKS rank order of the n*l pairs
  *   SKIM_K_QUERY union-estimator queries

@@ -85,6 +85,13 @@ __global__ void k_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint6
     warp_add(&ctl->stats[kStInsert], ins);
 }
 
+// every slot of the visited table empty (16-byte slots: key all ones, bits 0)
+__global__ void k_table_init(uint64_t *table, uint64_t slots) {
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < slots;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        reinterpret_cast<ulonglong2 *>(table)[i] = make_ulonglong2(kEmptyKey, 0ull);
+}
+
 __global__ void k_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hkeys, uint64_t *hvals) {
     for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
          r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
@@ -255,6 +262,11 @@ cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint
     note_launch();
     k_accept<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, lane_inst, lane_rank, l, k, lcnt,
                                               full, X, xlen, ctl);
+    return cudaGetLastError();
+}
+cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s) {
+    note_launch();
+    k_table_init<<<grid_for(slots, 256), 256, 0, s>>>(table, slots);
     return cudaGetLastError();
 }
 cudaError_t launch_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hkeys, uint64_t *hvals, cudaStream_t s) {

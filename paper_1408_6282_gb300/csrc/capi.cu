@@ -41,8 +41,8 @@ struct skim_ctx {
     // materialised instances (Section 2): per-edge live masks in both CSR
     // orders and the node-major live in-neighbour rows of every (v, i)
     bool mat = false;
-    uint64_t *rmask = nullptr, *fmask = nullptr, *loff = nullptr;
-    uint32_t *rlive = nullptr;
+    uint64_t *rmask = nullptr, *fmask = nullptr, *loff = nullptr, *foff = nullptr;
+    uint32_t *rlive = nullptr, *flive = nullptr;  // live in- and out-neighbour rows
     uint32_t *rrow = nullptr, *rev2fwd = nullptr;  // per reverse CSR edge: head, forward position
     uint64_t rlive_cap = 0, live_total = 0;
     uint64_t rank_key = 0;
@@ -235,11 +235,7 @@ int reset_ctl(skim_ctx *c) {
 }
 
 // every visited-table slot empty: keys all ones, lane bits zero
-cudaError_t clear_table(skim_ctx *c) {
-    cudaError_t e = cudaMemset2DAsync(c->hkeys, 16, 0xff, 8, c->hcap, c->st);
-    if (e == cudaSuccess) e = cudaMemset2DAsync(c->hvals, 16, 0, 8, c->hcap, c->st);
-    return e;
-}
+cudaError_t clear_table(skim_ctx *c) { return launch_table_init(c->hkeys, c->hcap, c->st); }
 
 // empty the work queue (cursors and slots) before another traversal round
 int reset_queue(skim_ctx *c, uint64_t used) {
@@ -253,9 +249,9 @@ int reset_queue(skim_ctx *c, uint64_t used) {
 TravArgs base_args(skim_ctx *c, bool forward) {
     TravArgs a{};
     a.ptr = forward ? c->fptr : c->rptr;
-    a.col = forward ? c->fcol : (c->mat ? c->rlive : c->rcol);
+    a.col = c->mat ? (forward ? c->flive : c->rlive) : (forward ? c->fcol : c->rcol);
     a.mat = c->mat ? 1 : 0;
-    a.loff = c->loff;
+    a.loff = forward ? c->foff : c->loff;
     a.lmask = forward ? c->fmask : nullptr;
     a.cm = c->cm;
     a.q = c->q;
@@ -302,6 +298,7 @@ int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out) {
         if (h.err & kErrRetryable) return SKIM_OK;  // caller re-runs the batch
         if (!h.spill) return SKIM_OK;
         RC(reset_queue(c, h.q_tail.v));
+        KTimer kt(c, forward ? SKIM_K_FWD : SKIM_K_REV);
         if (forward)
             CK(c, launch_respill_fwd(a, c->n, c->st));
         else
@@ -332,8 +329,11 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     }
     // IC-model searches are never pruned: every lane is its own instance
     a.prune = mode_build && c->rank_mode != SKIM_RANKS_IC_MODEL ? 1 : 0;
-    CK(c, launch_rev_sources(a, c->spair + p0, B, c->l, mode_build ? nullptr : c->covered,
-                             mode_build ? nullptr : c->alive, c->st));
+    {
+        KTimer kt(c, SKIM_K_REV);  // the sources are the searches' first level
+        CK(c, launch_rev_sources(a, c->spair + p0, B, c->l, mode_build ? nullptr : c->covered,
+                                 mode_build ? nullptr : c->alive, c->st));
+    }
     uint64_t R = 0;
     RC(run_traversal(c, a, false, &R));
     const DevCtl &h = *c->hctl;
@@ -358,6 +358,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
 }
 
 int clear_batch(skim_ctx *c) {
+    KTimer kt(c, SKIM_K_SORT);  // visit-record bookkeeping: empty the batch's table slots
     CK(c, launch_clear_slots(c->rval, c->bR, c->hkeys, c->hvals, c->st));
     c->bR = 0;
     return SKIM_OK;
@@ -580,6 +581,7 @@ int make_instances(skim_ctx *c) {
         RC(dalloc(c, &c->rmask, std::max<uint64_t>(c->m, 1)));
         RC(dalloc(c, &c->fmask, std::max<uint64_t>(c->m, 1)));
         RC(dalloc(c, &c->loff, c->nl + 1));
+        RC(dalloc(c, &c->foff, c->nl + 1));
     }
     CK(c, launch_live_masks(c->rrow, c->rcol, c->rhe, c->rtm1, c->rev2fwd, c->cm, c->m, c->l, c->rmask, c->fmask,
                             c->st));
@@ -591,11 +593,18 @@ int make_instances(skim_ctx *c) {
     if (c->live_total >= (1ull << 32)) return SKIM_OK;
     if (c->live_total > c->rlive_cap) {
         dfree(c->rlive);
+        dfree(c->flive);
         c->rlive_cap = 0;
         RC(dalloc(c, &c->rlive, c->live_total));
+        RC(dalloc(c, &c->flive, c->live_total));
         c->rlive_cap = c->live_total;
     }
-    CK(c, launch_live_fill(c->rptr, c->rcol, c->rmask, c->n, c->l, c->loff, c->rlive ? c->rlive : nullptr, c->st));
+    CK(c, launch_live_fill(c->rptr, c->rcol, c->rmask, c->n, c->l, c->loff, c->rlive, c->st));
+    // the same live pairs by tail: rows of live out-neighbours for the residual
+    CK(c, launch_live_count(c->fptr, c->fmask, c->n, c->l, c->foff, c->st));
+    CK(c, cudaMemsetAsync(c->foff + c->nl, 0, sizeof(uint64_t), c->st));
+    CK(c, exclusive_scan_u64(c->foff, c->foff, c->nl + 1, nullptr, c->ws, c->st));
+    CK(c, launch_live_fill(c->fptr, c->fcol, c->fmask, c->n, c->l, c->foff, c->flive, c->st));
     c->mat = true;
     return SKIM_OK;
 }
@@ -699,6 +708,7 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->size); dfree(c->seg_len); dfree(c->idx); dfree(c->chosen);
     dfree(c->rec_tau); dfree(c->rec_kp);
     dfree(c->rmask); dfree(c->fmask); dfree(c->loff); dfree(c->rlive); dfree(c->rrow); dfree(c->rev2fwd);
+    dfree(c->foff); dfree(c->flive);
     dfree(c->qk); dfree(c->qv); dfree(c->qseeds); dfree(c->qoff); dfree(c->qout);
     dfree(c->qtop); dfree(c->qtopu);
     if (c->qpart) cudaFree(c->qpart);

@@ -278,10 +278,20 @@ SKIM_DEV void emit_rev_mat(const TravArgs &A, Acc &acc, bool act, uint32_t u, ui
 }
 
 // Warp-collective: queue the expansion of node w in instances `trav` and the
-// erasure of the index entries of pairs (w, i), i in `erase`.
+// erasure of the index entries of pairs (w, i), i in `erase`.  With
+// materialised instances each instance gets row items of its own list of live
+// out-neighbours (none if it is empty).
+template <bool MAT>
 SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, uint64_t erase) {
     uint32_t ni = 0;
-    if (trav) ni = n_chunks(A.ptr[w + 1] - A.ptr[w], trav);
+    if (MAT) {
+        for (uint64_t m = trav; m; m &= m - 1) {
+            const uint64_t r = static_cast<uint64_t>(w) * A.l + (__ffsll(m) - 1);
+            ni += n_chunks(static_cast<uint32_t>(A.loff[r + 1] - A.loff[r]));
+        }
+    } else if (trav) {
+        ni = n_chunks(A.ptr[w + 1] - A.ptr[w], trav);
+    }
     for (uint64_t m = erase; m; m &= m - 1) {
         int i = __ffsll(m) - 1;
         ni += n_chunks(A.seg_len[static_cast<uint64_t>(w) * A.l + i]);
@@ -294,7 +304,15 @@ SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, u
         return;
     }
     uint32_t c = 0;
-    if (trav) {
+    if (MAT) {
+        for (uint64_t m = trav; m; m &= m - 1) {
+            const int i = __ffsll(m) - 1;
+            const uint64_t r = static_cast<uint64_t>(w) * A.l + i;
+            const uint64_t b0 = A.loff[r], b1 = A.loff[r + 1];
+            write_row_items(A, s + c, b0, b1, 0, i);
+            c += n_chunks(static_cast<uint32_t>(b1 - b0));
+        }
+    } else if (trav) {
         uint32_t nc = n_chunks(A.ptr[w + 1] - A.ptr[w], trav);
         for (; c < nc; c++) write_item(A, s + c, w, c, trav);
     }
@@ -312,6 +330,7 @@ SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, u
 
 // Warp-collective: lanes with `act` reach node w in the instances of `live`
 // during a residual search.
+template <bool MAT>
 SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64_t live) {
     if (!__any_sync(kFull, act && live)) return;
     uint64_t nb = 0;
@@ -330,7 +349,7 @@ SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64
         int i = __ffsll(m) - 1;
         if (A.seg_len[static_cast<uint64_t>(w) * A.l + i]) erase |= 1ull << i;
     }
-    push_fwd(A, acc, w, nb, erase);
+    push_fwd<MAT>(A, acc, w, nb, erase);
 }
 
 // Process the items held by the lanes with `have`, edges (or index entries)
@@ -380,13 +399,13 @@ SKIM_DEV Desc describe(const TravArgs &A, bool have, const Item &it) {
         return d;
     }
     const uint32_t chunk = it.w & ((1u << kChunkBits) - 1);
-    if (MAT && !FWD) {  // one lane and a chunk of its row (write_row_items)
+    if (MAT) {  // one lane (instance) and a chunk of its row (write_row_items)
         const uint32_t t = it.w >> 6, j = it.w & 63u;
         d.begin = it.v;
         d.cnt = static_cast<uint32_t>(it.mask);
         d.mask = 1ull << j;
         d.w = t << kChunkBits;
-        d.inst = A.lane_inst[static_cast<size_t>(t) * 64 + j];
+        d.inst = FWD ? j : A.lane_inst[static_cast<size_t>(t) * 64 + j];
         return d;
     }
     const uint32_t e0 = A.ptr[it.v], e1 = A.ptr[it.v + 1];
@@ -433,7 +452,7 @@ constexpr int kUnroll = SKIM_UNROLL;  // edges per lane per step: independent ha
 // reverse live rows need nothing).
 template <bool FWD, bool MAT>
 SKIM_DEV uint64_t edge_key(const TravArgs &A, const Desc &d, uint32_t idx, uint32_t x) {
-    if (MAT) return FWD ? A.lmask[idx] : 0;
+    if (MAT) return 0;  // materialised rows hold live edges only
 #if SKIM_HE_TABLE
     return A.he[idx];
 #else
@@ -446,7 +465,7 @@ SKIM_DEV uint64_t edge_key(const TravArgs &A, const Desc &d, uint32_t idx, uint3
 template <bool FWD, bool MAT>
 SKIM_DEV uint64_t edge_live_xh(const TravArgs &A, const Desc &d, uint32_t idx, uint32_t x, uint64_t he,
                                const uint64_t *ginst) {
-    if (MAT) return FWD ? (d.mask & he) : d.mask;
+    if (MAT) return d.mask;
     if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A, idx, d.v, x), ginst);
     const uint64_t t1 = edge_tm1_rev(A, idx, x, d.v, d.tm1);
     if (d.single) return fmix(he + d.g1) <= t1 ? d.mask : 0;
@@ -458,7 +477,7 @@ SKIM_DEV uint64_t edge_live(const TravArgs &A, const Desc &d, uint32_t idx, uint
     const uint32_t x = A.col[idx];
     const uint64_t he = edge_key<FWD, MAT>(A, d, idx, x);
     *tgt = x;
-    if (MAT) return FWD ? (d.mask & he) : d.mask;
+    if (MAT) return d.mask;
     if (FWD) return live_lanes(he, d.mask, edge_tm1_fwd(A, idx, d.v, x), ginst);
     const uint64_t t1 = edge_tm1_rev(A, idx, x, d.v, d.tm1);
     if (d.single) return fmix(he + d.g1) <= t1 ? d.mask : 0;
@@ -484,7 +503,7 @@ SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, const Desc &d, const uint64
     for (int q = 0; q < kUnroll; q++) {
         uint64_t live = lv[q];
         if (FWD) {
-            emit_fwd(A, acc, live != 0, tg[q], live);
+            emit_fwd<MAT>(A, acc, live != 0, tg[q], live);
         } else if (MAT) {
             emit_rev_mat(A, acc, live != 0, tg[q], d.w >> kChunkBits, __ffsll(d.mask) - 1, d.inst);
         } else {
@@ -773,14 +792,20 @@ __global__ void k_respill_fwd(TravArgs A, uint32_t n) {
             pe = atomicExch(reinterpret_cast<unsigned long long *>(&A.pend_erase[v]), 0ull);
         }
         Acc acc;
-        push_fwd(A, acc, v < n ? v : 0, pt, pe);
+        if (A.mat)
+            push_fwd<true>(A, acc, v < n ? v : 0, pt, pe);
+        else
+            push_fwd<false>(A, acc, v < n ? v : 0, pt, pe);
     }
 }
 
 __global__ void k_fwd_source(TravArgs A, uint32_t x) {
     const uint64_t lmask = A.l == 64 ? ~0ull : ((1ull << A.l) - 1);
     Acc acc;
-    emit_fwd(A, acc, threadIdx.x == 0, x, lmask);
+    if (A.mat)
+        emit_fwd<true>(A, acc, threadIdx.x == 0, x, lmask);
+    else
+        emit_fwd<false>(A, acc, threadIdx.x == 0, x, lmask);
     flush_acc(A, acc, true);
 }
 
