@@ -49,9 +49,13 @@ SKIM_DEV bool run_start(const uint64_t *rec_key, uint64_t r, uint32_t tbits) {
     return r == 0 || (rec_key[r] >> tbits) != (rec_key[r - 1] >> tbits);
 }
 
-__global__ void k_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                         const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
-                         uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl) {
+// Algorithm 2's acceptance for the records of one batch (sorted by key, so a
+// node's records are adjacent and in lane = rank order).
+__global__ void k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *__restrict__ rec_val, uint64_t R,
+                         uint32_t tbits, const uint64_t *__restrict__ hvals, const uint8_t *__restrict__ lane_inst,
+                         const uint64_t *__restrict__ lane_rank, uint32_t l, uint32_t k, uint8_t *__restrict__ lcnt,
+                         uint64_t *__restrict__ full, uint64_t *__restrict__ X, uint32_t *__restrict__ xlen,
+                         DevCtl *ctl) {
     unsigned long long ins = 0;
     for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
          r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {

@@ -44,6 +44,7 @@ struct skim_ctx {
     uint64_t *rmask = nullptr, *fmask = nullptr, *loff = nullptr, *foff = nullptr;
     uint32_t *rlive = nullptr, *flive = nullptr;  // live in- and out-neighbour rows
     uint32_t *rrow = nullptr, *rev2fwd = nullptr;  // per reverse CSR edge: head, forward position
+    void *pieces = nullptr;                         // workspace of the long-row passes
     uint64_t rlive_cap = 0, live_total = 0;
     uint64_t rank_key = 0;
     // graphs of a batch (skim_create_batch): per-node rank bases, per-edge
@@ -582,10 +583,11 @@ int make_instances(skim_ctx *c) {
         RC(dalloc(c, &c->fmask, std::max<uint64_t>(c->m, 1)));
         RC(dalloc(c, &c->loff, c->nl + 1));
         RC(dalloc(c, &c->foff, c->nl + 1));
+        CK(c, cudaMalloc(&c->pieces, live_pieces_bytes(c->m)));
     }
     CK(c, launch_live_masks(c->rrow, c->rcol, c->rhe, c->rtm1, c->rev2fwd, c->cm, c->m, c->l, c->rmask, c->fmask,
                             c->st));
-    CK(c, launch_live_count(c->rptr, c->rmask, c->n, c->l, c->loff, c->st));
+    CK(c, launch_live_count(c->rptr, c->rmask, c->n, c->m, c->l, c->loff, c->pieces, c->st));
     CK(c, cudaMemsetAsync(c->loff + c->nl, 0, sizeof(uint64_t), c->st));
     CK(c, exclusive_scan_u64(c->loff, c->loff, c->nl + 1, nullptr, c->ws, c->st));
     CK(c, cudaMemcpyAsync(&c->live_total, c->loff + c->nl, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->st));
@@ -599,12 +601,12 @@ int make_instances(skim_ctx *c) {
         RC(dalloc(c, &c->flive, c->live_total));
         c->rlive_cap = c->live_total;
     }
-    CK(c, launch_live_fill(c->rptr, c->rcol, c->rmask, c->n, c->l, c->loff, c->rlive, c->st));
+    CK(c, launch_live_fill(c->rptr, c->rcol, c->rmask, c->n, c->m, c->l, c->loff, c->rlive, c->pieces, c->st));
     // the same live pairs by tail: rows of live out-neighbours for the residual
-    CK(c, launch_live_count(c->fptr, c->fmask, c->n, c->l, c->foff, c->st));
+    CK(c, launch_live_count(c->fptr, c->fmask, c->n, c->m, c->l, c->foff, c->pieces, c->st));
     CK(c, cudaMemsetAsync(c->foff + c->nl, 0, sizeof(uint64_t), c->st));
     CK(c, exclusive_scan_u64(c->foff, c->foff, c->nl + 1, nullptr, c->ws, c->st));
-    CK(c, launch_live_fill(c->fptr, c->fcol, c->fmask, c->n, c->l, c->foff, c->flive, c->st));
+    CK(c, launch_live_fill(c->fptr, c->fcol, c->fmask, c->n, c->m, c->l, c->foff, c->flive, c->pieces, c->st));
     c->mat = true;
     return SKIM_OK;
 }
@@ -709,6 +711,7 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->rec_tau); dfree(c->rec_kp);
     dfree(c->rmask); dfree(c->fmask); dfree(c->loff); dfree(c->rlive); dfree(c->rrow); dfree(c->rev2fwd);
     dfree(c->foff); dfree(c->flive);
+    if (c->pieces) cudaFree(c->pieces);
     dfree(c->qk); dfree(c->qv); dfree(c->qseeds); dfree(c->qoff); dfree(c->qout);
     dfree(c->qtop); dfree(c->qtopu);
     if (c->qpart) cudaFree(c->qpart);

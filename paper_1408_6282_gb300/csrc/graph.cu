@@ -114,61 +114,175 @@ __global__ void k_live_masks(const uint32_t *rrow, const uint32_t *rcol, const u
     }
 }
 
-// One warp per node v, tiles of 32 in-edges (one per lane): for instance b
-// the tile holds popc(ballot(bit b)) live in-edges; lane b % 32 keeps the
-// counts of instances b < 32 and b >= 32.
-__global__ void k_live_count(const uint32_t *rptr, const uint64_t *rmask, uint32_t n, uint32_t l, uint64_t *off) {
+// Live rows from the masks.  A warp walks edges [e0, e1) of a row in tiles of
+// 32 (one per lane); for instance b the tile holds popc(ballot(bit b)) live
+// edges.  Lane b % 32 keeps the counts (or write cursors) of instances b < 32
+// (c0) and b >= 32 (c1).  Rows of up to kBigRow edges take one warp; longer
+// rows take a block of 8 warps on contiguous slices (kernels *_big).
+constexpr uint32_t kBigRow = 2048;
+
+// Rows longer than kBigRow are cut into pieces of kBigRow edges, one warp per
+// piece: the row's pieces get consecutive ids (in edge order) when the count
+// pass meets the row; each piece's per-instance counts are summed per row into
+// off, with the exclusive prefix of every piece kept for the fill pass.
+struct Pieces {
+    uint32_t *row;      // node of each piece
+    uint32_t *e0;       // first edge of each piece
+    uint64_t *cnt;      // 64 per piece: live edges of each instance, then the prefix within the row
+    unsigned *count;    // pieces in use
+    uint32_t cap;
+};
+
+SKIM_DEV void claim_pieces(const Pieces &P, uint32_t v, uint32_t e0, uint32_t e1) {
+    const uint32_t np = (e1 - e0 + kBigRow - 1) / kBigRow;
+    const unsigned base = atomicAdd(P.count, np);
+    for (uint32_t q = 0; q < np && base + q < P.cap; q++) {
+        P.row[base + q] = v;
+        P.e0[base + q] = e0 + q * kBigRow;
+    }
+}
+
+// A tile whose masks hold more than kDenseBits instances is walked edge by
+// edge instead (each lane tests its own two instances in every mask).
+constexpr int kDenseBits = 12;
+
+SKIM_DEV void warp_count(const uint64_t *mask, uint32_t e0, uint32_t e1, uint64_t &c0, uint64_t &c1) {
     const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
-        uint64_t c0 = 0, c1 = 0;
-        const uint32_t e1 = rptr[v + 1];
-        for (uint32_t e0 = rptr[v]; e0 < e1; e0 += 32) {
-            const uint64_t mk = e0 + lane < e1 ? rmask[e0 + lane] : 0;
-            uint64_t any = mk;
+    for (; e0 < e1; e0 += 32) {
+        const uint64_t mk = e0 + lane < e1 ? mask[e0 + lane] : 0;
+        uint64_t any = mk;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(kFull, any, o);
-            for (uint64_t bits = any; bits; bits &= bits - 1) {
-                const uint32_t b = __ffsll(bits) - 1;
-                const uint32_t c = __popc(__ballot_sync(kFull, (mk >> b) & 1ull));
-                if (lane == (b & 31)) {
-                    if (b < 32) c0 += c;
-                    else c1 += c;
-                }
+        for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(kFull, any, o);
+        if (__popcll(any) > kDenseBits) {
+#pragma unroll 8
+            for (int q = 0; q < 32; q++) {
+                const uint64_t m = __shfl_sync(kFull, mk, q);
+                c0 += (m >> lane) & 1ull;
+                c1 += (m >> (lane + 32)) & 1ull;
+            }
+            continue;
+        }
+        for (uint64_t bits = any; bits; bits &= bits - 1) {
+            const uint32_t b = __ffsll(bits) - 1;
+            const uint32_t c = __popc(__ballot_sync(kFull, (mk >> b) & 1ull));
+            if (lane == (b & 31)) {
+                if (b < 32) c0 += c;
+                else c1 += c;
             }
         }
+    }
+}
+
+SKIM_DEV void warp_fill(const uint64_t *mask, const uint32_t *col, uint32_t e0, uint32_t e1, uint64_t &p0,
+                        uint64_t &p1, uint32_t *live) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (; e0 < e1; e0 += 32) {
+        const bool in = e0 + lane < e1;
+        const uint64_t mk = in ? mask[e0 + lane] : 0;
+        const uint32_t w = in ? col[e0 + lane] : 0;
+        uint64_t any = mk;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(kFull, any, o);
+        if (__popcll(any) > kDenseBits) {
+#pragma unroll 8
+            for (int q = 0; q < 32; q++) {
+                const uint64_t m = __shfl_sync(kFull, mk, q);
+                const uint32_t x = __shfl_sync(kFull, w, q);
+                if ((m >> lane) & 1ull) live[p0++] = x;
+                if ((m >> (lane + 32)) & 1ull) live[p1++] = x;
+            }
+            continue;
+        }
+        for (uint64_t bits = any; bits; bits &= bits - 1) {
+            const uint32_t b = __ffsll(bits) - 1;
+            const unsigned bb = __ballot_sync(kFull, (mk >> b) & 1ull);
+            const uint64_t cur = __shfl_sync(kFull, b < 32 ? p0 : p1, b & 31);
+            if ((mk >> b) & 1ull) live[cur + __popc(bb & lanemask_lt())] = w;
+            if (lane == (b & 31)) {
+                if (b < 32) p0 += __popc(bb);
+                else p1 += __popc(bb);
+            }
+        }
+    }
+}
+
+// counts of live edges per (node, instance) into off[v*l + i], rows up to kBigRow
+__global__ void k_live_count(const uint32_t *ptr, const uint64_t *mask, uint32_t n, uint32_t l, uint64_t *off,
+                             Pieces P) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t e0 = ptr[v], e1 = ptr[v + 1];
+        if (e1 - e0 > kBigRow) {  // counted by pieces (k_piece_*)
+            if (lane == 0) claim_pieces(P, v, e0, e1);
+            continue;
+        }
+        uint64_t c0 = 0, c1 = 0;
+        warp_count(mask, e0, e1, c0, c1);
         const uint64_t base = static_cast<uint64_t>(v) * l;
         if (lane < l) off[base + lane] = c0;
         if (lane + 32 < l) off[base + lane + 32] = c1;
     }
 }
 
-// Same tiles: the live in-neighbours of (v, b) are written in row order from
-// off[v*l + b] on; lane b % 32 keeps the write cursors of instances b, b + 32.
-__global__ void k_live_fill(const uint32_t *rptr, const uint32_t *rcol, const uint64_t *rmask, uint32_t n,
-                            uint32_t l, const uint64_t *off, uint32_t *live) {
+// the live edges of (v, i) written in row order from off[v*l + i], rows up to kBigRow
+__global__ void k_live_fill(const uint32_t *ptr, const uint32_t *col, const uint64_t *mask, uint32_t n, uint32_t l,
+                            const uint64_t *off, uint32_t *live) {
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t e0 = ptr[v], e1 = ptr[v + 1];
+        if (e1 - e0 > kBigRow) continue;
         const uint64_t base = static_cast<uint64_t>(v) * l;
         uint64_t p0 = lane < l ? off[base + lane] : 0, p1 = lane + 32 < l ? off[base + lane + 32] : 0;
-        const uint32_t e1 = rptr[v + 1];
-        for (uint32_t e0 = rptr[v]; e0 < e1; e0 += 32) {
-            const bool in = e0 + lane < e1;
-            const uint64_t mk = in ? rmask[e0 + lane] : 0;
-            const uint32_t w = in ? rcol[e0 + lane] : 0;
-            uint64_t any = mk;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(kFull, any, o);
-            for (uint64_t bits = any; bits; bits &= bits - 1) {
-                const uint32_t b = __ffsll(bits) - 1;
-                const unsigned bb = __ballot_sync(kFull, (mk >> b) & 1ull);
-                const uint64_t cur = __shfl_sync(kFull, b < 32 ? p0 : p1, b & 31);
-                if ((mk >> b) & 1ull) live[cur + __popc(bb & lanemask_lt())] = w;
-                if (lane == (b & 31)) {
-                    if (b < 32) p0 += __popc(bb);
-                    else p1 += __popc(bb);
-                }
-            }
+        warp_fill(mask, col, e0, e1, p0, p1, live);
+    }
+}
+
+__global__ void k_piece_count(const uint32_t *ptr, const uint64_t *mask, Pieces P) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t np = min(*P.count, P.cap);
+    for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < np; p += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t v = P.row[p], e0 = P.e0[p], e1 = min(ptr[v + 1], e0 + kBigRow);
+        uint64_t c0 = 0, c1 = 0;
+        warp_count(mask, e0, e1, c0, c1);
+        P.cnt[static_cast<uint64_t>(p) * 64 + lane] = c0;
+        P.cnt[static_cast<uint64_t>(p) * 64 + lane + 32] = c1;
+    }
+}
+
+// one warp per row (its first piece): per instance, the row's total into off
+// and each piece's count replaced by the sum over the row's earlier pieces
+__global__ void k_piece_rows(const uint32_t *ptr, uint32_t l, uint64_t *off, Pieces P) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t np = min(*P.count, P.cap);
+    for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < np; p += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t v = P.row[p];
+        if (P.e0[p] != ptr[v]) continue;  // not the row's first piece
+        uint64_t r0 = 0, r1 = 0;
+        for (uint32_t q = p; q < np && P.row[q] == v; q++) {
+            uint64_t *c = P.cnt + static_cast<uint64_t>(q) * 64;
+            const uint64_t a0 = c[lane], a1 = c[lane + 32];
+            c[lane] = r0;
+            c[lane + 32] = r1;
+            r0 += a0;
+            r1 += a1;
         }
+        const uint64_t base = static_cast<uint64_t>(v) * l;
+        if (lane < l) off[base + lane] = r0;
+        if (lane + 32 < l) off[base + lane + 32] = r1;
+    }
+}
+
+__global__ void k_piece_fill(const uint32_t *ptr, const uint32_t *col, const uint64_t *mask, uint32_t l,
+                             const uint64_t *off, uint32_t *live, Pieces P) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t np = min(*P.count, P.cap);
+    for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < np; p += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t v = P.row[p], e0 = P.e0[p], e1 = min(ptr[v + 1], e0 + kBigRow);
+        const uint64_t base = static_cast<uint64_t>(v) * l;
+        const uint64_t *c = P.cnt + static_cast<uint64_t>(p) * 64;
+        uint64_t p0 = lane < l ? off[base + lane] + c[lane] : 0;
+        uint64_t p1 = lane + 32 < l ? off[base + lane + 32] + c[lane + 32] : 0;
+        warp_fill(mask, col, e0, e1, p0, p1, live);
     }
 }
 
@@ -182,8 +296,9 @@ __global__ void k_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long
 }
 
 // ---- rank order ---------------------------------------------------------
-constexpr int kBucketCap = 4096;     // pairs sorted in shared memory per bucket
-constexpr int kBucketThreads = 512;
+constexpr int kBucketCap = 2048;     // pairs sorted in shared memory per bucket
+constexpr int kBucketThreads = 256;
+constexpr int kSubBits = 11;         // counting sort of a bucket on the next 11 key bits
 constexpr uint64_t kBucketMean = 1024;  // target mean bucket size
 
 SKIM_DEV uint64_t rank_of(uint64_t rank_key, const uint64_t *rbase, uint32_t l, uint64_t x) {
@@ -205,6 +320,7 @@ struct UniformKeys {
     int bb;
     SKIM_DEV uint64_t key(uint64_t x) const { return rank_of(rank_key, rbase, l, x); }
     SKIM_DEV uint64_t bucket(uint64_t, uint64_t key) const { return bb ? (key >> (64 - bb)) : 0; }
+    SKIM_DEV uint32_t sub(uint64_t key) const { return static_cast<uint32_t>((key << bb) >> (64 - kSubBits)); }
     SKIM_DEV uint64_t out_rank(uint64_t, uint64_t key) const { return key; }
     SKIM_DEV uint32_t out_pair(uint64_t x) const { return static_cast<uint32_t>(x); }
 };
@@ -218,6 +334,7 @@ struct ChunkKeys {
     SKIM_DEV uint64_t bucket(uint64_t x, uint64_t key) const {
         return ((x / n) << bb) | (bb ? (key >> (64 - bb)) : 0);
     }
+    SKIM_DEV uint32_t sub(uint64_t key) const { return static_cast<uint32_t>((key << bb) >> (64 - kSubBits)); }
     SKIM_DEV uint64_t out_rank(uint64_t pos, uint64_t) const { return pos; }
     SKIM_DEV uint32_t out_pair(uint64_t x) const {
         const uint32_t v = static_cast<uint32_t>(x % n);
@@ -245,50 +362,81 @@ __global__ void k_rank_scatter(K kf, uint64_t total, const uint64_t *off, unsign
 }
 
 // Sort one bucket by key.  Keys are distinct (each key map is a bijection of
-// x), so a bucket larger than the shared-memory capacity can be placed by
-// counting smaller keys; that path is correct for any size and only its speed
-// depends on the (uniform) bucket sizes.
+// x) and uniform, so a bucket of up to kBucketCap elements is placed by a
+// counting sort on the next kSubBits bits below the bucket's own, after which
+// the few elements sharing a sub-bucket are put in order one sub-bucket per
+// thread.  A larger bucket is placed by counting smaller keys; that path is
+// correct for any size and only its speed depends on the bucket sizes.
 template <class K>
 __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(K kf, const uint64_t *off, const uint32_t *tmp,
                                                                 uint64_t *sorted_rank, uint32_t *sorted_pair) {
+    constexpr int kSub = 1 << kSubBits;
     __shared__ uint64_t key[kBucketCap];
     __shared__ uint32_t val[kBucketCap];
+    __shared__ uint32_t cnt[kSub];
+    __shared__ uint32_t wsum[kBucketThreads / 32];
     const uint64_t b0 = off[blockIdx.x], b1 = off[blockIdx.x + 1];
     const uint32_t s = static_cast<uint32_t>(b1 - b0);
     if (s == 0) return;
     if (s <= kBucketCap) {
-        uint32_t P = 1;
-        while (P < s) P <<= 1;
-        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-            if (i < s) {
-                uint32_t x = tmp[b0 + i];
-                val[i] = x;
-                key[i] = kf.key(x);
-            } else {
-                key[i] = ~0ull;
-                val[i] = 0;
+        for (uint32_t i = threadIdx.x; i < kSub; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) {
+            const uint32_t x = tmp[b0 + i];
+            const uint64_t kx = kf.key(x);
+            val[i] = x;
+            key[i] = kx;
+            atomicAdd(&cnt[kf.sub(kx)], 1u);
+        }
+        __syncthreads();
+        // exclusive scan of cnt: each thread owns kSub / blockDim.x consecutive counters
+        constexpr int per = kSub / kBucketThreads;
+        uint32_t loc[per], tot = 0;
+#pragma unroll
+        for (int q = 0; q < per; q++) {
+            loc[q] = tot;
+            tot += cnt[threadIdx.x * per + q];
+        }
+        uint32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, inc, o);
+            if ((threadIdx.x & 31) >= static_cast<unsigned>(o)) inc += y;
+        }
+        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = inc;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (uint32_t w = 0; w < (threadIdx.x >> 5); w++) wbase += wsum[w];
+        const uint32_t tbase = wbase + inc - tot;
+#pragma unroll
+        for (int q = 0; q < per; q++) cnt[threadIdx.x * per + q] = tbase + loc[q];
+        __syncthreads();
+        // scatter (keys in the rank slots for now); cnt[b] ends as the end of sub-bucket b
+        for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) {
+            const uint32_t pos = atomicAdd(&cnt[kf.sub(key[i])], 1u);
+            sorted_rank[b0 + pos] = key[i];
+            sorted_pair[b0 + pos] = val[i];
+        }
+        __syncthreads();
+        // order inside the sub-buckets that hold more than one element
+        for (uint32_t b = threadIdx.x; b < kSub; b += blockDim.x) {
+            const uint32_t lo = b ? cnt[b - 1] : 0, hi = cnt[b];
+            for (uint32_t i = lo + 1; i < hi; i++) {
+                const uint64_t kx = sorted_rank[b0 + i];
+                const uint32_t vx = sorted_pair[b0 + i];
+                uint32_t j = i;
+                for (; j > lo && sorted_rank[b0 + j - 1] > kx; j--) {
+                    sorted_rank[b0 + j] = sorted_rank[b0 + j - 1];
+                    sorted_pair[b0 + j] = sorted_pair[b0 + j - 1];
+                }
+                sorted_rank[b0 + j] = kx;
+                sorted_pair[b0 + j] = vx;
             }
         }
         __syncthreads();
-        for (uint32_t kk = 2; kk <= P; kk <<= 1) {
-            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                    uint32_t p = i ^ j;
-                    if (p > i) {
-                        bool up = (i & kk) == 0;
-                        uint64_t a = key[i], c = key[p];
-                        if ((a > c) == up) {
-                            key[i] = c; key[p] = a;
-                            uint32_t t = val[i]; val[i] = val[p]; val[p] = t;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
         for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) {
-            sorted_rank[b0 + i] = kf.out_rank(b0 + i, key[i]);
-            sorted_pair[b0 + i] = kf.out_pair(val[i]);
+            sorted_rank[b0 + i] = kf.out_rank(b0 + i, sorted_rank[b0 + i]);
+            sorted_pair[b0 + i] = kf.out_pair(sorted_pair[b0 + i]);
         }
         return;
     }
@@ -437,16 +585,46 @@ cudaError_t launch_live_masks(const uint32_t *rrow, const uint32_t *rcol, const 
     k_live_masks<<<grid_for(m, 256), 256, 0, s>>>(rrow, rcol, rhe, rtm1, rev2fwd, cm, m, l, rmask, fmask);
     return cudaGetLastError();
 }
-cudaError_t launch_live_count(const uint32_t *rptr, const uint64_t *rmask, uint32_t n, uint32_t l, uint64_t *off,
-                              cudaStream_t s) {
+size_t live_pieces_bytes(uint64_t m) {
+    const uint64_t cap = 2 * (m / kBigRow) + 2;
+    return cap * (4 + 4 + 64 * 8) + 256;
+}
+
+namespace {
+Pieces carve_pieces(void *ws, uint64_t m) {
+    Pieces P;
+    const uint64_t cap = 2 * (m / kBigRow) + 2;
+    char *p = static_cast<char *>(ws);
+    P.cnt = reinterpret_cast<uint64_t *>(p); p += cap * 64 * 8;
+    P.row = reinterpret_cast<uint32_t *>(p); p += cap * 4;
+    P.e0 = reinterpret_cast<uint32_t *>(p); p += cap * 4;
+    P.count = reinterpret_cast<unsigned *>((reinterpret_cast<uintptr_t>(p) + 15) & ~static_cast<uintptr_t>(15));
+    P.cap = static_cast<uint32_t>(cap);
+    return P;
+}
+unsigned piece_grid(uint64_t m) { return grid_for((2 * (m / kBigRow) + 2) * 32, 256, 152 * 8); }
+}  // namespace
+
+cudaError_t launch_live_count(const uint32_t *ptr, const uint64_t *mask, uint32_t n, uint64_t m, uint32_t l,
+                              uint64_t *off, void *pieces_ws, cudaStream_t s) {
+    const Pieces P = carve_pieces(pieces_ws, m);
+    cudaError_t e = cudaMemsetAsync(P.count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
     note_launch();
-    k_live_count<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(rptr, rmask, n, l, off);
+    k_live_count<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(ptr, mask, n, l, off, P);
+    note_launch();
+    k_piece_count<<<piece_grid(m), 256, 0, s>>>(ptr, mask, P);
+    note_launch();
+    k_piece_rows<<<piece_grid(m), 256, 0, s>>>(ptr, l, off, P);
     return cudaGetLastError();
 }
-cudaError_t launch_live_fill(const uint32_t *rptr, const uint32_t *rcol, const uint64_t *rmask, uint32_t n, uint32_t l,
-                             const uint64_t *off, uint32_t *live, cudaStream_t s) {
+cudaError_t launch_live_fill(const uint32_t *ptr, const uint32_t *col, const uint64_t *mask, uint32_t n, uint64_t m,
+                             uint32_t l, const uint64_t *off, uint32_t *live, void *pieces_ws, cudaStream_t s) {
+    const Pieces P = carve_pieces(pieces_ws, m);
     note_launch();
-    k_live_fill<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(rptr, rcol, rmask, n, l, off, live);
+    k_live_fill<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(ptr, col, mask, n, l, off, live);
+    note_launch();
+    k_piece_fill<<<piece_grid(m), 256, 0, s>>>(ptr, col, mask, l, off, live, P);
     return cudaGetLastError();
 }
 

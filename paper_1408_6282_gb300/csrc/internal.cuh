@@ -82,10 +82,14 @@ cudaError_t launch_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr
 cudaError_t launch_live_masks(const uint32_t *rrow, const uint32_t *rcol, const uint64_t *rhe, const uint64_t *rtm1,
                               const uint32_t *rev2fwd, const CoinModel &cm, uint64_t m, uint32_t l, uint64_t *rmask,
                               uint64_t *fmask, cudaStream_t s);
-cudaError_t launch_live_count(const uint32_t *rptr, const uint64_t *rmask, uint32_t n, uint32_t l, uint64_t *off,
-                              cudaStream_t s);
-cudaError_t launch_live_fill(const uint32_t *rptr, const uint32_t *rcol, const uint64_t *rmask, uint32_t n, uint32_t l,
-                             const uint64_t *off, uint32_t *live, cudaStream_t s);
+// Rows of more than 2048 edges are counted and filled in pieces, using a
+// workspace of live_pieces_bytes(m); the count pass of a CSR direction must
+// precede its fill pass with the same workspace.
+size_t live_pieces_bytes(uint64_t m);
+cudaError_t launch_live_count(const uint32_t *ptr, const uint64_t *mask, uint32_t n, uint64_t m, uint32_t l,
+                              uint64_t *off, void *pieces_ws, cudaStream_t s);
+cudaError_t launch_live_fill(const uint32_t *ptr, const uint32_t *col, const uint64_t *mask, uint32_t n, uint64_t m,
+                             uint32_t l, const uint64_t *off, uint32_t *live, void *pieces_ws, cudaStream_t s);
 cudaError_t launch_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_t n, uint64_t coin_key, int reverse,
                                uint64_t *he, cudaStream_t s);
 cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out, cudaStream_t s);
