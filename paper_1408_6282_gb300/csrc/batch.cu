@@ -96,14 +96,6 @@ __global__ void k_table_init(uint64_t *table, uint64_t slots) {
         reinterpret_cast<ulonglong2 *>(table)[i] = make_ulonglong2(kEmptyKey, 0ull);
 }
 
-__global__ void k_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hkeys, uint64_t *hvals) {
-    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
-         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        uint32_t s = rec_val[r];
-        hkeys[2ull * s] = kEmptyKey;  // key and bits of a slot share 16 bytes
-        hvals[2ull * s] = 0;
-    }
-}
 
 // lanes of word t inside [lo, hi] (inclusive), lo <= hi
 SKIM_DEV uint64_t range_mask(uint64_t t, uint32_t lo, uint32_t hi) {
@@ -271,12 +263,6 @@ cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint
 cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s) {
     note_launch();
     k_table_init<<<grid_for(slots, 256), 256, 0, s>>>(table, slots);
-    return cudaGetLastError();
-}
-cudaError_t launch_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hkeys, uint64_t *hvals, cudaStream_t s) {
-    if (R == 0) return cudaSuccess;
-    note_launch();
-    k_clear_slots<<<grid_for(R, 256), 256, 0, s>>>(rec_val, R, hkeys, hvals);
     return cudaGetLastError();
 }
 cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,

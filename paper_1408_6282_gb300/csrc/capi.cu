@@ -60,6 +60,7 @@ struct skim_ctx {
     uint64_t qcap = 0;
     uint64_t *hkeys = nullptr, *hvals = nullptr, *pend = nullptr;
     uint64_t hcap = 0;
+    uint64_t gen = 0;  // generation of the visited table's current keys
     uint64_t *rkey = nullptr, *rkey2 = nullptr;
     uint32_t *rval = nullptr, *rval2 = nullptr;
     uint64_t rcap = 0;
@@ -90,6 +91,7 @@ struct skim_ctx {
     uint32_t bB = 0, btbits = 0, blo = 0;
     uint64_t bR = 0;
     uint32_t skim_B = 0;
+    uint32_t retry_run = 0;  // consecutive SKIM batch re-runs
     // SKIM batch sizing: ranks consumed since the last seed, and the gap (in
     // ranks) between the last two seeds
     uint64_t since_stop = 0, last_gap = 0;
@@ -323,6 +325,11 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     if (!mode_build) CK(c, cudaMemsetAsync(c->alive, 0, T * sizeof(uint64_t), c->st));
     TravArgs a = base_args(c, false);
     a.tbits = tbits;
+    if (++c->gen >= kGenLimit) {  // generations used up: empty every slot once
+        CK(c, clear_table(c));
+        c->gen = 1;
+    }
+    a.hgen = c->gen << kGenShift;
     if (est_per_lane > 0) {
         const uint64_t want = pow2_at_least(std::max<uint64_t>(
             1ull << 16, static_cast<uint64_t>(8.0 * est_per_lane * static_cast<double>(B))));
@@ -358,9 +365,9 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     return SKIM_OK;
 }
 
+// Release the active batch's records.  Its table slots need no clearing: the
+// next batch's keys carry a new generation.
 int clear_batch(skim_ctx *c) {
-    KTimer kt(c, SKIM_K_SORT);  // visit-record bookkeeping: empty the batch's table slots
-    CK(c, launch_clear_slots(c->rval, c->bR, c->hkeys, c->hvals, c->st));
     c->bR = 0;
     return SKIM_OK;
 }
@@ -531,10 +538,12 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
             bool retry = false;
             RC(rev_batch(c, c->cursor, B, false, &retry, c->vpl_est));
             if (retry) {
+                if (++c->retry_run > 48) return SKIM_ENOMEM;  // the tables cannot hold even small batches
                 c->skim_B = std::max<uint32_t>(64, B / 2);
                 c->vpl_est *= 4;  // more records than expected: a larger table too
                 continue;
             }
+            c->retry_run = 0;
             c->skim_B = 0;
             c->batch_active = true;
             c->bp0 = c->cursor;
@@ -1101,6 +1110,7 @@ int skim_build_sketches(skim_ctx *c) {
         bool retry = false;
         RC(rev_batch(c, p0, b, true, &retry, rpl));
         if (retry) {
+            if (b <= 64) return SKIM_ENOMEM;  // even the smallest batch overflows the tables
             B = std::max<uint32_t>(64, b / 4);
             rpl = 0;  // the whole table for the re-run
             continue;

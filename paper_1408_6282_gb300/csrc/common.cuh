@@ -22,6 +22,12 @@ inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_rel
 
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kEmptyKey = ~0ull;
+// Visited-table keys carry the generation of their batch in bits 51..62, so a
+// slot of an earlier batch counts as empty and no batch has to clear the
+// table (node << tbits | word stays below 2^51: node < 2^32, tbits <= 19).
+constexpr int kGenShift = 51;
+constexpr uint64_t kGenMask = 0xFFFull << kGenShift;
+constexpr uint64_t kGenLimit = 0xFFF;  // generations 1 .. kGenLimit - 1, then a full clear
 // key of the within-chunk node order of permutation ranks: fmix(rank_key ^ salt)
 constexpr uint64_t kPermSalt = 0x7065726d75746531ull;
 constexpr unsigned kFull = 0xffffffffu;

@@ -35,6 +35,7 @@ struct TravArgs {
     uint64_t *hkeys;
     uint64_t *hvals;
     uint64_t hmask;
+    uint64_t hgen;              // generation of this batch's table keys, already shifted (kGenShift)
     uint64_t *rec_key;
     uint32_t *rec_val;
     uint64_t rcap;
@@ -143,7 +144,6 @@ cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint
                           uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
                           cudaStream_t s);
 cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s);
-cudaError_t launch_clear_slots(const uint32_t *rec_val, uint64_t R, uint64_t *hkeys, uint64_t *hvals, cudaStream_t s);
 cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                               const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
                               uint32_t k, DevCtl *ctl, cudaStream_t s);

@@ -45,26 +45,49 @@ SKIM_DEV uint64_t edge_tm1_fwd(const TravArgs &A, uint32_t idx, uint32_t u, uint
     return cm.tm1_class[fmix(cm.prob_key ^ ((static_cast<uint64_t>(u) << 32) | w)) % 3u];
 }
 
+// 16-byte compare-and-swap of a table slot {key, bits}: true if the slot held
+// {ek, eb}; *ok, *ob = what it held.
+SKIM_DEV bool cas_slot(uint64_t *slot, uint64_t ek, uint64_t eb, uint64_t nk, uint64_t nb, uint64_t *ok,
+                       uint64_t *ob) {
+    uint64_t lo, hi;
+    asm volatile(
+        "{\n\t.reg .b128 d, b, c;\n\t"
+        "mov.b128 b, {%2, %3};\n\t"
+        "mov.b128 c, {%4, %5};\n\t"
+        "atom.global.cas.b128 d, [%6], b, c;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(lo), "=l"(hi)
+        : "l"(ek), "l"(eb), "l"(nk), "l"(nb), "l"(slot)
+        : "memory");
+    *ok = lo;
+    *ob = hi;
+    return lo == ek && hi == eb;
+}
+
 // Insert-or-merge of (key, bits) into the visited table.  Returns false if the
 // probe limit is hit.  *old = bits present before, *slot = table slot,
 // *first = this call created the entry.  Slot h keeps its key at hkeys[2h] and
-// its bits at hvals[2h] (hvals = hkeys + 1): both in one 16-byte sector.
-SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t key, uint64_t bits, uint64_t *old,
-                      uint64_t *slot, bool *first) {
+// its bits at hvals[2h] (hvals = hkeys + 1): both in one 16-byte sector.  Keys
+// carry the batch's generation gen (already shifted); a slot holding another
+// generation's key, or none, is free and is claimed by a 16-byte CAS that sets
+// key and bits together (so no other lane can OR bits into a stale word).
+SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t gen, uint64_t key, uint64_t bits,
+                      uint64_t *old, uint64_t *slot, bool *first) {
+    key |= gen;
     uint64_t h = fmix(key) & hmask;
     for (int p = 0; p < kMaxProbe; p++) {
-        uint64_t k = *reinterpret_cast<volatile uint64_t *>(&hkeys[2 * h]);
-        if (k == kEmptyKey) {
-            unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long *>(&hkeys[2 * h]),
-                                                static_cast<unsigned long long>(kEmptyKey),
-                                                static_cast<unsigned long long>(key));
-            if (prev == kEmptyKey) {
+        uint64_t k, b;
+        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(k), "=l"(b) : "l"(&hkeys[2 * h]) : "memory");
+        if (k != key && (k == kEmptyKey || (k & kGenMask) != gen)) {
+            uint64_t ok, ob;
+            if (cas_slot(&hkeys[2 * h], k, b, key, bits, &ok, &ob)) {
                 *first = true;
                 *slot = h;
-                *old = atomicOr(reinterpret_cast<unsigned long long *>(&hvals[2 * h]), bits);
+                *old = 0;
                 return true;
             }
-            k = prev;
+            k = ok;  // someone else changed the slot: look at what is there now
+            if (k != key && (k == kEmptyKey || (k & kGenMask) != gen)) continue;  // still free: try again
         }
         if (k == key) {
             *first = false;
@@ -198,7 +221,7 @@ SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32
     if (act && bits) {
         uint64_t old;
         uint64_t key = (static_cast<uint64_t>(u) << A.tbits) | t;
-        if (hash_or(A.hkeys, A.hvals, A.hmask, key, bits, &old, &slot, &first)) {
+        if (hash_or(A.hkeys, A.hvals, A.hmask, A.hgen, key, bits, &old, &slot, &first)) {
             nb = bits & ~old;
         } else {
             atomicOr(&A.ctl->err, kErrHash);
@@ -244,7 +267,7 @@ SKIM_DEV void emit_rev_mat(const TravArgs &A, Acc &acc, bool act, uint32_t u, ui
     if (act) {
         uint64_t old;
         const uint64_t key = (static_cast<uint64_t>(u) << A.tbits) | t;
-        if (hash_or(A.hkeys, A.hvals, A.hmask, key, bit, &old, &slot, &first))
+        if (hash_or(A.hkeys, A.hvals, A.hmask, A.hgen, key, bit, &old, &slot, &first))
             fresh = !(old & bit);
         else
             atomicOr(&A.ctl->err, kErrHash);
