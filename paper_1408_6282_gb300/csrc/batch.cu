@@ -17,6 +17,7 @@
 // and the inverted index), the rest stay valid for the next step because a
 // search from an uncovered pair never meets a covered node.
 #include "internal.cuh"
+#include "prims.cuh"
 
 namespace skim {
 
@@ -49,42 +50,170 @@ SKIM_DEV bool run_start(const uint64_t *rec_key, uint64_t r, uint32_t tbits) {
     return r == 0 || (rec_key[r] >> tbits) != (rec_key[r - 1] >> tbits);
 }
 
-// Algorithm 2's acceptance for the records of one batch (sorted by key, so a
-// node's records are adjacent and in lane = rank order).
-__global__ void k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *__restrict__ rec_val, uint64_t R,
-                         uint32_t tbits, const uint64_t *__restrict__ hvals, const uint8_t *__restrict__ lane_inst,
+// Algorithm 2's acceptance for the records of one batch, sorted by key so that
+// a node's records are adjacent and in lane = rank order.  Per (node v,
+// instance i) the first k - lcnt[v,i] offers are accepted (the instance-local
+// sketch), and accepted ranks are appended to X_v while it holds fewer than k.
+//
+// The runs (one per node) are listed in order first (run_flags, a scan,
+// run_list); then each lane of a warp takes one run: runs of up to kLongRun
+// records are walked by their lane, longer ones by the whole warp, 32
+// records at a time.
+
+#ifndef SKIM_LONG_RUN
+#define SKIM_LONG_RUN 8
+#endif
+constexpr uint32_t kLongRun = SKIM_LONG_RUN;
+
+__global__ void k_run_flags(const uint64_t *rec_key, uint64_t R, uint32_t tbits, uint64_t *flag) {
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r <= R;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        flag[r] = r < R && run_start(rec_key, r, tbits) ? 1 : 0;
+}
+
+// starts[q] = first record of run q (flag holds the exclusive scan of the
+// run-start flags); starts[runs] = R
+__global__ void k_run_list(const uint64_t *rec_key, uint64_t R, uint32_t tbits, const uint64_t *flag,
+                           uint32_t *starts) {
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r <= R;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        if (r == R) starts[flag[R]] = static_cast<uint32_t>(R);
+        else if (run_start(rec_key, r, tbits)) starts[flag[r]] = static_cast<uint32_t>(r);
+    }
+}
+
+__global__ void k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *__restrict__ rec_val,
+                         const uint32_t *__restrict__ starts, const uint64_t *__restrict__ nruns_p, uint32_t tbits,
+                         const uint64_t *__restrict__ hvals, const uint8_t *__restrict__ lane_inst,
                          const uint64_t *__restrict__ lane_rank, uint32_t l, uint32_t k, uint8_t *__restrict__ lcnt,
                          uint64_t *__restrict__ full, uint64_t *__restrict__ X, uint32_t *__restrict__ xlen,
                          DevCtl *ctl) {
+    __shared__ uint32_t need_s[8][64], seen_s[8][64];
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *need = need_s[wib], *seen = seen_s[wib];
+    const uint64_t nruns = *nruns_p;
+    const uint64_t tmask = (1ull << tbits) - 1;
     unsigned long long ins = 0;
-    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
-         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        if (!run_start(rec_key, r, tbits)) continue;
-        const uint64_t v = rec_key[r] >> tbits;
-        uint8_t *lc = lcnt + v * l;
-        uint64_t *xv = X + v * k;
-        uint32_t len = xlen[v];
-        uint64_t newfull = 0;
-        const uint64_t tmask = (1ull << tbits) - 1;
-        for (uint64_t rr = r; rr < R && (rec_key[rr] >> tbits) == v; rr++) {
-            const uint64_t t = rec_key[rr] & tmask;
-            uint64_t m = hvals[2ull * rec_val[rr]];
-            while (m) {
-                int j = __ffsll(m) - 1;
-                m &= m - 1;
-                const uint64_t lane = t * 64 + j;
-                const uint32_t i = lane_inst[lane];
-                const uint32_t c = lc[i];
-                if (c < k) {
-                    lc[i] = static_cast<uint8_t>(c + 1);
-                    ins++;
-                    if (c + 1 == k) newfull |= 1ull << i;
-                    if (len < k) xv[len++] = lane_rank[lane];
+    const uint64_t warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t w = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5; w * 32 < nruns; w += warps) {
+        const uint64_t q = w * 32 + lane;
+        uint32_t r0 = 0, r1 = 0;
+        if (q < nruns) {
+            r0 = starts[q];
+            r1 = starts[q + 1];
+        }
+        const bool longrun = r1 - r0 > kLongRun;
+        // short runs: one lane each
+        if (r1 > r0 && !longrun) {
+            const uint64_t v = rec_key[r0] >> tbits;
+            uint8_t *lc = lcnt + v * l;
+            uint64_t *xv = X + v * k;
+            uint32_t len = xlen[v];
+            uint64_t newfull = 0;
+            for (uint32_t rr = r0; rr < r1; rr++) {
+                const uint64_t t = rec_key[rr] & tmask;
+                uint64_t m = hvals[2ull * rec_val[rr]];
+                while (m) {
+                    const int j = __ffsll(m) - 1;
+                    m &= m - 1;
+                    const uint64_t ln = t * 64 + j;
+                    const uint32_t i = lane_inst[ln];
+                    const uint32_t c = lc[i];
+                    if (c < k) {
+                        lc[i] = static_cast<uint8_t>(c + 1);
+                        ins++;
+                        if (c + 1 == k) newfull |= 1ull << i;
+                        if (len < k) xv[len++] = lane_rank[ln];
+                    }
                 }
             }
+            xlen[v] = len;
+            if (newfull) full[v] |= newfull;
         }
-        xlen[v] = len;
-        if (newfull) full[v] |= newfull;
+        // long runs: the whole warp, one after another
+        for (unsigned lb = __ballot_sync(kFull, longrun); lb; lb &= lb - 1) {
+            const int src = __ffs(lb) - 1;
+            const uint32_t a0 = __shfl_sync(kFull, r0, src), a1 = __shfl_sync(kFull, r1, src);
+            const uint64_t v = rec_key[a0] >> tbits;
+            uint8_t *lc = lcnt + v * l;
+            uint64_t *xv = X + v * k;
+            for (uint32_t i = lane; i < 64; i += 32) {
+                need[i] = i < l ? k - lc[i] : 0;
+                seen[i] = 0;
+            }
+            uint32_t len = xlen[v];
+            __syncwarp();
+            for (uint32_t c0 = a0; c0 < a1; c0 += 32) {
+                const uint32_t rr = c0 + lane;
+                uint64_t m = 0, t = 0;
+                if (rr < a1) {
+                    m = hvals[2ull * rec_val[rr]];
+                    t = rec_key[rr] & tmask;
+                }
+                // the chunk's offers in lane (= rank) order, 32 at a time: offer o
+                // is bit (o - pre_s) of the record s with pre_s <= o < pre_s + cnt_s
+                const uint32_t cnt = __popcll(m);
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= static_cast<unsigned>(o)) incl += y;
+                }
+                const uint32_t pre = incl - cnt, total = __shfl_sync(kFull, incl, 31);
+                for (uint32_t g = 0; g < total; g += 32) {
+                    const uint32_t o = g + lane;
+                    const bool has = o < total;
+                    uint32_t src = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const uint32_t cand = src + step;
+                        const uint32_t pc = __shfl_sync(kFull, pre, cand);
+                        if (has && pc <= o) src = cand;
+                    }
+                    const uint64_t ms = __shfl_sync(kFull, m, src), ts = __shfl_sync(kFull, t, src);
+                    const uint32_t ps = __shfl_sync(kFull, pre, src);
+                    uint64_t ln = 0;
+                    uint32_t i = 0;
+                    if (has) {
+                        uint64_t x = ms;
+                        for (uint32_t skip = o - ps; skip; skip--) x &= x - 1;
+                        ln = ts * 64 + (__ffsll(x) - 1);
+                        i = lane_inst[ln];
+                    }
+                    // rank among the group's offers of the same instance
+                    const unsigned grp = __match_any_sync(kFull, has ? i : 64 + lane);
+                    const uint32_t before = __popc(grp & lanemask_lt());
+                    const bool acc = has && seen[i] + before < need[i];
+                    const unsigned ab = __ballot_sync(kFull, acc);
+                    if (acc) {
+                        const uint32_t pos = len + __popc(ab & lanemask_lt());
+                        if (pos < k) xv[pos] = lane_rank[ln];
+                        ins++;
+                    }
+                    len = min(k, len + __popc(ab));
+                    __syncwarp();
+                    if (has && before == 0) seen[i] += __popc(grp);  // one lane per instance group
+                    __syncwarp();
+                }
+            }
+            // local counts and full instances
+            uint64_t nf = 0;
+            for (uint32_t i = lane; i < l; i += 32) {
+                const uint32_t add = min(seen[i], need[i]);
+                if (add) {
+                    lc[i] = static_cast<uint8_t>(k - need[i] + add);
+                    if (add == need[i]) nf |= 1ull << i;
+                }
+            }
+            nf |= __shfl_xor_sync(kFull, nf, 16);
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) nf |= __shfl_xor_sync(kFull, nf, o);
+            if (lane == 0) {
+                xlen[v] = len;
+                if (nf) full[v] |= nf;
+            }
+            __syncwarp();
+        }
     }
     warp_add(&ctl->stats[kStInsert], ins);
 }
@@ -253,11 +382,17 @@ cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_ran
 cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                           const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
                           uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
-                          cudaStream_t s) {
+                          uint64_t *flag, uint32_t *starts, void *scan_ws, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
     note_launch();
-    k_accept<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, lane_inst, lane_rank, l, k, lcnt,
-                                              full, X, xlen, ctl);
+    k_run_flags<<<grid_for(R + 1, 256), 256, 0, s>>>(rec_key, R, tbits, flag);
+    cudaError_t e = exclusive_scan_u64(flag, flag, R + 1, nullptr, scan_ws, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_run_list<<<grid_for(R + 1, 256), 256, 0, s>>>(rec_key, R, tbits, flag, starts);
+    note_launch();
+    k_accept<<<grid_for((R + 31) / 32 * 32, 256), 256, 0, s>>>(rec_key, rec_val, starts, flag + R, tbits, hvals,
+                                                               lane_inst, lane_rank, l, k, lcnt, full, X, xlen, ctl);
     return cudaGetLastError();
 }
 cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s) {

@@ -822,6 +822,7 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         const uint64_t lanes_max = std::min<uint64_t>(npos, prm->batch_lanes ? prm->batch_lanes : (1u << 21));
         const uint64_t rcap = std::min<uint64_t>(std::max<uint64_t>(16ull * lanes_max, 1u << 20), 1ull << 26);
         size_t ws = std::max({scan_workspace_bytes(static_cast<size_t>(n) + 1), scan_workspace_bytes(nl + 1),
+                              scan_workspace_bytes(rcap + 1),
                               radix_workspace_bytes(m),
                               radix_workspace_bytes(rcap), scan_workspace_bytes(static_cast<size_t>(kMaxWords) * 64)});
         c->ws_bytes = ws;
@@ -906,9 +907,9 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         TRYC(clear_table(c));
         TRYC(cudaMemsetAsync(c->pend, 0, c->hcap * sizeof(uint64_t), c->st));
         TRY(dalloc(c, &c->rkey, c->rcap));
-        TRY(dalloc(c, &c->rkey2, c->rcap));
+        TRY(dalloc(c, &c->rkey2, c->rcap + 1));  // also the acceptance's run scratch (R + 1 entries)
         TRY(dalloc(c, &c->rval, c->rcap));
-        TRY(dalloc(c, &c->rval2, c->rcap));
+        TRY(dalloc(c, &c->rval2, c->rcap + 1));
         TRY(dalloc(c, &c->lane_inst, c->lane_cap));
         TRYC(cudaMemsetAsync(c->lane_inst, 0, c->lane_cap, c->st));
         TRY(dalloc(c, &c->lane_g, c->lane_cap));
@@ -1117,8 +1118,9 @@ int skim_build_sketches(skim_ctx *c) {
         }
         {
             KTimer kt(c, SKIM_K_ACCEPT);
+            // run scratch: the sort's alternate buffers are free after the sort
             CK(c, launch_accept(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->lane_inst, c->srank + p0, c->l,
-                                c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl, c->st));
+                                c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl, c->rkey2, c->rval2, c->ws, c->st));
         }
         const uint64_t recs = c->bR;
         RC(clear_batch(c));

@@ -139,10 +139,12 @@ int traverse_grid(bool forward);  // resident blocks for the persistent traversa
 // batch.cu
 cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_rank, uint32_t B, uint32_t l,
                              uint8_t *lane_inst, uint64_t *lane_g, cudaStream_t s);
+// Algorithm 2 acceptance of a batch's sorted records.  flag: R + 1 uint64 and
+// starts: R + 1 uint32 of scratch; scan_ws: scan workspace for R + 1 entries.
 cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                           const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
                           uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
-                          cudaStream_t s);
+                          uint64_t *flag, uint32_t *starts, void *scan_ws, cudaStream_t s);
 cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s);
 cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                               const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
