@@ -254,7 +254,7 @@ int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
 /* Kernel timing with CUDA events on the context's stream (off by default).
  * When on, the device time of each launch group below is accumulated until
  * the next call with reset != 0.  Kinds (index into ms_out / launches_out):
- *   SKIM_K_REV   reverse searches (Algorithms 1 and 2, the batched BFS, sources included)
+ *   SKIM_K_REV   reverse searches (Algorithms 1 and 2, the batched BFS)
  *   SKIM_K_FWD   residual forward searches (Algorithm 1)
  *   SKIM_K_ACCEPT Algorithm 2 acceptance into the sketches
  *   SKIM_K_SORT  grouping of visit records by node (radix sort), emptying their table slots
@@ -263,6 +263,7 @@ int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
  *   SKIM_K_QUERY union-estimator queries
  *   SKIM_K_SETUP CSR construction and validation
  *   SKIM_K_INSTANCES generation of the live-edge instances (skim_instances)
+ *   SKIM_K_SOURCES the sources of each batch of reverse searches (their first level)
  * Turning timing on creates a pool of 2048 CUDA events at once (so that no
  * event is created inside a timed bracket).  A bracket that holds a host
  * synchronisation (SKIM_K_STEP) also counts the host's share of that wait. */
@@ -275,7 +276,8 @@ int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
 #define SKIM_K_QUERY 6
 #define SKIM_K_SETUP 7
 #define SKIM_K_INSTANCES 8
-#define SKIM_K_COUNT 9
+#define SKIM_K_SOURCES 9
+#define SKIM_K_COUNT 10
 int skim_set_timing(skim_ctx *ctx, int on);
 
 /* Number of kernels this library has launched in the calling process since it

@@ -22,7 +22,7 @@ _ERR = {-1: "SKIM_EINVAL", -2: "SKIM_ENOMEM", -3: "SKIM_ENOTBUILT", -4: "SKIM_ET
 PROB_UNIFORM, PROB_WC, PROB_TRIVALENCY = 0, 1, 2
 RANKS_UNIFORM, RANKS_PERMUTATION, RANKS_IC_MODEL = 0, 1, 2
 KERNEL_NAMES = ("rev_search", "fwd_search", "accept", "record_sort", "skim_step", "rank_order", "query", "setup",
-                "instances")
+                "instances", "rev_sources")
 STAT_NAMES = ("rev_visits", "rev_coins", "insertions", "fwd_visits", "fwd_coins", "batches", "ranks", "retries",
               "rev_edges", "fwd_edges")
 

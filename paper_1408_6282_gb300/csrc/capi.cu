@@ -338,7 +338,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     // IC-model searches are never pruned: every lane is its own instance
     a.prune = mode_build && c->rank_mode != SKIM_RANKS_IC_MODEL ? 1 : 0;
     {
-        KTimer kt(c, SKIM_K_REV);  // the sources are the searches' first level
+        KTimer kt(c, SKIM_K_SOURCES);
         CK(c, launch_rev_sources(a, c->spair + p0, B, c->l, mode_build ? nullptr : c->covered,
                                  mode_build ? nullptr : c->alive, c->st));
     }
