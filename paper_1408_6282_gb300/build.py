@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libskim.so")
-SOURCES = ["prims.cu", "graph.cu", "traverse.cu", "batch.cu", "query.cu", "capi.cu", "server.cu", "adaptive.cu"]
+SOURCES = ["prims.cu", "graph.cu", "traverse.cu", "batch.cu", "recsort.cu", "query.cu", "capi.cu", "server.cu", "adaptive.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

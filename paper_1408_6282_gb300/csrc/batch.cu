@@ -82,8 +82,13 @@ __global__ void k_run_list(const uint64_t *rec_key, uint64_t R, uint32_t tbits, 
     }
 }
 
+// starts: run q covers records [starts[q], starts[q+1]); its length is read
+// from *nruns_p, or is nruns when nruns_p is null (node offsets, where run v is
+// node v's possibly empty segment).
+template <class Off>
 __global__ void k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *__restrict__ rec_val,
-                         const uint32_t *__restrict__ starts, const uint64_t *__restrict__ nruns_p, uint32_t tbits,
+                         const Off *__restrict__ starts, const uint64_t *__restrict__ nruns_p, uint64_t nruns_fixed,
+                         uint32_t tbits,
                          const uint64_t *__restrict__ hvals, const uint8_t *__restrict__ lane_inst,
                          const uint64_t *__restrict__ lane_rank, uint32_t l, uint32_t k, uint8_t *__restrict__ lcnt,
                          uint64_t *__restrict__ full, uint64_t *__restrict__ X, uint32_t *__restrict__ xlen,
@@ -91,7 +96,7 @@ __global__ void k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *_
     __shared__ uint32_t need_s[8][64], seen_s[8][64];
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *need = need_s[wib], *seen = seen_s[wib];
-    const uint64_t nruns = *nruns_p;
+    const uint64_t nruns = nruns_p ? *nruns_p : nruns_fixed;
     const uint64_t tmask = (1ull << tbits) - 1;
     unsigned long long ins = 0;
     const uint64_t warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -99,8 +104,8 @@ __global__ void k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *_
         const uint64_t q = w * 32 + lane;
         uint32_t r0 = 0, r1 = 0;
         if (q < nruns) {
-            r0 = starts[q];
-            r1 = starts[q + 1];
+            r0 = static_cast<uint32_t>(starts[q]);
+            r1 = static_cast<uint32_t>(starts[q + 1]);
         }
         const bool longrun = r1 - r0 > kLongRun;
         // short runs: one lane each
@@ -391,8 +396,18 @@ cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint
     note_launch();
     k_run_list<<<grid_for(R + 1, 256), 256, 0, s>>>(rec_key, R, tbits, flag, starts);
     note_launch();
-    k_accept<<<grid_for((R + 31) / 32 * 32, 256), 256, 0, s>>>(rec_key, rec_val, starts, flag + R, tbits, hvals,
+    k_accept<<<grid_for((R + 31) / 32 * 32, 256), 256, 0, s>>>(rec_key, rec_val, starts, flag + R, 0, tbits, hvals,
                                                                lane_inst, lane_rank, l, k, lcnt, full, X, xlen, ctl);
+    return cudaGetLastError();
+}
+cudaError_t launch_accept_nodes(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                                const uint64_t *noff, uint32_t n, const uint64_t *hvals, const uint8_t *lane_inst,
+                                const uint64_t *lane_rank, uint32_t l, uint32_t k, uint8_t *lcnt, uint64_t *full,
+                                uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    note_launch();
+    k_accept<<<grid_for((static_cast<size_t>(n) + 31) / 32 * 32, 256), 256, 0, s>>>(
+        rec_key, rec_val, noff, nullptr, n, tbits, hvals, lane_inst, lane_rank, l, k, lcnt, full, X, xlen, ctl);
     return cudaGetLastError();
 }
 cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s) {

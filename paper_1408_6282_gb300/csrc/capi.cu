@@ -64,6 +64,12 @@ struct skim_ctx {
     uint64_t *rkey = nullptr, *rkey2 = nullptr;
     uint32_t *rval = nullptr, *rval2 = nullptr;
     uint64_t rcap = 0;
+    // per-node placement of a batch's records (recsort.cu): counters (all
+    // zero between batches), node offsets, node lists
+    uint64_t *ncnt = nullptr, *noff = nullptr;
+    uint32_t *nlist = nullptr;
+    unsigned *nlist_cnt = nullptr;
+    bool bnode = false;  // the active batch's records were placed per node
     void *ws = nullptr;
     size_t ws_bytes = 0;
     uint8_t *lane_inst = nullptr;
@@ -309,6 +315,17 @@ int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out) {
     }
 }
 
+// A batch's records are placed node by node when there are at least n / 4
+// of them; below that the pass over the n node counters costs more than a
+// radix sort of the records.
+constexpr uint64_t kNodeSortDensity = 4;
+
+#ifndef SKIM_TABLE_SLOTS
+#define SKIM_TABLE_SLOTS 8
+#endif
+// visited-table slots per expected visit record of a batch
+constexpr double kTableSlots = SKIM_TABLE_SLOTS;
+
 // Reverse search of the batch of ranks [p0, p0+B).  mode_build: Algorithm 2
 // (pruned by local counts); otherwise SKIM (covered sources skipped).
 // est_per_lane: expected visit records per lane (0 = unknown).  The visited
@@ -332,7 +349,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     a.hgen = c->gen << kGenShift;
     if (est_per_lane > 0) {
         const uint64_t want = pow2_at_least(std::max<uint64_t>(
-            1ull << 16, static_cast<uint64_t>(8.0 * est_per_lane * static_cast<double>(B))));
+            1ull << 16, static_cast<uint64_t>(kTableSlots * est_per_lane * static_cast<double>(B))));
         a.hmask = std::min(want, c->hcap) - 1;
     }
     // IC-model searches are never pruned: every lane is its own instance
@@ -355,9 +372,23 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     }
     RC(reset_queue(c, h.q_tail.v));
     const int bits = bitlen(c->n - 1) + static_cast<int>(tbits);
+    // records dense over the nodes: place them node by node (one pass over
+    // the n node counters); sparse: radix sort over the key bits
+    c->bnode = static_cast<uint64_t>(c->n) <= kNodeSortDensity * R;
+    if (c->bnode && !c->ncnt) {
+        RC(dalloc(c, &c->ncnt, static_cast<size_t>(c->n) + 1));
+        RC(dalloc(c, &c->noff, static_cast<size_t>(c->n) + 1));
+        RC(dalloc(c, &c->nlist, c->n));
+        RC(dalloc(c, &c->nlist_cnt, 2));
+        CK(c, cudaMemsetAsync(c->ncnt, 0, (static_cast<size_t>(c->n) + 1) * sizeof(uint64_t), c->st));
+    }
     {
         KTimer kt(c, SKIM_K_SORT);
-        CK(c, radix_sort_pairs(c->rkey, c->rval, c->rkey2, c->rval2, R, bits, c->ws, c->st));
+        if (c->bnode)
+            CK(c, launch_node_sort(c->rkey, c->rval, R, tbits, c->n, c->ncnt, c->noff, c->rkey2, c->nlist,
+                                   c->nlist_cnt, c->ws, c->st));
+        else
+            CK(c, radix_sort_pairs(c->rkey, c->rval, c->rkey2, c->rval2, R, bits, c->ws, c->st));
     }
     c->bR = R;
     c->btbits = tbits;
@@ -369,6 +400,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
 // next batch's keys carry a new generation.
 int clear_batch(skim_ctx *c) {
     c->bR = 0;
+    c->bnode = false;
     return SKIM_OK;
 }
 
@@ -712,6 +744,7 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->q); dfree(c->hkeys); dfree(c->pend);
     c->hvals = nullptr;
     dfree(c->rkey); dfree(c->rkey2); dfree(c->rval); dfree(c->rval2);
+    dfree(c->ncnt); dfree(c->noff); dfree(c->nlist); dfree(c->nlist_cnt);
     if (c->ws) cudaFree(c->ws);
     dfree(c->lane_inst); dfree(c->lane_g); dfree(c->alive); dfree(c->lane_cnt); dfree(c->lane_off); dfree(c->lane_fill);
     dfree(c->lcnt); dfree(c->full); dfree(c->X); dfree(c->xlen);
@@ -1119,8 +1152,13 @@ int skim_build_sketches(skim_ctx *c) {
         {
             KTimer kt(c, SKIM_K_ACCEPT);
             // run scratch: the sort's alternate buffers are free after the sort
-            CK(c, launch_accept(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->lane_inst, c->srank + p0, c->l,
-                                c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl, c->rkey2, c->rval2, c->ws, c->st));
+            if (c->bnode)
+                CK(c, launch_accept_nodes(c->rkey, c->rval, c->bR, c->btbits, c->noff, c->n, c->hvals, c->lane_inst,
+                                          c->srank + p0, c->l, c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl, c->st));
+            else
+                CK(c, launch_accept(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->lane_inst, c->srank + p0, c->l,
+                                    c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl, c->rkey2, c->rval2, c->ws,
+                                    c->st));
         }
         const uint64_t recs = c->bR;
         RC(clear_batch(c));

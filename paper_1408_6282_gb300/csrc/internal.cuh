@@ -145,7 +145,19 @@ cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint
                           const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
                           uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
                           uint64_t *flag, uint32_t *starts, void *scan_ws, cudaStream_t s);
+// Acceptance over the node offsets of launch_node_sort (run v = node v).
+cudaError_t launch_accept_nodes(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
+                                const uint64_t *noff, uint32_t n, const uint64_t *hvals, const uint8_t *lane_inst,
+                                const uint64_t *lane_rank, uint32_t l, uint32_t k, uint8_t *lcnt, uint64_t *full,
+                                uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s);
 cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s);
+
+// recsort.cu: order a batch's R records by key, node by node.  cnt: n + 1
+// counters, all zero on entry and on return; off: n + 1 node offsets (out);
+// tmp: R scratch words; list: n scratch entries; nlist: 2 scratch counters.
+cudaError_t launch_node_sort(uint64_t *rec_key, uint32_t *rec_val, uint64_t R, uint32_t tbits, uint32_t n,
+                             uint64_t *cnt, uint64_t *off, uint64_t *tmp, uint32_t *list, unsigned *nlist,
+                             void *scan_ws, cudaStream_t s);
 cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                               const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
                               uint32_t k, DevCtl *ctl, cudaStream_t s);
