@@ -51,112 +51,95 @@ SKIM_DEV bool run_start(const uint64_t *rec_key, uint64_t r, uint32_t tbits) {
 }
 
 // Algorithm 2's acceptance for the records of one batch, sorted by key so that
-// a node's records are adjacent and in lane = rank order.  Per (node v,
+// a node's records are adjacent and in word (= rank) order.  Per (node v,
 // instance i) the first k - lcnt[v,i] offers are accepted (the instance-local
 // sketch), and accepted ranks are appended to X_v while it holds fewer than k.
 //
-// The runs (one per node) are listed in order first (run_flags, a scan,
-// run_list); then each lane of a warp takes one run: runs of up to kLongRun
-// records are walked by their lane, longer ones by the whole warp, 32
-// records at a time.
+// Records are split into windows of 32; a warp owns the nodes whose runs start
+// in its window and walks their records 32 at a time, past the window's end
+// for the last one.  The offers (record, lane bit) are taken 32 per step in
+// rank order.  An offer of (v, i) with rank rho among the step's offers of
+// (v, i) is accepted iff lcnt[v,i] + rho < k, which is the sequential rule;
+// its place in X_v is xlen[v] plus the accepted offers of v before it in the
+// step.  Counts, lengths and full bits are written back after every step, so
+// the next step reads them current.
 
-#ifndef SKIM_LONG_RUN
-#define SKIM_LONG_RUN 8
-#endif
-constexpr uint32_t kLongRun = SKIM_LONG_RUN;
-
-__global__ void k_run_flags(const uint64_t *rec_key, uint64_t R, uint32_t tbits, uint64_t *flag) {
-    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r <= R;
-         r += static_cast<uint64_t>(gridDim.x) * blockDim.x)
-        flag[r] = r < R && run_start(rec_key, r, tbits) ? 1 : 0;
-}
-
-// starts[q] = first record of run q (flag holds the exclusive scan of the
-// run-start flags); starts[runs] = R
-__global__ void k_run_list(const uint64_t *rec_key, uint64_t R, uint32_t tbits, const uint64_t *flag,
-                           uint32_t *starts) {
-    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r <= R;
-         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        if (r == R) starts[flag[R]] = static_cast<uint32_t>(R);
-        else if (run_start(rec_key, r, tbits)) starts[flag[r]] = static_cast<uint32_t>(r);
+// One step: offer `has` of node v at batch lane ln (one per warp lane).
+SKIM_DEV void accept_step(bool has, uint32_t v, uint64_t ln, const uint8_t *__restrict__ lane_inst,
+                          const uint64_t *__restrict__ lane_rank, uint32_t l, uint32_t k, uint8_t *lcnt,
+                          uint64_t *full, uint64_t *X, uint32_t *xlen, unsigned long long &ins) {
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t i = 0, lc0 = 0, len0 = 0;
+    if (has) {
+        i = lane_inst[ln];
+        lc0 = lcnt[static_cast<uint64_t>(v) * l + i];
+        len0 = xlen[v];
     }
+    // peers in (v, i) and in v; idle lanes get keys no offer has
+    const unsigned pvi = __match_any_sync(kFull, has ? (static_cast<uint64_t>(v) << 6 | i) : ~0ull - lane);
+    const unsigned pv = __match_any_sync(kFull, has ? static_cast<uint64_t>(v) : (1ull << 32 | lane));
+    const uint32_t rho = __popc(pvi & lanemask_lt());
+    const bool acc = has && lc0 + rho < k;
+    const unsigned ab = __ballot_sync(kFull, acc);
+    if (acc) {
+        const uint32_t pos = len0 + __popc(ab & pv & lanemask_lt());
+        if (pos < k) X[static_cast<uint64_t>(v) * k + pos] = lane_rank[ln];
+        ins++;
+    }
+    __syncwarp();
+    if (has && rho == 0 && lc0 < k) {  // one lane per (v, i)
+        const uint32_t c = min(k, lc0 + __popc(pvi));
+        lcnt[static_cast<uint64_t>(v) * l + i] = static_cast<uint8_t>(c);
+        if (c == k) atomicOr(reinterpret_cast<unsigned long long *>(&full[v]), 1ull << i);
+    }
+    if (has && (pv & lanemask_lt()) == 0) {  // one lane per v
+        const uint32_t len = min(k, len0 + __popc(ab & pv));
+        if (len != len0) xlen[v] = len;
+    }
+    __syncwarp();
 }
 
-// starts: run q covers records [starts[q], starts[q+1]); its length is read
-// from *nruns_p, or is nruns when nruns_p is null (node offsets, where run v is
-// node v's possibly empty segment).
-template <class Off>
-__global__ void k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *__restrict__ rec_val,
-                         const Off *__restrict__ starts, const uint64_t *__restrict__ nruns_p, uint64_t nruns_fixed,
-                         uint32_t tbits,
-                         const uint64_t *__restrict__ hvals, const uint8_t *__restrict__ lane_inst,
-                         const uint64_t *__restrict__ lane_rank, uint32_t l, uint32_t k, uint8_t *__restrict__ lcnt,
-                         uint64_t *__restrict__ full, uint64_t *__restrict__ X, uint32_t *__restrict__ xlen,
-                         DevCtl *ctl) {
-    __shared__ uint32_t need_s[8][64], seen_s[8][64];
-    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *need = need_s[wib], *seen = seen_s[wib];
-    const uint64_t nruns = nruns_p ? *nruns_p : nruns_fixed;
+// rec_mask: the records' lane bits in record order, or null to read them from
+// the table slots hvals[2 * rec_val[r]].
+__global__ void __launch_bounds__(256)
+    k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *__restrict__ rec_val,
+             const uint64_t *__restrict__ rec_mask, const uint64_t *__restrict__ hvals, uint64_t R, uint32_t tbits,
+             const uint8_t *__restrict__ lane_inst, const uint64_t *__restrict__ lane_rank, uint32_t l, uint32_t k,
+             uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl) {
+    const uint32_t lane = threadIdx.x & 31;
     const uint64_t tmask = (1ull << tbits) - 1;
     unsigned long long ins = 0;
     const uint64_t warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (uint64_t w = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5; w * 32 < nruns; w += warps) {
-        const uint64_t q = w * 32 + lane;
-        uint32_t r0 = 0, r1 = 0;
-        if (q < nruns) {
-            r0 = static_cast<uint32_t>(starts[q]);
-            r1 = static_cast<uint32_t>(starts[q + 1]);
-        }
-        const bool longrun = r1 - r0 > kLongRun;
-        // short runs: one lane each
-        if (r1 > r0 && !longrun) {
-            const uint64_t v = rec_key[r0] >> tbits;
-            uint8_t *lc = lcnt + v * l;
-            uint64_t *xv = X + v * k;
-            uint32_t len = xlen[v];
-            uint64_t newfull = 0;
-            for (uint32_t rr = r0; rr < r1; rr++) {
-                const uint64_t t = rec_key[rr] & tmask;
-                uint64_t m = hvals[2ull * rec_val[rr]];
-                while (m) {
-                    const int j = __ffsll(m) - 1;
-                    m &= m - 1;
-                    const uint64_t ln = t * 64 + j;
-                    const uint32_t i = lane_inst[ln];
-                    const uint32_t c = lc[i];
-                    if (c < k) {
-                        lc[i] = static_cast<uint8_t>(c + 1);
-                        ins++;
-                        if (c + 1 == k) newfull |= 1ull << i;
-                        if (len < k) xv[len++] = lane_rank[ln];
-                    }
-                }
+    const uint64_t nwin = (R + 31) / 32;
+    for (uint64_t w = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5; w < nwin; w += warps) {
+        const uint64_t W0 = w * 32, W1 = min(R, W0 + 32);
+        bool st = false;
+        if (W0 + lane < W1) st = run_start(rec_key, W0 + lane, tbits);
+        const unsigned sb = __ballot_sync(kFull, st);
+        if (!sb) continue;  // the window lies inside a run owned by an earlier warp
+        const uint64_t s0 = W0 + __ffs(sb) - 1;
+        const uint64_t last = rec_key[W1 - 1] >> tbits;
+        for (uint64_t c0 = s0;; c0 += 32) {
+            // the warp's records form one stretch [s0, end of last's run)
+            const uint64_t rr = c0 + lane;
+            uint64_t key = 0, m = 0;
+            bool act = false;
+            if (rr < R) {
+                key = rec_key[rr];
+                act = rr < W1 || (key >> tbits) == last;
             }
-            xlen[v] = len;
-            if (newfull) full[v] |= newfull;
-        }
-        // long runs: the whole warp, one after another
-        for (unsigned lb = __ballot_sync(kFull, longrun); lb; lb &= lb - 1) {
-            const int src = __ffs(lb) - 1;
-            const uint32_t a0 = __shfl_sync(kFull, r0, src), a1 = __shfl_sync(kFull, r1, src);
-            const uint64_t v = rec_key[a0] >> tbits;
-            uint8_t *lc = lcnt + v * l;
-            uint64_t *xv = X + v * k;
-            for (uint32_t i = lane; i < 64; i += 32) {
-                need[i] = i < l ? k - lc[i] : 0;
-                seen[i] = 0;
-            }
-            uint32_t len = xlen[v];
-            __syncwarp();
-            for (uint32_t c0 = a0; c0 < a1; c0 += 32) {
-                const uint32_t rr = c0 + lane;
-                uint64_t m = 0, t = 0;
-                if (rr < a1) {
-                    m = hvals[2ull * rec_val[rr]];
-                    t = rec_key[rr] & tmask;
-                }
-                // the chunk's offers in lane (= rank) order, 32 at a time: offer o
-                // is bit (o - pre_s) of the record s with pre_s <= o < pre_s + cnt_s
+            const unsigned actb = __ballot_sync(kFull, act);
+            if (!actb) break;
+            if (act) m = rec_mask ? rec_mask[rr] : hvals[2ull * rec_val[rr]];
+            const uint32_t vr = static_cast<uint32_t>(key >> tbits);
+            const uint64_t tr = key & tmask;
+            if (!__any_sync(kFull, __popcll(m) > 1)) {
+                // one offer per record (the common case)
+                const bool has = m != 0;
+                accept_step(has, vr, tr * 64 + (has ? __ffsll(m) - 1 : 0), lane_inst, lane_rank, l, k, lcnt, full, X,
+                            xlen, ins);
+            } else {
+                // offer o is bit (o - pre_s) of record s with pre_s <= o < pre_s + cnt_s
                 const uint32_t cnt = __popcll(m);
                 uint32_t incl = cnt;
 #pragma unroll
@@ -175,49 +158,18 @@ __global__ void k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *_
                         const uint32_t pc = __shfl_sync(kFull, pre, cand);
                         if (has && pc <= o) src = cand;
                     }
-                    const uint64_t ms = __shfl_sync(kFull, m, src), ts = __shfl_sync(kFull, t, src);
-                    const uint32_t ps = __shfl_sync(kFull, pre, src);
+                    const uint64_t ms = __shfl_sync(kFull, m, src), ts = __shfl_sync(kFull, tr, src);
+                    const uint32_t ps = __shfl_sync(kFull, pre, src), vs = __shfl_sync(kFull, vr, src);
                     uint64_t ln = 0;
-                    uint32_t i = 0;
                     if (has) {
                         uint64_t x = ms;
                         for (uint32_t skip = o - ps; skip; skip--) x &= x - 1;
                         ln = ts * 64 + (__ffsll(x) - 1);
-                        i = lane_inst[ln];
                     }
-                    // rank among the group's offers of the same instance
-                    const unsigned grp = __match_any_sync(kFull, has ? i : 64 + lane);
-                    const uint32_t before = __popc(grp & lanemask_lt());
-                    const bool acc = has && seen[i] + before < need[i];
-                    const unsigned ab = __ballot_sync(kFull, acc);
-                    if (acc) {
-                        const uint32_t pos = len + __popc(ab & lanemask_lt());
-                        if (pos < k) xv[pos] = lane_rank[ln];
-                        ins++;
-                    }
-                    len = min(k, len + __popc(ab));
-                    __syncwarp();
-                    if (has && before == 0) seen[i] += __popc(grp);  // one lane per instance group
-                    __syncwarp();
+                    accept_step(has, vs, ln, lane_inst, lane_rank, l, k, lcnt, full, X, xlen, ins);
                 }
             }
-            // local counts and full instances
-            uint64_t nf = 0;
-            for (uint32_t i = lane; i < l; i += 32) {
-                const uint32_t add = min(seen[i], need[i]);
-                if (add) {
-                    lc[i] = static_cast<uint8_t>(k - need[i] + add);
-                    if (add == need[i]) nf |= 1ull << i;
-                }
-            }
-            nf |= __shfl_xor_sync(kFull, nf, 16);
-#pragma unroll
-            for (int o = 8; o > 0; o >>= 1) nf |= __shfl_xor_sync(kFull, nf, o);
-            if (lane == 0) {
-                xlen[v] = len;
-                if (nf) full[v] |= nf;
-            }
-            __syncwarp();
+            if (actb != kFull) break;
         }
     }
     warp_add(&ctl->stats[kStInsert], ins);
@@ -384,30 +336,14 @@ cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_ran
     k_lane_inst<<<grid_for(B, 256), 256, 0, s>>>(lane_pair, lane_rank, B, l, lane_inst, lane_g);
     return cudaGetLastError();
 }
-cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                          const uint64_t *hvals, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l,
-                          uint32_t k, uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
-                          uint64_t *flag, uint32_t *starts, void *scan_ws, cudaStream_t s) {
+cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, const uint64_t *rec_mask,
+                          const uint64_t *hvals, uint64_t R, uint32_t tbits, const uint8_t *lane_inst,
+                          const uint64_t *lane_rank, uint32_t l, uint32_t k, uint8_t *lcnt, uint64_t *full,
+                          uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
     note_launch();
-    k_run_flags<<<grid_for(R + 1, 256), 256, 0, s>>>(rec_key, R, tbits, flag);
-    cudaError_t e = exclusive_scan_u64(flag, flag, R + 1, nullptr, scan_ws, s);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    k_run_list<<<grid_for(R + 1, 256), 256, 0, s>>>(rec_key, R, tbits, flag, starts);
-    note_launch();
-    k_accept<<<grid_for((R + 31) / 32 * 32, 256), 256, 0, s>>>(rec_key, rec_val, starts, flag + R, 0, tbits, hvals,
-                                                               lane_inst, lane_rank, l, k, lcnt, full, X, xlen, ctl);
-    return cudaGetLastError();
-}
-cudaError_t launch_accept_nodes(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                                const uint64_t *noff, uint32_t n, const uint64_t *hvals, const uint8_t *lane_inst,
-                                const uint64_t *lane_rank, uint32_t l, uint32_t k, uint8_t *lcnt, uint64_t *full,
-                                uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s) {
-    if (R == 0) return cudaSuccess;
-    note_launch();
-    k_accept<<<grid_for((static_cast<size_t>(n) + 31) / 32 * 32, 256), 256, 0, s>>>(
-        rec_key, rec_val, noff, nullptr, n, tbits, hvals, lane_inst, lane_rank, l, k, lcnt, full, X, xlen, ctl);
+    k_accept<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, rec_mask, hvals, R, tbits, lane_inst, lane_rank, l, k,
+                                               lcnt, full, X, xlen, ctl);
     return cudaGetLastError();
 }
 cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s) {

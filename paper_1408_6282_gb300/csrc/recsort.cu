@@ -18,7 +18,9 @@
 //           the 2^tbits words (any s).
 //
 // The result is the same array a full sort gives (keys are distinct), and the
-// node offsets double as the acceptance's run list.
+// node offsets double as the acceptance's run list.  For the acceptance the
+// ordering also copies each record's lane bits out of the visited table next
+// to the record.
 #include "internal.cuh"
 #include "prims.cuh"
 
@@ -60,9 +62,21 @@ __global__ void k_node_scatter(const uint64_t *__restrict__ rec_key, const uint3
     }
 }
 
-SKIM_DEV void put(uint64_t *rec_key, uint32_t *rec_val, uint64_t at, uint64_t vhi, uint64_t p) {
-    rec_key[at] = vhi | (p >> 32);
-    rec_val[at] = static_cast<uint32_t>(p);
+// Outputs of the ordering: key and slot of each record, and (when rec_mask
+// is given) the record's lane bits read from its table slot, so that the
+// acceptance reads them in order instead of one random slot at a time.
+struct OrderOut {
+    uint64_t *rec_key;
+    uint32_t *rec_val;
+    const uint64_t *hvals;
+    uint64_t *rec_mask;
+};
+
+SKIM_DEV void put(const OrderOut &o, uint64_t at, uint64_t vhi, uint64_t p) {
+    const uint32_t slot = static_cast<uint32_t>(p);
+    o.rec_key[at] = vhi | (p >> 32);
+    o.rec_val[at] = slot;
+    if (o.rec_mask) o.rec_mask[at] = o.hvals[2ull * slot];
 }
 
 SKIM_DEV void cswap(uint64_t &a, uint64_t &b) {
@@ -75,8 +89,7 @@ SKIM_DEV void cswap(uint64_t &a, uint64_t &b) {
 // registers (odd-even transposition network, padded with all-ones keys);
 // longer ones are listed for the warp (front of `list`) or block (back) pass.
 __global__ void k_node_order(const uint64_t *__restrict__ tmp, const uint64_t *__restrict__ off, uint32_t n,
-                             uint32_t tbits, uint64_t *__restrict__ rec_key, uint32_t *__restrict__ rec_val,
-                             uint32_t *list, unsigned *nlist) {
+                             uint32_t tbits, OrderOut o, uint32_t *list, unsigned *nlist) {
     const uint32_t lane = threadIdx.x & 31;
     for (uint64_t base = blockIdx.x * static_cast<uint64_t>(blockDim.x); base < n;
          base += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
@@ -98,7 +111,7 @@ __global__ void k_node_order(const uint64_t *__restrict__ tmp, const uint64_t *_
             const uint64_t vhi = v << tbits;
 #pragma unroll
             for (uint32_t i = 0; i < kThreadSeg; i++)
-                if (i < s) put(rec_key, rec_val, b0 + i, vhi, a[i]);
+                if (i < s) put(o, b0 + i, vhi, a[i]);
         }
         // warp-aggregated appends to the two lists
         const bool mid = s > kThreadSeg && s <= kWarpSeg, big = s > kWarpSeg;
@@ -119,7 +132,7 @@ __global__ void k_node_order(const uint64_t *__restrict__ tmp, const uint64_t *_
 // network across the 32 lanes, padded with all-ones keys.
 __global__ void k_node_order_warp(const uint64_t *__restrict__ tmp, const uint64_t *__restrict__ off,
                                   const uint32_t *__restrict__ list, const unsigned *__restrict__ nlist,
-                                  uint32_t tbits, uint64_t *__restrict__ rec_key, uint32_t *__restrict__ rec_val) {
+                                  uint32_t tbits, OrderOut o) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t cnt = nlist[0];
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -136,7 +149,7 @@ __global__ void k_node_order_warp(const uint64_t *__restrict__ tmp, const uint64
                 x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
             }
         }
-        if (lane < s) put(rec_key, rec_val, b0 + lane, v << tbits, x);
+        if (lane < s) put(o, b0 + lane, v << tbits, x);
     }
 }
 
@@ -146,7 +159,7 @@ __global__ void k_node_order_warp(const uint64_t *__restrict__ tmp, const uint64
 __global__ void __launch_bounds__(kBigThreads)
     k_node_order_block(const uint64_t *__restrict__ tmp, const uint64_t *__restrict__ off,
                        const uint32_t *__restrict__ list, const unsigned *__restrict__ nlist, uint32_t n,
-                       uint32_t tbits, uint64_t *__restrict__ rec_key, uint32_t *__restrict__ rec_val) {
+                       uint32_t tbits, OrderOut o) {
     extern __shared__ uint32_t sm[];
     __shared__ uint32_t wsum[kBigThreads / 32];
     const uint32_t words = tbits > 5 ? 1u << (tbits - 5) : 1u;
@@ -188,7 +201,7 @@ __global__ void __launch_bounds__(kBigThreads)
             const uint64_t p = tmp[b0 + i];
             const uint32_t t = static_cast<uint32_t>(p >> 32);
             const uint32_t pos = pre[t >> 5] + __popc(bm[t >> 5] & ((1u << (t & 31)) - 1));
-            put(rec_key, rec_val, b0 + pos, vhi, p);
+            put(o, b0 + pos, vhi, p);
         }
         __syncthreads();
     }
@@ -202,8 +215,9 @@ inline size_t block_smem(uint32_t tbits) {
 }  // namespace
 
 cudaError_t launch_node_sort(uint64_t *rec_key, uint32_t *rec_val, uint64_t R, uint32_t tbits, uint32_t n,
-                             uint64_t *cnt, uint64_t *off, uint64_t *tmp, uint32_t *list, unsigned *nlist,
-                             void *scan_ws, cudaStream_t s) {
+                             const uint64_t *hvals, uint64_t *rec_mask, uint64_t *cnt, uint64_t *off, uint64_t *tmp,
+                             uint32_t *list, unsigned *nlist, void *scan_ws, cudaStream_t s) {
+    const OrderOut o{rec_key, rec_val, hvals, rec_mask};
     // empty batch: off must still read all zeros for the acceptance
     cudaError_t e = cudaMemsetAsync(nlist, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
@@ -218,9 +232,9 @@ cudaError_t launch_node_sort(uint64_t *rec_key, uint32_t *rec_val, uint64_t R, u
     k_node_scatter<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, off,
                                                     reinterpret_cast<unsigned long long *>(cnt), tmp);
     note_launch();
-    k_node_order<<<grid_for(n, 256), 256, 0, s>>>(tmp, off, n, tbits, rec_key, rec_val, list, nlist);
+    k_node_order<<<grid_for(n, 256), 256, 0, s>>>(tmp, off, n, tbits, o, list, nlist);
     note_launch();
-    k_node_order_warp<<<152 * 4, 256, 0, s>>>(tmp, off, list, nlist, tbits, rec_key, rec_val);
+    k_node_order_warp<<<152 * 4, 256, 0, s>>>(tmp, off, list, nlist, tbits, o);
     const size_t smem = block_smem(tbits);
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k_node_order_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -228,7 +242,7 @@ cudaError_t launch_node_sort(uint64_t *rec_key, uint32_t *rec_val, uint64_t R, u
         if (e != cudaSuccess) return e;
     }
     note_launch();
-    k_node_order_block<<<SKIM_BIG_BLOCKS, kBigThreads, smem, s>>>(tmp, off, list, nlist, n, tbits, rec_key, rec_val);
+    k_node_order_block<<<SKIM_BIG_BLOCKS, kBigThreads, smem, s>>>(tmp, off, list, nlist, n, tbits, o);
     return cudaGetLastError();
 }
 
