@@ -99,11 +99,10 @@ SKIM_DEV void accept_step(bool has, uint32_t v, uint64_t ln, const uint8_t *__re
     __syncwarp();
 }
 
-// rec_mask: the records' lane bits in record order, or null to read them from
-// the table slots hvals[2 * rec_val[r]].
+// Record r's lane bits are those of its table slot, hvals[2 * rec_val[r]].
 __global__ void __launch_bounds__(256)
     k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *__restrict__ rec_val,
-             const uint64_t *__restrict__ rec_mask, const uint64_t *__restrict__ hvals, uint64_t R, uint32_t tbits,
+             const uint64_t *__restrict__ hvals, uint64_t R, uint32_t tbits,
              const uint8_t *__restrict__ lane_inst, const uint64_t *__restrict__ lane_rank, uint32_t l, uint32_t k,
              uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl) {
     const uint32_t lane = threadIdx.x & 31;
@@ -130,7 +129,7 @@ __global__ void __launch_bounds__(256)
             }
             const unsigned actb = __ballot_sync(kFull, act);
             if (!actb) break;
-            if (act) m = rec_mask ? rec_mask[rr] : hvals[2ull * rec_val[rr]];
+            if (act) m = hvals[2ull * rec_val[rr]];
             const uint32_t vr = static_cast<uint32_t>(key >> tbits);
             const uint64_t tr = key & tmask;
             if (!__any_sync(kFull, __popcll(m) > 1)) {
@@ -336,13 +335,12 @@ cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_ran
     k_lane_inst<<<grid_for(B, 256), 256, 0, s>>>(lane_pair, lane_rank, B, l, lane_inst, lane_g);
     return cudaGetLastError();
 }
-cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, const uint64_t *rec_mask,
-                          const uint64_t *hvals, uint64_t R, uint32_t tbits, const uint8_t *lane_inst,
-                          const uint64_t *lane_rank, uint32_t l, uint32_t k, uint8_t *lcnt, uint64_t *full,
-                          uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s) {
+cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, const uint64_t *hvals, uint64_t R,
+                          uint32_t tbits, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l, uint32_t k,
+                          uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
     note_launch();
-    k_accept<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, rec_mask, hvals, R, tbits, lane_inst, lane_rank, l, k,
+    k_accept<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, hvals, R, tbits, lane_inst, lane_rank, l, k,
                                                lcnt, full, X, xlen, ctl);
     return cudaGetLastError();
 }

@@ -65,9 +65,8 @@ struct skim_ctx {
     uint32_t *rval = nullptr, *rval2 = nullptr;
     uint64_t rcap = 0;
     // per-node placement of a batch's records (recsort.cu): counters (all
-    // zero between batches), node offsets, the records' lane bits (build), node
-    // lists
-    uint64_t *ncnt = nullptr, *noff = nullptr, *nmask = nullptr;
+    // zero between batches), node offsets, node lists
+    uint64_t *ncnt = nullptr, *noff = nullptr;
     uint32_t *nlist = nullptr;
     unsigned *nlist_cnt = nullptr;
     bool bnode = false;  // the active batch's records were placed per node
@@ -381,14 +380,13 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         RC(dalloc(c, &c->noff, static_cast<size_t>(c->n) + 1));
         RC(dalloc(c, &c->nlist, c->n));
         RC(dalloc(c, &c->nlist_cnt, 2));
-        RC(dalloc(c, &c->nmask, c->rcap));
         CK(c, cudaMemsetAsync(c->ncnt, 0, (static_cast<size_t>(c->n) + 1) * sizeof(uint64_t), c->st));
     }
     {
         KTimer kt(c, SKIM_K_SORT);
         if (c->bnode)
-            CK(c, launch_node_sort(c->rkey, c->rval, R, tbits, c->n, c->hvals, mode_build ? c->nmask : nullptr,
-                                   c->ncnt, c->noff, c->rkey2, c->nlist, c->nlist_cnt, c->ws, c->st));
+            CK(c, launch_node_sort(c->rkey, c->rval, R, tbits, c->n, c->ncnt, c->noff, c->rkey2, c->nlist,
+                                   c->nlist_cnt, c->ws, c->st));
         else
             CK(c, radix_sort_pairs(c->rkey, c->rval, c->rkey2, c->rval2, R, bits, c->ws, c->st));
     }
@@ -746,7 +744,7 @@ int skim_destroy(skim_ctx *c) {
     dfree(c->q); dfree(c->hkeys); dfree(c->pend);
     c->hvals = nullptr;
     dfree(c->rkey); dfree(c->rkey2); dfree(c->rval); dfree(c->rval2);
-    dfree(c->ncnt); dfree(c->noff); dfree(c->nmask); dfree(c->nlist); dfree(c->nlist_cnt);
+    dfree(c->ncnt); dfree(c->noff); dfree(c->nlist); dfree(c->nlist_cnt);
     if (c->ws) cudaFree(c->ws);
     dfree(c->lane_inst); dfree(c->lane_g); dfree(c->alive); dfree(c->lane_cnt); dfree(c->lane_off); dfree(c->lane_fill);
     dfree(c->lcnt); dfree(c->full); dfree(c->X); dfree(c->xlen);
@@ -1153,9 +1151,8 @@ int skim_build_sketches(skim_ctx *c) {
         }
         {
             KTimer kt(c, SKIM_K_ACCEPT);
-            CK(c, launch_accept(c->rkey, c->rval, c->bnode ? c->nmask : nullptr, c->hvals, c->bR, c->btbits,
-                                c->lane_inst, c->srank + p0, c->l, c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl,
-                                c->st));
+            CK(c, launch_accept(c->rkey, c->rval, c->hvals, c->bR, c->btbits, c->lane_inst, c->srank + p0, c->l,
+                                c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl, c->st));
         }
         const uint64_t recs = c->bR;
         RC(clear_batch(c));

@@ -141,22 +141,19 @@ cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_ran
                              uint8_t *lane_inst, uint64_t *lane_g, cudaStream_t s);
 // Algorithm 2 acceptance of a batch's sorted records.  flag: R + 1 uint64 and
 // starts: R + 1 uint32 of scratch; scan_ws: scan workspace for R + 1 entries.
-// Algorithm 2's acceptance of a batch's sorted records; their lane bits are
-// rec_mask[r] when given, else hvals[2 * rec_val[r]].
-cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, const uint64_t *rec_mask,
-                          const uint64_t *hvals, uint64_t R, uint32_t tbits, const uint8_t *lane_inst,
-                          const uint64_t *lane_rank, uint32_t l, uint32_t k, uint8_t *lcnt, uint64_t *full,
-                          uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s);
+// Algorithm 2's acceptance of a batch's sorted records; record r's lane bits
+// are hvals[2 * rec_val[r]].
+cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, const uint64_t *hvals, uint64_t R,
+                          uint32_t tbits, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l, uint32_t k,
+                          uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s);
 cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s);
 
-// recsort.cu: order a batch's R records by key, node by node.  rec_mask
-// (optional, R words): the lane bits hvals[2 * slot] of each ordered record.
-// cnt: n + 1 counters, all zero on entry and on return; off: n + 1 node
-// offsets (out); tmp: R scratch words; list: n scratch entries; nlist: 2
-// scratch counters.
+// recsort.cu: order a batch's R records by key, node by node.  cnt: n + 1
+// counters, all zero on entry and on return; off: n + 1 node offsets (out);
+// tmp: R scratch words; list: n scratch entries; nlist: 2 scratch counters.
 cudaError_t launch_node_sort(uint64_t *rec_key, uint32_t *rec_val, uint64_t R, uint32_t tbits, uint32_t n,
-                             const uint64_t *hvals, uint64_t *rec_mask, uint64_t *cnt, uint64_t *off, uint64_t *tmp,
-                             uint32_t *list, unsigned *nlist, void *scan_ws, cudaStream_t s);
+                             uint64_t *cnt, uint64_t *off, uint64_t *tmp, uint32_t *list, unsigned *nlist,
+                             void *scan_ws, cudaStream_t s);
 cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                               const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
                               uint32_t k, DevCtl *ctl, cudaStream_t s);

@@ -18,9 +18,7 @@
 //           the 2^tbits words (any s).
 //
 // The result is the same array a full sort gives (keys are distinct), and the
-// node offsets double as the acceptance's run list.  For the acceptance the
-// ordering also copies each record's lane bits out of the visited table next
-// to the record.
+// node offsets are left for the caller.
 #include "internal.cuh"
 #include "prims.cuh"
 
@@ -62,21 +60,15 @@ __global__ void k_node_scatter(const uint64_t *__restrict__ rec_key, const uint3
     }
 }
 
-// Outputs of the ordering: key and slot of each record, and (when rec_mask
-// is given) the record's lane bits read from its table slot, so that the
-// acceptance reads them in order instead of one random slot at a time.
+// Output of the ordering: key and table slot of each record.
 struct OrderOut {
     uint64_t *rec_key;
     uint32_t *rec_val;
-    const uint64_t *hvals;
-    uint64_t *rec_mask;
 };
 
 SKIM_DEV void put(const OrderOut &o, uint64_t at, uint64_t vhi, uint64_t p) {
-    const uint32_t slot = static_cast<uint32_t>(p);
     o.rec_key[at] = vhi | (p >> 32);
-    o.rec_val[at] = slot;
-    if (o.rec_mask) o.rec_mask[at] = o.hvals[2ull * slot];
+    o.rec_val[at] = static_cast<uint32_t>(p);
 }
 
 SKIM_DEV void cswap(uint64_t &a, uint64_t &b) {
@@ -215,9 +207,9 @@ inline size_t block_smem(uint32_t tbits) {
 }  // namespace
 
 cudaError_t launch_node_sort(uint64_t *rec_key, uint32_t *rec_val, uint64_t R, uint32_t tbits, uint32_t n,
-                             const uint64_t *hvals, uint64_t *rec_mask, uint64_t *cnt, uint64_t *off, uint64_t *tmp,
-                             uint32_t *list, unsigned *nlist, void *scan_ws, cudaStream_t s) {
-    const OrderOut o{rec_key, rec_val, hvals, rec_mask};
+                             uint64_t *cnt, uint64_t *off, uint64_t *tmp, uint32_t *list, unsigned *nlist,
+                             void *scan_ws, cudaStream_t s) {
+    const OrderOut o{rec_key, rec_val};
     // empty batch: off must still read all zeros for the acceptance
     cudaError_t e = cudaMemsetAsync(nlist, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
