@@ -300,24 +300,33 @@ SKIM_DEV void emit_rev_mat(const TravArgs &A, Acc &acc, bool act, uint32_t u, ui
     if (ni) write_row_items(A, s, b0, b1, t, j);
 }
 
+// Row bounds, index length and index start of one pair (w, i), loaded ahead
+// of time by a residual search whose item carries the single instance i.
+struct PairPre {
+    bool ok = false;
+    uint64_t b0 = 0, b1 = 0, st = 0;
+    uint32_t sl = 0;
+};
+
 // Warp-collective: queue the expansion of node w in instances `trav` and the
 // erasure of the index entries of pairs (w, i), i in `erase`.  With
 // materialised instances each instance gets row items of its own list of live
-// out-neighbours (none if it is empty).
+// out-neighbours (none if it is empty).  pre.ok: trav and erase hold at most
+// the bit of pre's instance, whose values are taken from pre.
 template <bool MAT>
-SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, uint64_t erase) {
+SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, uint64_t erase, const PairPre &pre) {
     uint32_t ni = 0;
     if (MAT) {
         for (uint64_t m = trav; m; m &= m - 1) {
             const uint64_t r = static_cast<uint64_t>(w) * A.l + (__ffsll(m) - 1);
-            ni += n_chunks(static_cast<uint32_t>(A.loff[r + 1] - A.loff[r]));
+            ni += n_chunks(static_cast<uint32_t>(pre.ok ? pre.b1 - pre.b0 : A.loff[r + 1] - A.loff[r]));
         }
     } else if (trav) {
         ni = n_chunks(A.ptr[w + 1] - A.ptr[w], trav);
     }
     for (uint64_t m = erase; m; m &= m - 1) {
         int i = __ffsll(m) - 1;
-        ni += n_chunks(A.seg_len[static_cast<uint64_t>(w) * A.l + i]);
+        ni += n_chunks(pre.ok ? pre.sl : A.seg_len[static_cast<uint64_t>(w) * A.l + i]);
     }
     if (!__any_sync(kFull, ni != 0)) return;
     unsigned long long s = reserve_slots(A, acc, ni);
@@ -331,7 +340,7 @@ SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, u
         for (uint64_t m = trav; m; m &= m - 1) {
             const int i = __ffsll(m) - 1;
             const uint64_t r = static_cast<uint64_t>(w) * A.l + i;
-            const uint64_t b0 = A.loff[r], b1 = A.loff[r + 1];
+            const uint64_t b0 = pre.ok ? pre.b0 : A.loff[r], b1 = pre.ok ? pre.b1 : A.loff[r + 1];
             write_row_items(A, s + c, b0, b1, 0, i);
             c += n_chunks(static_cast<uint32_t>(b1 - b0));
         }
@@ -342,27 +351,42 @@ SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, u
     for (uint64_t m = erase; m; m &= m - 1) {
         int i = __ffsll(m) - 1;
         uint64_t pair = static_cast<uint64_t>(w) * A.l + i;
-        uint32_t len = A.seg_len[pair];
+        uint32_t len = pre.ok ? pre.sl : A.seg_len[pair];
         if (!len) continue;
         A.seg_len[pair] = 0;  // erase index[w,i]
-        uint64_t st = A.seg_start[pair];
+        uint64_t st = pre.ok ? pre.st : A.seg_start[pair];
         uint32_t ne = n_chunks(len);
         for (uint32_t e = 0; e < ne; e++, c++) write_item(A, s + c, len, kEraseTag | e, st + 1);
     }
 }
 
 // Warp-collective: lanes with `act` reach node w in the instances of `live`
-// during a residual search.
+// during a residual search.  A materialised item carries one instance: the
+// pair's row bounds and index entries are requested together with the OR
+// that covers it (an index is erased only by the lane whose OR newly covers
+// its pair, so reading it first is safe).
 template <bool MAT>
 SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64_t live) {
     if (!__any_sync(kFull, act && live)) return;
     uint64_t nb = 0;
+    PairPre pre;
     if (act && live) {
-        uint64_t cov = *reinterpret_cast<volatile uint64_t *>(&A.covered[w]);
-        nb = live & ~cov;
-        if (nb) {
-            uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(&A.covered[w]), nb);
-            nb &= ~old;
+        if (MAT && (live & (live - 1)) == 0) {
+            const uint64_t r = static_cast<uint64_t>(w) * A.l + (__ffsll(live) - 1);
+            pre.ok = true;
+            pre.b0 = A.loff[r];
+            pre.b1 = A.loff[r + 1];
+            pre.sl = A.seg_len[r];
+            pre.st = A.seg_start[r];
+            const uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(&A.covered[w]), live);
+            nb = live & ~old;
+        } else {
+            uint64_t cov = *reinterpret_cast<volatile uint64_t *>(&A.covered[w]);
+            nb = live & ~cov;
+            if (nb) {
+                uint64_t old = atomicOr(reinterpret_cast<unsigned long long *>(&A.covered[w]), nb);
+                nb &= ~old;
+            }
         }
     }
     acc.cov += __popcll(nb);
@@ -370,9 +394,9 @@ SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64
     uint64_t erase = 0;
     for (uint64_t m = nb; m; m &= m - 1) {
         int i = __ffsll(m) - 1;
-        if (A.seg_len[static_cast<uint64_t>(w) * A.l + i]) erase |= 1ull << i;
+        if (pre.ok ? pre.sl : A.seg_len[static_cast<uint64_t>(w) * A.l + i]) erase |= 1ull << i;
     }
-    push_fwd<MAT>(A, acc, w, nb, erase);
+    push_fwd<MAT>(A, acc, w, nb, erase, pre);
 }
 
 // Process the items held by the lanes with `have`, edges (or index entries)
@@ -816,9 +840,9 @@ __global__ void k_respill_fwd(TravArgs A, uint32_t n) {
         }
         Acc acc;
         if (A.mat)
-            push_fwd<true>(A, acc, v < n ? v : 0, pt, pe);
+            push_fwd<true>(A, acc, v < n ? v : 0, pt, pe, PairPre{});
         else
-            push_fwd<false>(A, acc, v < n ? v : 0, pt, pe);
+            push_fwd<false>(A, acc, v < n ? v : 0, pt, pe, PairPre{});
     }
 }
 
