@@ -649,6 +649,10 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
     for (uint32_t st = 0; st < steps; st++) expand_step<FWD, MAT>(A, acc, d, st * kUnroll, 1, mine != 0, ginst);
 }
 
+// Items a warp finishes before it adds them to the shared done count with one
+// atomic (the queue cursors are single words that every warp updates).
+constexpr unsigned long long kDoneBatch = 64;
+
 template <bool FWD, bool MAT>
 __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse(TravArgs A) {
     __shared__ uint64_t ginst[64];  // (i + 1) * G for instance i (residual searches)
@@ -659,6 +663,10 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
     Acc acc;
     uint64_t t_progress = globaltimer();
     unsigned long long seen_done = ld_volatile(&C->q_done.v);
+    // items this warp has finished but not yet added to the done count: added
+    // in batches, and always before the warp waits or leaves (a done count
+    // that lags only delays the drain test)
+    unsigned long long done_pend = 0;
     bool done = false;
     while (!done) {
         // Claims are interleaved across warps: claim c of a grid with W warps
@@ -691,11 +699,19 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
                 // of coherence before this one is issued.  (Items themselves are
                 // found by their non-zero fields, not by ordering.)
                 acc.pushed = false;
-                if (lane == 0) atomicAdd(&C->q_done.v, static_cast<unsigned long long>(__popc(hb)));
+                done_pend += __popc(hb);
+                if (done_pend >= kDoneBatch) {
+                    if (lane == 0) atomicAdd(&C->q_done.v, done_pend);
+                    done_pend = 0;
+                }
                 t_progress = globaltimer();
                 backoff = 32;
                 polls = 0;
             } else if (__any_sync(kFull, pending)) {
+                if (done_pend) {
+                    if (lane == 0) atomicAdd(&C->q_done.v, done_pend);
+                    done_pend = 0;
+                }
                 // nothing ready: items are still being written, more may be
                 // pushed, or the queue has drained.  The shared cursors are
                 // read only every 8th poll of the warp's own slots.
@@ -738,6 +754,7 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
         }
         if (__any_sync(kFull, empty)) done = true;
     }
+    if (done_pend && lane == 0) atomicAdd(&C->q_done.v, done_pend);
     flush_acc(A, acc, FWD);
 }
 
