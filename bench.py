@@ -112,14 +112,14 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_record(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel's
-    source has not changed since it was captured."""
+def traffic_record(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    this workload and the kernel's source has not changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get(kernel)
-    if not rec:
+    if not rec or rec.get("workload") != workload:
         return None
     src = os.path.join(ROOT, "paper_1408_6282_gb300", "csrc", rec["source"])
     if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
@@ -127,7 +127,7 @@ def traffic_record(kernel: str):
     return rec
 
 
-def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms):
+def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms, workload):
     """Roofline of one kernel group of the step, from its CUDA-event time and
     the algorithmic work of one step (the oracle's counts, so redundant GPU
     work is not credited).
@@ -164,7 +164,7 @@ def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms):
         units = f"{E} forward expansions x 16 B + {L} live out-edges x 20 B + {X} index entries x 8 B per step"
         key = "k_traverse_fwd"
     achieved = byts / sec / 1e9
-    trb = traffic_record(key)
+    trb = traffic_record(key, workload)
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
             "traffic": trb["dram_bytes_per_launch"] if trb else None,
             "traffic_note": (f"DRAM bytes per launch ({trb['launch']}), from profiles/traffic.json") if trb
@@ -476,7 +476,7 @@ def main():
     hbm_peak = json.load(open(PEAKS)).get("hbm_gbs", 6800.0) if os.path.exists(PEAKS) else 6800.0
     total_ms = sum(v[0] for v in kt.values())
     dominant = max(("rev_search", "fwd_search", "instances"), key=lambda kname: kt[kname][0])
-    roofline = kernel_roofline(dominant, kt, gold, g.m, w.l, args.steps, sm_max, hbm_peak, total_ms)
+    roofline = kernel_roofline(dominant, kt, gold, g.m, w.l, args.steps, sm_max, hbm_peak, total_ms, w.name)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1000.0, "higher_is_better": True,

@@ -354,6 +354,7 @@ class Workload:
 
 WORKLOADS = {
     "er4096": Workload("er4096", 1, "er", 4096, 32768, 0, 0.1, 16, 16, 10),
+    "rmat18_wc": Workload("rmat18_wc", 3, "rmat", 18, 16, 1, 0.0, 64, 64, 50),
     "rmat20_wc": Workload("rmat20_wc", 2, "rmat", 20, 16, 1, 0.0, 64, 64, 50),
     "rmat22_wc": Workload("rmat22_wc", 4, "rmat", 22, 16, 1, 0.0, 64, 64, 0),
     "rmat24_p01": Workload("rmat24_p01", 5, "rmat", 24, 16, 0, 0.01, 64, 64, 200),

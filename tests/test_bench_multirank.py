@@ -58,3 +58,20 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = argparse.Namespace(workload="er4096", warmup=0, steps=1, gpus=2)
     bench.run_reference(args, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_record_only_for_its_workload_and_source():
+    """roofline.traffic comes from profiles/traffic.json only for the workload
+    and the kernel source it was captured on."""
+    import hashlib
+    import json
+
+    import bench
+    recs = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    for kernel, rec in recs.items():
+        src = os.path.join(bench.ROOT, "paper_1408_6282_gb300", "csrc", rec["source"])
+        current = hashlib.sha256(open(src, "rb").read()).hexdigest() == rec["source_sha256"]
+        got = bench.traffic_record(kernel, rec["workload"])
+        assert (got is not None) == current
+        assert bench.traffic_record(kernel, rec["workload"] + "_other") is None
+    assert bench.traffic_record("no_such_kernel", "rmat20_wc") is None

@@ -161,11 +161,12 @@ def _golden(name):
     return json.load(open(path))
 
 
-def test_rmat20_wc_full_size(pkg):
-    """R-MAT scale 20, weighted cascade, l = k = 64: every sketch, 50 SKIM seeds
-    and the query set against stored oracle values."""
-    gold = _golden("rmat20_wc")
-    w = synth.WORKLOADS["rmat20_wc"]
+@pytest.mark.parametrize("name", ["rmat18_wc", "rmat20_wc"])
+def test_rmat_wc_full_size(pkg, name):
+    """R-MAT scale 18 and 20, weighted cascade, l = k = 64: every sketch, 50
+    SKIM seeds and the query set against stored oracle values."""
+    gold = _golden(name)
+    w = synth.WORKLOADS[name]
     g = w.graph(device="cuda")
     assert g.digest() == gold["graph_sha256"]
     ks = w.keys()
