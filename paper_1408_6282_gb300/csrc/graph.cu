@@ -142,37 +142,36 @@ SKIM_DEV void claim_pieces(const Pieces &P, uint32_t v, uint32_t e0, uint32_t e1
     }
 }
 
-// A tile whose masks hold more than kDenseBits instances is walked edge by
-// edge instead (each lane tests its own two instances in every mask).
-constexpr int kDenseBits = 12;
+// A tile of 32 edges (lane q holds edge q's 64-bit live mask) is turned into
+// one word per instance by transposing the two 32 x 32 bit matrices across
+// the warp: afterwards lane b holds, in bit q, whether edge q is live in
+// instance b (lo) and in instance b + 32 (hi).  Step j swaps the off-diagonal
+// j x j blocks of every 2j x 2j block: a lane without bit j keeps its columns
+// without bit j and takes its partner's others shifted up, the partner the
+// reverse.
+SKIM_DEV uint32_t warp_transpose32(uint32_t x) {
+    const uint32_t lane = threadIdx.x & 31;
+    constexpr uint32_t lo_cols[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+        const uint32_t j = 16u >> s, lo = lo_cols[s];
+        const uint32_t y = __shfl_xor_sync(kFull, x, j);
+        x = (lane & j) ? ((x & ~lo) | ((y >> j) & lo)) : ((x & lo) | ((y << j) & ~lo));
+    }
+    return x;
+}
 
 SKIM_DEV void warp_count(const uint64_t *mask, uint32_t e0, uint32_t e1, uint64_t &c0, uint64_t &c1) {
     const uint32_t lane = threadIdx.x & 31;
     for (; e0 < e1; e0 += 32) {
         const uint64_t mk = e0 + lane < e1 ? mask[e0 + lane] : 0;
-        uint64_t any = mk;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(kFull, any, o);
-        if (__popcll(any) > kDenseBits) {
-#pragma unroll 8
-            for (int q = 0; q < 32; q++) {
-                const uint64_t m = __shfl_sync(kFull, mk, q);
-                c0 += (m >> lane) & 1ull;
-                c1 += (m >> (lane + 32)) & 1ull;
-            }
-            continue;
-        }
-        for (uint64_t bits = any; bits; bits &= bits - 1) {
-            const uint32_t b = __ffsll(bits) - 1;
-            const uint32_t c = __popc(__ballot_sync(kFull, (mk >> b) & 1ull));
-            if (lane == (b & 31)) {
-                if (b < 32) c0 += c;
-                else c1 += c;
-            }
-        }
+        c0 += __popc(warp_transpose32(static_cast<uint32_t>(mk)));
+        c1 += __popc(warp_transpose32(static_cast<uint32_t>(mk >> 32)));
     }
 }
 
+// Writes the tile's live edges of instances lane and lane + 32 at p0 and p1,
+// in edge order; the warp loops as often as the fullest instance needs.
 SKIM_DEV void warp_fill(const uint64_t *mask, const uint32_t *col, uint32_t e0, uint32_t e1, uint64_t &p0,
                         uint64_t &p1, uint32_t *live) {
     const uint32_t lane = threadIdx.x & 31;
@@ -180,27 +179,18 @@ SKIM_DEV void warp_fill(const uint64_t *mask, const uint32_t *col, uint32_t e0, 
         const bool in = e0 + lane < e1;
         const uint64_t mk = in ? mask[e0 + lane] : 0;
         const uint32_t w = in ? col[e0 + lane] : 0;
-        uint64_t any = mk;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(kFull, any, o);
-        if (__popcll(any) > kDenseBits) {
-#pragma unroll 8
-            for (int q = 0; q < 32; q++) {
-                const uint64_t m = __shfl_sync(kFull, mk, q);
-                const uint32_t x = __shfl_sync(kFull, w, q);
-                if ((m >> lane) & 1ull) live[p0++] = x;
-                if ((m >> (lane + 32)) & 1ull) live[p1++] = x;
+        uint32_t m0 = warp_transpose32(static_cast<uint32_t>(mk));
+        uint32_t m1 = warp_transpose32(static_cast<uint32_t>(mk >> 32));
+        while (__any_sync(kFull, (m0 | m1) != 0)) {
+            const uint32_t x0 = __shfl_sync(kFull, w, m0 ? __ffs(m0) - 1 : 0);
+            const uint32_t x1 = __shfl_sync(kFull, w, m1 ? __ffs(m1) - 1 : 0);
+            if (m0) {
+                live[p0++] = x0;
+                m0 &= m0 - 1;
             }
-            continue;
-        }
-        for (uint64_t bits = any; bits; bits &= bits - 1) {
-            const uint32_t b = __ffsll(bits) - 1;
-            const unsigned bb = __ballot_sync(kFull, (mk >> b) & 1ull);
-            const uint64_t cur = __shfl_sync(kFull, b < 32 ? p0 : p1, b & 31);
-            if ((mk >> b) & 1ull) live[cur + __popc(bb & lanemask_lt())] = w;
-            if (lane == (b & 31)) {
-                if (b < 32) p0 += __popc(bb);
-                else p1 += __popc(bb);
+            if (m1) {
+                live[p1++] = x1;
+                m1 &= m1 - 1;
             }
         }
     }
