@@ -227,12 +227,9 @@ cudaError_t launch_node_sort(uint64_t *rec_key, uint32_t *rec_val, uint64_t R, u
     k_node_order<<<grid_for(n, 256), 256, 0, s>>>(tmp, off, n, tbits, o, list, nlist);
     note_launch();
     k_node_order_warp<<<152 * 4, 256, 0, s>>>(tmp, off, list, nlist, tbits, o);
-    const size_t smem = block_smem(tbits);
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_node_order_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-    }
+    const size_t smem = block_smem(tbits);  // up to 128 KB (19 word bits)
+    e = cudaFuncSetAttribute(k_node_order_block, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
     note_launch();
     k_node_order_block<<<SKIM_BIG_BLOCKS, kBigThreads, smem, s>>>(tmp, off, list, nlist, n, tbits, o);
     return cudaGetLastError();

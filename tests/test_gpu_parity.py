@@ -182,6 +182,22 @@ def test_rmat_wc_full_size(pkg, name):
         _check_skim(sk, gold["skim"], w.seeds)
 
 
+def test_rmat18_wc_sketches_large_batches(pkg):
+    """Batches of up to 2^24 lanes (the record table holds them to about 8M
+    here: 17 word bits, so 32 KB of shared memory per block for a node's word
+    bitmap and its prefix counts, four times the default run's): the sketches
+    must still match the stored oracle values."""
+    gold = _golden("rmat18_wc")
+    w = synth.WORKLOADS["rmat18_wc"]
+    g = w.graph(device="cuda")
+    ks = w.keys()
+    with pkg.Skim(g.n, g.src, g.dst, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob,
+                  batch_lanes=1 << 24) as sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        assert _digest(x, ln) == gold["sketches"]["sha256"]
+
+
 def _check_skim(sk, gs, s):
     """Seeds and coverages, and the Section 4.3.2 records where stored."""
     seeds, cov, tau, kp = sk.greedy_stops(s)
