@@ -12,7 +12,9 @@
  *     context is unusable and must be destroyed.
  *   - Ownership: inputs are borrowed for the duration of the call and copied;
  *     outputs are written to caller-owned buffers.  All device memory used by
- *     a context is allocated by the library and released by skim_destroy().
+ *     a context is allocated by the library, on the context's stream, from a
+ *     pool per device, and skim_destroy() returns it to that pool (see
+ *     skim_release_memory()).
  *   - Pointers marked (host) must be host memory; pointers marked
  *     (host|device) may be either, as stated by the accompanying flag.
  *   - Calls on one context are not thread-safe; use one context per thread.
@@ -350,6 +352,16 @@ int skim_union_estimate_static(const uint64_t *x_dev, const uint32_t *len_dev, u
                                const uint32_t *seeds_dev, uint32_t n_seeds, double *est_dev, void *stream);
 
 int skim_destroy(skim_ctx *ctx);
+
+/* The library keeps one stream-ordered device memory pool per device: blocks
+ * that skim_destroy() frees stay reserved for the next context on that
+ * device, so a context per graph or per request does not pay for cudaMalloc
+ * and cudaFree of its scratch (several GB at R-MAT scale 20) each time.
+ * skim_release_memory() hands every block that no live context holds back to
+ * the device, on every device the library has used; live contexts are not
+ * affected.  Thread-safe.
+ * Errors: SKIM_ECUDA. */
+int skim_release_memory(void);
 
 const char *skim_strerror(int code);
 

@@ -70,6 +70,7 @@ def load():
     lib.skim_oracle_query_batch.argtypes = [vp, vp, u32, vp, vp, C.c_int]
     lib.skim_get_stats.argtypes = [vp, vp, u32]
     lib.skim_destroy.argtypes = [vp]
+    lib.skim_release_memory.argtypes = []
     lib.skim_rank_order.argtypes = [vp]
     lib.skim_instances.argtypes = [vp]
     lib.skim_instance_stats.argtypes = [vp, vp, vp]
@@ -274,6 +275,11 @@ def skim_server_stop(srv: int):
 
 def skim_destroy(ctx: int):
     _check(load().skim_destroy(ctx), "skim_destroy")
+
+
+def skim_release_memory():
+    """Hand the device memory pooled from destroyed contexts back to the device."""
+    _check(load().skim_release_memory(), "skim_release_memory")
 
 
 def skim_strerror(code: int) -> str:

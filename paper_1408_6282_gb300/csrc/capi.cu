@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -151,11 +152,44 @@ int fail_cuda(skim_ctx *c, cudaError_t e) {
         if (r_ != SKIM_OK) return r_; \
     } while (0)
 
-template <class T>
-int dalloc(skim_ctx *c, T **p, size_t count) {
+// Device memory of every context comes from one stream-ordered pool per
+// device that keeps the blocks freed by skim_destroy (release threshold: never)
+// for the next context, so a context per graph or per request does not pay
+// for cudaMalloc and cudaFree of its gigabytes of scratch each time.
+// Allocations and frees are ordered on the context's stream.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaError_t device_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if ((e = cudaMemPoolCreate(&p, &props)) != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        if ((e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pool[dev] = p;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+int dalloc_bytes(skim_ctx *c, void **p, size_t bytes) {
     *p = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    cudaMemPool_t pool;
+    cudaError_t e = device_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, c->st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -165,8 +199,13 @@ int dalloc(skim_ctx *c, T **p, size_t count) {
 }
 
 template <class T>
-void dfree(T *&p) {
-    if (p) cudaFree(p);
+int dalloc(skim_ctx *c, T **p, size_t count) {
+    return dalloc_bytes(c, reinterpret_cast<void **>(p), (count ? count : 1) * sizeof(T));
+}
+
+template <class T>
+void dfree(skim_ctx *c, T *&p) {
+    if (p) cudaFreeAsync(p, c->st);
     p = nullptr;
 }
 
@@ -470,7 +509,7 @@ int ensure_idx(skim_ctx *c, uint64_t need) {
     RC(dalloc(c, &nb, cap));
     if (c->idx_used) CK(c, cudaMemcpyAsync(nb, c->idx, c->idx_used * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->st));
     CK(c, cudaStreamSynchronize(c->st));
-    dfree(c->idx);
+    dfree(c, c->idx);
     c->idx = nb;
     c->idx_cap = cap;
     return SKIM_OK;
@@ -624,7 +663,7 @@ int make_instances(skim_ctx *c) {
         RC(dalloc(c, &c->fmask, std::max<uint64_t>(c->m, 1)));
         RC(dalloc(c, &c->loff, c->nl + 1));
         RC(dalloc(c, &c->foff, c->nl + 1));
-        CK(c, cudaMalloc(&c->pieces, live_pieces_bytes(c->m)));
+        RC(dalloc_bytes(c, &c->pieces, live_pieces_bytes(c->m)));
     }
     CK(c, launch_live_masks(c->rrow, c->rcol, c->rhe, c->rtm1, c->rev2fwd, c->cm, c->m, c->l, c->rmask, c->fmask,
                             c->st));
@@ -635,8 +674,8 @@ int make_instances(skim_ctx *c) {
     CK(c, cudaStreamSynchronize(c->st));
     if (c->live_total >= (1ull << 32)) return SKIM_OK;
     if (c->live_total > c->rlive_cap) {
-        dfree(c->rlive);
-        dfree(c->flive);
+        dfree(c, c->rlive);
+        dfree(c, c->flive);
         c->rlive_cap = 0;
         RC(dalloc(c, &c->rlive, c->live_total));
         RC(dalloc(c, &c->flive, c->live_total));
@@ -668,26 +707,24 @@ int rank_order(skim_ctx *c) {
 
 int ensure_query_space(skim_ctx *c, uint64_t seeds, uint64_t q, uint64_t table, uint64_t chunks) {
     if (chunks > c->qpart_cap) {
-        if (c->qpart) cudaFree(c->qpart);
-        c->qpart = nullptr;
+        dfree(c, c->qpart);
         c->qpart_cap = std::max<uint64_t>(chunks, 1024);
-        cudaError_t e = cudaMalloc(&c->qpart, c->qpart_cap * query_partial_bytes());
-        if (e != cudaSuccess) {
-            cudaGetLastError();
+        const int rc = dalloc_bytes(c, &c->qpart, c->qpart_cap * query_partial_bytes());
+        if (rc != SKIM_OK) {
             c->qpart_cap = 0;
-            return SKIM_ENOMEM;
+            return rc;
         }
     }
     if (seeds > c->qseeds_cap) {
-        dfree(c->qseeds);
+        dfree(c, c->qseeds);
         c->qseeds_cap = std::max<uint64_t>(seeds, 4096);
         RC(dalloc(c, &c->qseeds, c->qseeds_cap));
     }
     if (q + 1 > c->qmeta_cap) {
-        dfree(c->qoff);
-        dfree(c->qout);
-        dfree(c->qtop);
-        dfree(c->qtopu);
+        dfree(c, c->qoff);
+        dfree(c, c->qout);
+        dfree(c, c->qtop);
+        dfree(c, c->qtopu);
         c->qmeta_cap = std::max<uint64_t>(q + 1, 1024);
         RC(dalloc(c, &c->qoff, 3 * c->qmeta_cap));  // seed, table and chunk offsets in one upload
         RC(dalloc(c, &c->qout, c->qmeta_cap));
@@ -695,8 +732,8 @@ int ensure_query_space(skim_ctx *c, uint64_t seeds, uint64_t q, uint64_t table, 
         RC(dalloc(c, &c->qtopu, c->qmeta_cap));
     }
     if (table > c->qtcap) {
-        dfree(c->qk);
-        dfree(c->qv);
+        dfree(c, c->qk);
+        dfree(c, c->qv);
         c->qtcap = std::max<uint64_t>(table, 1ull << 16);
         RC(dalloc(c, &c->qk, c->qtcap));
         RC(dalloc(c, &c->qv, c->qtcap));
@@ -734,32 +771,42 @@ const char *skim_strerror(int code) {
 int skim_destroy(skim_ctx *c) {
     if (!c) return SKIM_EINVAL;
     cudaStreamSynchronize(c->st);
-    dfree(c->fptr); dfree(c->fcol); dfree(c->rptr); dfree(c->rcol); dfree(c->thr_wc);
-    dfree(c->rhe); dfree(c->fhe);
-    dfree(c->srank); dfree(c->spair);
-    if (c->rank_ws) cudaFree(c->rank_ws);
-    dfree(c->rbase); dfree(c->rtm1); dfree(c->ftm1);
-    dfree(c->ctl); dfree(c->dflag);
+    dfree(c, c->fptr); dfree(c, c->fcol); dfree(c, c->rptr); dfree(c, c->rcol); dfree(c, c->thr_wc);
+    dfree(c, c->rhe); dfree(c, c->fhe);
+    dfree(c, c->srank); dfree(c, c->spair);
+    dfree(c, c->rank_ws);
+    dfree(c, c->rbase); dfree(c, c->rtm1); dfree(c, c->ftm1);
+    dfree(c, c->ctl); dfree(c, c->dflag);
     if (c->hctl) cudaFreeHost(c->hctl);
-    dfree(c->q); dfree(c->hkeys); dfree(c->pend);
+    dfree(c, c->q); dfree(c, c->hkeys); dfree(c, c->pend);
     c->hvals = nullptr;
-    dfree(c->rkey); dfree(c->rkey2); dfree(c->rval); dfree(c->rval2);
-    dfree(c->ncnt); dfree(c->noff); dfree(c->nlist); dfree(c->nlist_cnt);
-    if (c->ws) cudaFree(c->ws);
-    dfree(c->lane_inst); dfree(c->lane_g); dfree(c->alive); dfree(c->lane_cnt); dfree(c->lane_off); dfree(c->lane_fill);
-    dfree(c->lcnt); dfree(c->full); dfree(c->X); dfree(c->xlen);
-    dfree(c->covered); dfree(c->seg_start); dfree(c->pend_trav); dfree(c->pend_erase);
-    dfree(c->size); dfree(c->seg_len); dfree(c->idx); dfree(c->chosen);
-    dfree(c->rec_tau); dfree(c->rec_kp);
-    dfree(c->rmask); dfree(c->fmask); dfree(c->loff); dfree(c->rlive); dfree(c->rrow); dfree(c->rev2fwd);
-    dfree(c->foff); dfree(c->flive);
-    if (c->pieces) cudaFree(c->pieces);
-    dfree(c->qk); dfree(c->qv); dfree(c->qseeds); dfree(c->qoff); dfree(c->qout);
-    dfree(c->qtop); dfree(c->qtopu);
-    if (c->qpart) cudaFree(c->qpart);
+    dfree(c, c->rkey); dfree(c, c->rkey2); dfree(c, c->rval); dfree(c, c->rval2);
+    dfree(c, c->ncnt); dfree(c, c->noff); dfree(c, c->nlist); dfree(c, c->nlist_cnt);
+    dfree(c, c->ws);
+    dfree(c, c->lane_inst); dfree(c, c->lane_g); dfree(c, c->alive); dfree(c, c->lane_cnt); dfree(c, c->lane_off); dfree(c, c->lane_fill);
+    dfree(c, c->lcnt); dfree(c, c->full); dfree(c, c->X); dfree(c, c->xlen);
+    dfree(c, c->covered); dfree(c, c->seg_start); dfree(c, c->pend_trav); dfree(c, c->pend_erase);
+    dfree(c, c->size); dfree(c, c->seg_len); dfree(c, c->idx); dfree(c, c->chosen);
+    dfree(c, c->rec_tau); dfree(c, c->rec_kp);
+    dfree(c, c->rmask); dfree(c, c->fmask); dfree(c, c->loff); dfree(c, c->rlive); dfree(c, c->rrow); dfree(c, c->rev2fwd);
+    dfree(c, c->foff); dfree(c, c->flive);
+    dfree(c, c->pieces);
+    dfree(c, c->qk); dfree(c, c->qv); dfree(c, c->qseeds); dfree(c, c->qoff); dfree(c, c->qout);
+    dfree(c, c->qtop); dfree(c, c->qtopu);
+    dfree(c, c->qpart);
     for (auto &p : c->kpend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->kpool) cudaEventDestroy(e);
     delete c;
+    return SKIM_OK;
+}
+
+int skim_release_memory(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int d = 0; d < kMaxDevices; d++)
+        if (g_pool[d] && cudaMemPoolTrimTo(g_pool[d], 0) != cudaSuccess) {
+            cudaGetLastError();
+            return SKIM_ECUDA;
+        }
     return SKIM_OK;
 }
 
@@ -845,7 +892,7 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         TRYC(cudaMemcpyAsync(&bad, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
         TRYC(cudaStreamSynchronize(c->st));
         if (bad) {
-            if (own_edges) { dfree(dsrc); dfree(ddst); }
+            if (own_edges) { dfree(c, dsrc); dfree(c, ddst); }
             rc = SKIM_EGRAPH;
             goto fail;
         }
@@ -859,7 +906,7 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
                               radix_workspace_bytes(m),
                               radix_workspace_bytes(rcap), scan_workspace_bytes(static_cast<size_t>(kMaxWords) * 64)});
         c->ws_bytes = ws;
-        TRYC(cudaMalloc(&c->ws, ws));
+        TRY(dalloc_bytes(c, &c->ws, ws));
         // forward CSR: rows of the (src,dst)-sorted list
         uint64_t *deg = nullptr;
         TRY(dalloc(c, &deg, static_cast<size_t>(n) + 1));
@@ -890,11 +937,11 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
             TRY(dalloc(c, &c->rev2fwd, m));
             TRYC(launch_split_rev(k1, v1, m, c->rcol, c->rrow, c->rev2fwd, c->st));
             TRYC(cudaStreamSynchronize(c->st));
-            dfree(k1); dfree(k2); dfree(v1); dfree(v2);
+            dfree(c, k1); dfree(c, k2); dfree(c, v1); dfree(c, v2);
         }
         TRYC(cudaStreamSynchronize(c->st));
-        dfree(deg);
-        if (own_edges) { dfree(dsrc); dfree(ddst); }
+        dfree(c, deg);
+        if (own_edges) { dfree(c, dsrc); dfree(c, ddst); }
         // degree limits of the chunked work items
         unsigned long long *md = reinterpret_cast<unsigned long long *>(c->ctl);
         TRYC(cudaMemsetAsync(md, 0, sizeof(unsigned long long), c->st));
@@ -918,10 +965,10 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         // rank order of the n*l pairs
         TRY(dalloc(c, &c->srank, npos));
         TRY(dalloc(c, &c->spair, npos));
-        TRYC(cudaMalloc(&c->rank_ws, c->rank_mode == SKIM_RANKS_UNIFORM
-                                         ? rank_sort_workspace_bytes(nl)
-                                         : perm_sort_workspace_bytes(n, c->l, static_cast<uint32_t>(npos / n),
-                                                                     c->rank_mode == SKIM_RANKS_IC_MODEL)));
+        TRY(dalloc_bytes(c, &c->rank_ws, c->rank_mode == SKIM_RANKS_UNIFORM
+                                             ? rank_sort_workspace_bytes(nl)
+                                             : perm_sort_workspace_bytes(n, c->l, static_cast<uint32_t>(npos / n),
+                                                                         c->rank_mode == SKIM_RANKS_IC_MODEL)));
         c->rank_key = prm->rank_key;
         TRY(rank_order(c));
         // traversal scratch
@@ -1042,10 +1089,10 @@ int skim_create_batch(const skim_graph *graphs, const skim_params *prm, uint32_t
              launch_rank_bases(b, c->n, c->l, c->rbase, c->st) == cudaSuccess;
     }
     if (ok) ok = cudaStreamSynchronize(c->st) == cudaSuccess;
-    dfree(d_off);
-    dfree(d_ng);
-    dfree(d_keys);
-    dfree(d_model);
+    dfree(c, d_off);
+    dfree(c, d_ng);
+    dfree(c, d_keys);
+    dfree(c, d_model);
     if (!ok) return fail(fail_cuda(c, cudaGetLastError()));
     c->cm.model = 3;
     c->batch_count = count;
@@ -1244,8 +1291,8 @@ int skim_greedy_ex(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t 
                 if (kprime_out) kprime_out[j] = static_cast<int32_t>(kp[j]);
             }
         }
-        dfree(c->rec_tau);
-        dfree(c->rec_kp);
+        dfree(c, c->rec_tau);
+        dfree(c, c->rec_kp);
         RC(rc);
     } else {
         RC(greedy_loop(c, n_seeds, seeds_out, cov_out));
@@ -1335,7 +1382,7 @@ int skim_node_estimates(skim_ctx *c, double *out, int out_on_device) {
          cudaMemcpyAsync(out, d, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess) ||
         cudaStreamSynchronize(c->st) != cudaSuccess)
         rc = fail_cuda(c, cudaGetLastError());
-    if (!out_on_device) dfree(d);
+    if (!out_on_device) dfree(c, d);
     return rc;
 }
 

@@ -182,6 +182,24 @@ def test_rmat_wc_full_size(pkg, name):
         _check_skim(sk, gold["skim"], w.seeds)
 
 
+def test_contexts_on_pooled_memory(pkg):
+    """Contexts created one after another reuse the pooled blocks of the
+    destroyed ones (stale contents included) and after a release take fresh
+    ones: the sketches match the stored oracle values every time."""
+    gold = _golden("er4096")
+    w = synth.WORKLOADS["er4096"]
+    g = w.graph()
+    ks = w.keys()
+    for rep in range(3):
+        if rep == 2:
+            pkg.skim_release_memory()
+        with pkg.Skim(g.n, g.src, g.dst, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob) as sk:
+            sk.build_sketches()
+            x, ln = sk.sketches()
+            assert _digest(x, ln) == gold["sketches"]["sha256"]
+            _check_skim(sk, gold["skim"], w.seeds)
+
+
 def test_rmat18_wc_sketches_large_batches(pkg):
     """Batches of up to 2^24 lanes (the record table holds them to about 8M
     here: 17 word bits, so 32 KB of shared memory per block for a node's word
