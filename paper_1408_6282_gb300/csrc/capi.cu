@@ -908,22 +908,15 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         c->ws_bytes = ws;
         TRY(dalloc_bytes(c, &c->ws, ws));
         // forward CSR: rows of the (src,dst)-sorted list
-        uint64_t *deg = nullptr;
-        TRY(dalloc(c, &deg, static_cast<size_t>(n) + 1));
         TRY(dalloc(c, &c->fptr, static_cast<size_t>(n) + 1));
         TRY(dalloc(c, &c->rptr, static_cast<size_t>(n) + 1));
         TRY(dalloc(c, &c->fcol, m));
         TRY(dalloc(c, &c->rcol, m));
-        TRYC(cudaMemsetAsync(deg, 0, (static_cast<size_t>(n) + 1) * sizeof(uint64_t), c->st));
-        TRYC(launch_degree_count(dsrc, m, deg, c->st));
-        TRYC(exclusive_scan_u64(deg, deg, static_cast<size_t>(n) + 1, nullptr, c->ws, c->st));
-        TRYC(launch_u64_to_u32(deg, c->fptr, static_cast<size_t>(n) + 1, c->st));
+        TRY(dalloc(c, &c->rrow, m));
+        TRY(dalloc(c, &c->rev2fwd, m));
+        TRYC(launch_row_ptr(dsrc, m, n, c->fptr, c->st));
         if (m) TRYC(cudaMemcpyAsync(c->fcol, ddst, m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->st));
-        // reverse CSR: sort by (dst, src)
-        TRYC(cudaMemsetAsync(deg, 0, (static_cast<size_t>(n) + 1) * sizeof(uint64_t), c->st));
-        TRYC(launch_degree_count(ddst, m, deg, c->st));
-        TRYC(exclusive_scan_u64(deg, deg, static_cast<size_t>(n) + 1, nullptr, c->ws, c->st));
-        TRYC(launch_u64_to_u32(deg, c->rptr, static_cast<size_t>(n) + 1, c->st));
+        // reverse CSR: (dst, src) order, by a stable sort on the dst bits
         if (m) {
             uint64_t *k1 = nullptr, *k2 = nullptr;
             uint32_t *v1 = nullptr, *v2 = nullptr;
@@ -932,30 +925,16 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
             TRY(dalloc(c, &v1, m));
             TRY(dalloc(c, &v2, m));
             TRYC(launch_make_rev_keys(dsrc, ddst, m, k1, v1, c->st));
-            TRYC(radix_sort_pairs(k1, v1, k2, v2, m, 32 + bitlen(n - 1), c->ws, c->st));
-            TRY(dalloc(c, &c->rrow, m));
-            TRY(dalloc(c, &c->rev2fwd, m));
+            TRYC(radix_sort_pairs(k1, v1, k2, v2, m, std::max(1, bitlen(n - 1)), c->ws, c->st));
             TRYC(launch_split_rev(k1, v1, m, c->rcol, c->rrow, c->rev2fwd, c->st));
-            TRYC(cudaStreamSynchronize(c->st));
-            dfree(c, k1); dfree(c, k2); dfree(c, v1); dfree(c, v2);
+            dfree(c, k1); dfree(c, k2); dfree(c, v1); dfree(c, v2);  // (stream-ordered)
         }
-        TRYC(cudaStreamSynchronize(c->st));
-        dfree(c, deg);
+        TRYC(launch_row_ptr(c->rrow, m, n, c->rptr, c->st));
         if (own_edges) { dfree(c, dsrc); dfree(c, ddst); }
-        // degree limits of the chunked work items
-        unsigned long long *md = reinterpret_cast<unsigned long long *>(c->ctl);
-        TRYC(cudaMemsetAsync(md, 0, sizeof(unsigned long long), c->st));
-        TRYC(launch_max_degree(c->rptr, n, md, c->st));
-        TRYC(launch_max_degree(c->fptr, n, md, c->st));
-        unsigned long long maxdeg = 0;
-        TRYC(cudaMemcpyAsync(&maxdeg, md, sizeof(maxdeg), cudaMemcpyDeviceToHost, c->st));
-        TRYC(cudaStreamSynchronize(c->st));
         TRYC(cudaMemsetAsync(c->ctl, 0, sizeof(DevCtl), c->st));
-        (void)maxdeg;
         TRY(dalloc(c, &c->rhe, m));
         TRY(dalloc(c, &c->fhe, m));
-        TRYC(launch_edge_states(c->rptr, c->rcol, n, prm->coin_key, 1, c->rhe, c->st));
-        TRYC(launch_edge_states(c->fptr, c->fcol, n, prm->coin_key, 0, c->fhe, c->st));
+        TRYC(launch_edge_states_both(c->rcol, c->rrow, c->rev2fwd, m, prm->coin_key, c->rhe, c->fhe, c->st));
         if (prm->prob_model == 1) {
             TRY(dalloc(c, &c->thr_wc, n));
             TRYC(launch_wc_thresholds(c->rptr, n, c->thr_wc, c->st));

@@ -41,23 +41,52 @@ __global__ void k_u64_to_u32(const uint64_t *in, uint32_t *out, size_t n) {
         out[i] = static_cast<uint32_t>(in[i]);
 }
 
+// Keys for the reverse CSR: (src << 32 | dst).  The input is sorted by
+// (src, dst), so a stable sort on the dst bits alone yields (dst, src) order.
 __global__ void k_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint64_t m, uint64_t *key, uint32_t *val) {
     for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < m;
          e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        key[e] = (static_cast<uint64_t>(dst[e]) << 32) | src[e];
-        val[e] = static_cast<uint32_t>(e);  // forward CSR position (the input is sorted by (src, dst))
+        key[e] = (static_cast<uint64_t>(src[e]) << 32) | dst[e];
+        val[e] = static_cast<uint32_t>(e);  // forward CSR position
     }
 }
 
-// reverse CSR from the (dst, src)-sorted keys: column (src), row (dst) and the
+// reverse CSR from the (dst, src)-ordered keys: column (src), row (dst) and the
 // edge's forward CSR position
 __global__ void k_split_rev(const uint64_t *key, const uint32_t *val, uint64_t m, uint32_t *rcol, uint32_t *rrow,
                             uint32_t *rev2fwd) {
     for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < m;
          e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        rcol[e] = static_cast<uint32_t>(key[e]);
-        rrow[e] = static_cast<uint32_t>(key[e] >> 32);
+        rcol[e] = static_cast<uint32_t>(key[e] >> 32);
+        rrow[e] = static_cast<uint32_t>(key[e]);
         rev2fwd[e] = val[e];
+    }
+}
+
+// CSR row pointers of a row-sorted edge array: ptr[v] = the first edge whose
+// row is at least v (a binary search per node), ptr[n] = m.
+__global__ void k_row_ptr(const uint32_t *row, uint64_t m, uint32_t n, uint32_t *ptr) {
+    for (uint64_t v = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; v <= n;
+         v += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        uint64_t lo = 0, hi = m;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (row[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        ptr[v] = static_cast<uint32_t>(lo);
+    }
+}
+
+// Per-edge coin states of both CSR orders from the reverse one: an edge's
+// state depends on (src, dst) only.
+__global__ void k_edge_states_both(const uint32_t *rcol, const uint32_t *rrow, const uint32_t *rev2fwd, uint64_t m,
+                                   uint64_t coin_key, uint64_t *rhe, uint64_t *fhe) {
+    for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < m;
+         e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t h = edge_state(coin_key, rcol[e], rrow[e]);
+        rhe[e] = h;
+        fhe[rev2fwd[e]] = h;
     }
 }
 
@@ -553,6 +582,18 @@ cudaError_t launch_split_rev(const uint64_t *key, const uint32_t *val, uint64_t 
     if (m == 0) return cudaSuccess;
     note_launch();
     k_split_rev<<<grid_for(m, 256), 256, 0, s>>>(key, val, m, rcol, rrow, rev2fwd);
+    return cudaGetLastError();
+}
+cudaError_t launch_row_ptr(const uint32_t *row, uint64_t m, uint32_t n, uint32_t *ptr, cudaStream_t s) {
+    note_launch();
+    k_row_ptr<<<grid_for(static_cast<size_t>(n) + 1, 256), 256, 0, s>>>(row, m, n, ptr);
+    return cudaGetLastError();
+}
+cudaError_t launch_edge_states_both(const uint32_t *rcol, const uint32_t *rrow, const uint32_t *rev2fwd, uint64_t m,
+                                    uint64_t coin_key, uint64_t *rhe, uint64_t *fhe, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    note_launch();
+    k_edge_states_both<<<grid_for(m, 256), 256, 0, s>>>(rcol, rrow, rev2fwd, m, coin_key, rhe, fhe);
     return cudaGetLastError();
 }
 cudaError_t launch_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr, cudaStream_t s) {

@@ -68,6 +68,11 @@ struct TravArgs {
 cudaError_t launch_check_edges(const uint32_t *src, const uint32_t *dst, uint64_t m, uint32_t n, unsigned *bad,
                                cudaStream_t s);
 cudaError_t launch_degree_count(const uint32_t *idx, uint64_t m, uint64_t *deg, cudaStream_t s);
+// ptr[v] = first index with row[index] >= v, for v = 0..n (row sorted)
+cudaError_t launch_row_ptr(const uint32_t *row, uint64_t m, uint32_t n, uint32_t *ptr, cudaStream_t s);
+// rhe[e] = fhe[rev2fwd[e]] = edge_state(coin_key, rcol[e], rrow[e]) over the reverse CSR
+cudaError_t launch_edge_states_both(const uint32_t *rcol, const uint32_t *rrow, const uint32_t *rev2fwd, uint64_t m,
+                                    uint64_t coin_key, uint64_t *rhe, uint64_t *fhe, cudaStream_t s);
 cudaError_t launch_u64_to_u32(const uint64_t *in, uint32_t *out, size_t n, cudaStream_t s);
 cudaError_t launch_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint64_t m, uint64_t *key, uint32_t *val,
                                  cudaStream_t s);
