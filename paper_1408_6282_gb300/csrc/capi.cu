@@ -365,6 +365,17 @@ constexpr uint64_t kNodeSortDensity = 4;
 // visited-table slots per expected visit record of a batch
 constexpr double kTableSlots = SKIM_TABLE_SLOTS;
 
+// Buffers of the per-node record placement; the counters start at zero.
+int node_buffers(skim_ctx *c) {
+    if (c->ncnt) return SKIM_OK;
+    RC(dalloc(c, &c->ncnt, static_cast<size_t>(c->n) + 1));
+    RC(dalloc(c, &c->noff, static_cast<size_t>(c->n) + 1));
+    RC(dalloc(c, &c->nlist, c->n));
+    RC(dalloc(c, &c->nlist_cnt, 2));
+    CK(c, cudaMemsetAsync(c->ncnt, 0, (static_cast<size_t>(c->n) + 1) * sizeof(uint64_t), c->st));
+    return SKIM_OK;
+}
+
 // Reverse search of the batch of ranks [p0, p0+B).  mode_build: Algorithm 2
 // (pruned by local counts); otherwise SKIM (covered sources skipped).
 // est_per_lane: expected visit records per lane (0 = unknown).  The visited
@@ -414,13 +425,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     // records dense over the nodes: place them node by node (one pass over
     // the n node counters); sparse: radix sort over the key bits
     c->bnode = static_cast<uint64_t>(c->n) <= kNodeSortDensity * R;
-    if (c->bnode && !c->ncnt) {
-        RC(dalloc(c, &c->ncnt, static_cast<size_t>(c->n) + 1));
-        RC(dalloc(c, &c->noff, static_cast<size_t>(c->n) + 1));
-        RC(dalloc(c, &c->nlist, c->n));
-        RC(dalloc(c, &c->nlist_cnt, 2));
-        CK(c, cudaMemsetAsync(c->ncnt, 0, (static_cast<size_t>(c->n) + 1) * sizeof(uint64_t), c->st));
-    }
+    if (c->bnode) RC(node_buffers(c));
     {
         KTimer kt(c, SKIM_K_SORT);
         if (c->bnode)

@@ -863,13 +863,19 @@ __global__ void k_respill_fwd(TravArgs A, uint32_t n) {
     }
 }
 
+// The seed x covers its pairs in every instance: with materialised instances
+// lane j takes instances j and j + 32, otherwise lane 0 takes them all.
 __global__ void k_fwd_source(TravArgs A, uint32_t x) {
     const uint64_t lmask = A.l == 64 ? ~0ull : ((1ull << A.l) - 1);
     Acc acc;
-    if (A.mat)
-        emit_fwd<true>(A, acc, threadIdx.x == 0, x, lmask);
-    else
+    if (A.mat) {
+        for (uint32_t i0 = 0; i0 < A.l; i0 += 32) {
+            const uint32_t i = i0 + threadIdx.x;
+            emit_fwd<true>(A, acc, i < A.l, x, i < A.l ? 1ull << i : 0);
+        }
+    } else {
         emit_fwd<false>(A, acc, threadIdx.x == 0, x, lmask);
+    }
     flush_acc(A, acc, true);
 }
 
