@@ -384,7 +384,8 @@ __global__ void k_rank_scatter(K kf, uint64_t total, const uint64_t *off, unsign
 // x) and uniform, so a bucket of up to kBucketCap elements is placed by a
 // counting sort on the next kSubBits bits below the bucket's own, after which
 // the few elements sharing a sub-bucket are put in order one sub-bucket per
-// thread.  A larger bucket is placed by counting smaller keys; that path is
+// thread; all of it on a permutation in shared memory, so that the bucket is
+// written to memory once.  A larger bucket is placed by counting smaller keys; that path is
 // correct for any size and only its speed depends on the bucket sizes.
 template <class K>
 __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(K kf, const uint64_t *off, const uint32_t *tmp,
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(K kf, const uint
     __shared__ uint64_t key[kBucketCap];
     __shared__ uint32_t val[kBucketCap];
     __shared__ uint32_t cnt[kSub];
+    __shared__ uint16_t perm[kBucketCap];
     __shared__ uint32_t wsum[kBucketThreads / 32];
     const uint64_t b0 = off[blockIdx.x], b1 = off[blockIdx.x + 1];
     const uint32_t s = static_cast<uint32_t>(b1 - b0);
@@ -430,32 +432,30 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_sort(K kf, const uint
 #pragma unroll
         for (int q = 0; q < per; q++) cnt[threadIdx.x * per + q] = tbase + loc[q];
         __syncthreads();
-        // scatter (keys in the rank slots for now); cnt[b] ends as the end of sub-bucket b
+        // scatter positions (a permutation in shared memory); cnt[b] ends as
+        // the end of sub-bucket b
         for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) {
             const uint32_t pos = atomicAdd(&cnt[kf.sub(key[i])], 1u);
-            sorted_rank[b0 + pos] = key[i];
-            sorted_pair[b0 + pos] = val[i];
+            perm[pos] = static_cast<uint16_t>(i);
         }
         __syncthreads();
         // order inside the sub-buckets that hold more than one element
         for (uint32_t b = threadIdx.x; b < kSub; b += blockDim.x) {
             const uint32_t lo = b ? cnt[b - 1] : 0, hi = cnt[b];
             for (uint32_t i = lo + 1; i < hi; i++) {
-                const uint64_t kx = sorted_rank[b0 + i];
-                const uint32_t vx = sorted_pair[b0 + i];
+                const uint16_t pi = perm[i];
+                const uint64_t kx = key[pi];
                 uint32_t j = i;
-                for (; j > lo && sorted_rank[b0 + j - 1] > kx; j--) {
-                    sorted_rank[b0 + j] = sorted_rank[b0 + j - 1];
-                    sorted_pair[b0 + j] = sorted_pair[b0 + j - 1];
-                }
-                sorted_rank[b0 + j] = kx;
-                sorted_pair[b0 + j] = vx;
+                for (; j > lo && key[perm[j - 1]] > kx; j--) perm[j] = perm[j - 1];
+                perm[j] = pi;
             }
         }
         __syncthreads();
+        // one coalesced write of the bucket
         for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) {
-            sorted_rank[b0 + i] = kf.out_rank(b0 + i, sorted_rank[b0 + i]);
-            sorted_pair[b0 + i] = kf.out_pair(sorted_pair[b0 + i]);
+            const uint16_t pi = perm[i];
+            sorted_rank[b0 + i] = kf.out_rank(b0 + i, key[pi]);
+            sorted_pair[b0 + i] = kf.out_pair(val[pi]);
         }
         return;
     }
