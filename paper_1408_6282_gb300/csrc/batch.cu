@@ -192,30 +192,69 @@ SKIM_DEV uint64_t range_mask(uint64_t t, uint32_t lo, uint32_t hi) {
     return m;
 }
 
+// SKIM's stop: per node v the lane at which size[v] reaches k, i.e. the
+// need = k - size[v]-th uncovered lane bit (from lane lo on) of v's records in
+// rank order (a node already at k stops at its first record).  Warps own the
+// runs that start in 32-record windows, as in the acceptance; a segmented
+// scan over the lanes counts each node's bits in order.
 __global__ void k_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                              const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
                              uint32_t k, DevCtl *ctl) {
+    const uint32_t lane = threadIdx.x & 31;
     const uint64_t tmask = (1ull << tbits) - 1;
-    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
-         r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        if (!run_start(rec_key, r, tbits)) continue;
-        const uint64_t v = rec_key[r] >> tbits;
-        const uint32_t need = k - size[v];
-        uint32_t cum = 0;
-        for (uint64_t rr = r; rr < R && (rec_key[rr] >> tbits) == v; rr++) {
-            const uint64_t t = rec_key[rr] & tmask;
-            uint64_t m = hvals[2ull * rec_val[rr]] & alive[t] & range_mask(t, lo, 0xffffffffu);
-            uint32_t c = __popcll(m);
-            if (cum + c >= need) {
-                uint64_t p = t * 64 + nth_set_bit(m, static_cast<int>(need - cum - 1));
-                atomicMin(&ctl->best, (p << 32) | v);
-                break;
+    const uint64_t warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+    const uint64_t nwin = (R + 31) / 32;
+    for (uint64_t w = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5; w < nwin; w += warps) {
+        const uint64_t W0 = w * 32, W1 = min(R, W0 + 32);
+        bool st = false;
+        if (W0 + lane < W1) st = run_start(rec_key, W0 + lane, tbits);
+        const unsigned sb = __ballot_sync(kFull, st);
+        if (!sb) continue;
+        const uint64_t s0 = W0 + __ffs(sb) - 1;
+        const uint64_t last = rec_key[W1 - 1] >> tbits;
+        uint64_t cv = ~0ull;  // node that continues from the previous chunk, and its count so far
+        uint32_t ccum = 0;
+        for (uint64_t c0 = s0;; c0 += 32) {
+            const uint64_t rr = c0 + lane;
+            uint64_t key = 0, m = 0;
+            bool act = false;
+            if (rr < R) {
+                key = rec_key[rr];
+                act = rr < W1 || (key >> tbits) == last;
             }
-            cum += c;
+            const unsigned actb = __ballot_sync(kFull, act);
+            if (!actb) break;
+            const uint64_t v = key >> tbits, t = key & tmask;
+            if (act) m = hvals[2ull * rec_val[rr]] & alive[t] & range_mask(t, lo, 0xffffffffu);
+            const uint32_t c = __popcll(m);
+            // inclusive count of v's bits up to this record (runs are contiguous)
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                const uint64_t vo = __shfl_up_sync(kFull, v, o);
+                if (lane >= static_cast<unsigned>(o) && vo == v) incl += y;
+            }
+            if (v == cv) incl += ccum;
+            if (act) {
+                const uint32_t excl = incl - c, need = k - size[v];
+                const bool hit = need == 0 ? run_start(rec_key, rr, tbits) : (excl < need && incl >= need);
+                if (hit) {
+                    const uint64_t p = t * 64 + nth_set_bit(m, static_cast<int>(need - excl - 1));
+                    atomicMin(&ctl->best, (p << 32) | v);
+                }
+            }
+            const int ll = 31 - __clz(actb);
+            cv = __shfl_sync(kFull, v, ll);
+            ccum = __shfl_sync(kFull, incl, ll);
+            if (actb != kFull) break;
         }
     }
 }
 
+// Commit of lanes [lo, hi]: size[v] += the committed uncovered lane bits of
+// v's records, and per lane the number of nodes it reaches (the index
+// segment lengths).  Additive, so one thread per record.
 __global__ void k_commit_count(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                                const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size,
                                unsigned long long *lane_cnt, DevCtl *ctl) {
@@ -223,21 +262,18 @@ __global__ void k_commit_count(const uint64_t *rec_key, const uint32_t *rec_val,
     unsigned long long ins = 0;
     for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
          r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        if (!run_start(rec_key, r, tbits)) continue;
-        const uint64_t v = rec_key[r] >> tbits;
-        uint32_t add = 0;
-        for (uint64_t rr = r; rr < R && (rec_key[rr] >> tbits) == v; rr++) {
-            const uint64_t t = rec_key[rr] & tmask;
-            uint64_t m = hvals[2ull * rec_val[rr]] & alive[t] & range_mask(t, lo, hi);
-            add += __popcll(m);
-            while (m) {
-                int j = __ffsll(m) - 1;
-                m &= m - 1;
-                atomicAdd(&lane_cnt[t * 64 + j], 1ull);
-            }
+        const uint64_t key = rec_key[r];
+        const uint64_t t = key & tmask;
+        uint64_t m = hvals[2ull * rec_val[r]] & alive[t] & range_mask(t, lo, hi);
+        if (!m) continue;
+        const uint32_t c = __popcll(m);
+        atomicAdd(&size[key >> tbits], c);
+        ins += c;
+        while (m) {
+            const int j = __ffsll(m) - 1;
+            m &= m - 1;
+            atomicAdd(&lane_cnt[t * 64 + j], 1ull);
         }
-        if (add) size[v] += add;
-        ins += add;
     }
     warp_add(&ctl->stats[kStInsert], ins);
 }
