@@ -280,9 +280,10 @@ __global__ void k_commit_count(const uint64_t *rec_key, const uint32_t *rec_val,
 
 __global__ void k_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                                  const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi,
-                                 const uint64_t *lane_off, uint32_t *lane_fill, uint64_t idx_base,
+                                 const uint64_t *lane_off, uint32_t *lane_fill, const uint64_t *idx_ctr,
                                  uint32_t *idx_nodes) {
     const uint64_t tmask = (1ull << tbits) - 1;
+    const uint64_t idx_base = idx_ctr[0];
     for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
          r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         const uint64_t v = rec_key[r] >> tbits;
@@ -299,8 +300,9 @@ __global__ void k_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_va
 }
 
 __global__ void k_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32_t hi, const uint64_t *lane_cnt,
-                                  const uint64_t *lane_off, uint64_t idx_base, uint64_t *seg_start,
+                                  const uint64_t *lane_off, const uint64_t *idx_ctr, uint64_t *seg_start,
                                   uint32_t *seg_len) {
+    const uint64_t idx_base = idx_ctr[0];
     for (uint64_t j = lo + blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; j <= hi;
          j += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         uint64_t c = lane_cnt[j];
@@ -310,6 +312,13 @@ __global__ void k_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32
             seg_len[pr] = static_cast<uint32_t>(c);
         }
     }
+}
+
+// After a commit of `total` index entries: idx_ctr[1] = the commit's first
+// entry, idx_ctr[0] = the next free one.
+__global__ void k_idx_advance(uint64_t *idx_ctr, const unsigned long long *total) {
+    idx_ctr[1] = idx_ctr[0];
+    idx_ctr[0] += *total;
 }
 
 __global__ void k_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, uint32_t l, const uint64_t *covered,
@@ -325,9 +334,9 @@ __global__ void k_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, u
 
 // Section 4.3.2: add delta to the size of every node in the committed index
 // list of lane p (each node appears once in a lane's list).
-__global__ void k_lane_size_add(const uint32_t *idx_nodes, uint64_t idx_base, const uint64_t *lane_off,
+__global__ void k_lane_size_add(const uint32_t *idx_nodes, const uint64_t *idx_base, const uint64_t *lane_off,
                                 const uint64_t *lane_cnt, uint32_t p, uint32_t *size, int delta) {
-    const uint64_t off = idx_base + lane_off[p], cnt = lane_cnt[p];
+    const uint64_t off = *idx_base + lane_off[p], cnt = lane_cnt[p];
     for (uint64_t j = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; j < cnt;
          j += static_cast<uint64_t>(gridDim.x) * blockDim.x)
         size[idx_nodes[off + j]] += static_cast<uint32_t>(delta);
@@ -404,19 +413,19 @@ cudaError_t launch_commit_count(const uint64_t *rec_key, const uint32_t *rec_val
 }
 cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                                   const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi,
-                                  const uint64_t *lane_off, uint32_t *lane_fill, uint64_t idx_base,
+                                  const uint64_t *lane_off, uint32_t *lane_fill, const uint64_t *idx_ctr,
                                   uint32_t *idx_nodes, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
     note_launch();
     k_commit_scatter<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, hi, lane_off,
-                                                      lane_fill, idx_base, idx_nodes);
+                                                      lane_fill, idx_ctr, idx_nodes);
     return cudaGetLastError();
 }
 cudaError_t launch_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32_t hi, const uint64_t *lane_cnt,
-                                   const uint64_t *lane_off, uint64_t idx_base, uint64_t *seg_start,
+                                   const uint64_t *lane_off, const uint64_t *idx_ctr, uint64_t *seg_start,
                                    uint32_t *seg_len, cudaStream_t s) {
     note_launch();
-    k_commit_segments<<<grid_for(hi - lo + 1, 256), 256, 0, s>>>(lane_pair, lo, hi, lane_cnt, lane_off, idx_base,
+    k_commit_segments<<<grid_for(hi - lo + 1, 256), 256, 0, s>>>(lane_pair, lo, hi, lane_cnt, lane_off, idx_ctr,
                                                                  seg_start, seg_len);
     return cudaGetLastError();
 }
@@ -432,7 +441,7 @@ cudaError_t launch_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl, cu
     k_argmax_size<<<grid_for(n, 256), 256, 0, s>>>(size, n, ctl);
     return cudaGetLastError();
 }
-cudaError_t launch_second_size(const uint32_t *idx_nodes, uint64_t idx_base, const uint64_t *lane_off,
+cudaError_t launch_second_size(const uint32_t *idx_nodes, const uint64_t *idx_base, const uint64_t *lane_off,
                                const uint64_t *lane_cnt, uint32_t p, uint32_t *size, uint32_t n, uint32_t x,
                                uint32_t *out, cudaStream_t s) {
     // the stop lane's list holds at most n nodes (its length is on the device)
@@ -443,6 +452,11 @@ cudaError_t launch_second_size(const uint32_t *idx_nodes, uint64_t idx_base, con
     k_max_size_except<<<grid_for(n, 256), 256, 0, s>>>(size, n, x, out);
     note_launch();
     k_lane_size_add<<<g, 256, 0, s>>>(idx_nodes, idx_base, lane_off, lane_cnt, p, size, 1);
+    return cudaGetLastError();
+}
+cudaError_t launch_idx_advance(uint64_t *idx_ctr, const unsigned long long *total, cudaStream_t s) {
+    note_launch();
+    k_idx_advance<<<1, 1, 0, s>>>(idx_ctr, total);
     return cudaGetLastError();
 }
 cudaError_t launch_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl, cudaStream_t s) {

@@ -90,7 +90,12 @@ struct skim_ctx {
     uint64_t *covered = nullptr, *seg_start = nullptr, *pend_trav = nullptr, *pend_erase = nullptr;
     uint32_t *size = nullptr, *seg_len = nullptr, *idx = nullptr;
     uint8_t *chosen = nullptr;
-    uint64_t idx_cap = 0, idx_used = 0;
+    uint64_t idx_cap = 0;
+    // inverted index fill: on the device [0] entries used, [1] first entry of
+    // the last commit; on the host an upper bound of [0] (the visit bits of
+    // the SKIM batches so far), which sizes the index without a read-back
+    uint64_t *idx_ctr = nullptr;
+    uint64_t idx_bound = 0, vis_seen = 0;
     uint64_t cursor = 0;
     uint32_t nseeds = 0;
     bool batch_active = false;
@@ -365,6 +370,8 @@ constexpr uint64_t kNodeSortDensity = 4;
 // visited-table slots per expected visit record of a batch
 constexpr double kTableSlots = SKIM_TABLE_SLOTS;
 
+int ensure_idx(skim_ctx *c, uint64_t need);
+
 // Buffers of the per-node record placement; the counters start at zero.
 int node_buffers(skim_ctx *c) {
     if (c->ncnt) return SKIM_OK;
@@ -421,6 +428,12 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         return SKIM_OK;
     }
     RC(reset_queue(c, h.q_tail.v));
+    if (!mode_build) {  // SKIM: the batch's commits add at most its visit bits to the index
+        const uint64_t vis = h.stats[kStRevVisits] - c->vis_seen;
+        c->vis_seen = h.stats[kStRevVisits];
+        RC(ensure_idx(c, c->idx_bound + vis));
+        c->idx_bound += vis;
+    }
     const int bits = bitlen(c->n - 1) + static_cast<int>(tbits);
     // records dense over the nodes: place them node by node (one pass over
     // the n node counters); sparse: radix sort over the key bits
@@ -463,6 +476,7 @@ int pull_stats(skim_ctx *c) {
 int reset_stats(skim_ctx *c) {
     CK(c, cudaMemsetAsync(c->ctl->stats, 0, sizeof(c->ctl->stats), c->st));
     std::fill(c->hstats, c->hstats + SKIM_STAT_COUNT, 0);
+    c->vis_seen = 0;
     return SKIM_OK;
 }
 
@@ -486,6 +500,7 @@ int skim_state_init(skim_ctx *c) {
         RC(dalloc(c, &c->chosen, c->n));
         RC(dalloc(c, &c->pend_trav, c->n));
         RC(dalloc(c, &c->pend_erase, c->n));
+        RC(dalloc(c, &c->idx_ctr, 2));
     }
     CK(c, cudaMemsetAsync(c->covered, 0, c->n * sizeof(uint64_t), c->st));
     CK(c, cudaMemsetAsync(c->size, 0, c->n * sizeof(uint32_t), c->st));
@@ -494,7 +509,8 @@ int skim_state_init(skim_ctx *c) {
     CK(c, cudaMemsetAsync(c->pend_trav, 0, c->n * sizeof(uint64_t), c->st));
     CK(c, cudaMemsetAsync(c->pend_erase, 0, c->n * sizeof(uint64_t), c->st));
     if (c->batch_active) RC(clear_batch(c));
-    c->idx_used = 0;
+    CK(c, cudaMemsetAsync(c->idx_ctr, 0, 2 * sizeof(uint64_t), c->st));
+    c->idx_bound = 0;
     c->cursor = 0;
     c->nseeds = 0;
     c->batch_active = false;
@@ -512,8 +528,10 @@ int ensure_idx(skim_ctx *c, uint64_t need) {
     uint64_t cap = std::max<uint64_t>(need + need / 2, 1ull << 22);
     uint32_t *nb = nullptr;
     RC(dalloc(c, &nb, cap));
-    if (c->idx_used) CK(c, cudaMemcpyAsync(nb, c->idx, c->idx_used * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->st));
-    CK(c, cudaStreamSynchronize(c->st));
+    // every committed entry lies below idx_bound (the frees are stream-ordered)
+    if (c->idx && c->idx_bound)
+        CK(c, cudaMemcpyAsync(nb, c->idx, std::min(c->idx_bound, c->idx_cap) * sizeof(uint32_t),
+                              cudaMemcpyDeviceToDevice, c->st));
     dfree(c, c->idx);
     c->idx = nb;
     c->idx_cap = cap;
@@ -521,6 +539,8 @@ int ensure_idx(skim_ctx *c, uint64_t need) {
 }
 
 // Commit lanes [lo, hi] of the active batch: sizes and the inverted index.
+// The index was sized for the whole batch when it was searched, and its fill
+// offset stays on the device, so a commit needs no read-back.
 int commit_lanes(skim_ctx *c, uint32_t lo, uint32_t hi) {
     if (lo > hi) return SKIM_OK;
     const uint32_t cnt = hi - lo + 1;
@@ -529,15 +549,13 @@ int commit_lanes(skim_ctx *c, uint32_t lo, uint32_t hi) {
     KTimer kt(c, SKIM_K_STEP);
     CK(c, launch_commit_count(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, lo, hi, c->size, c->lane_cnt,
                               c->ctl, c->st));
-    CK(c, exclusive_scan_u64(c->lane_cnt + lo, c->lane_off + lo, cnt, reinterpret_cast<uint64_t *>(&c->ctl->total), c->ws, c->st));
-    RC(sync_ctl(c));
-    const uint64_t tot = c->hctl->total;
-    RC(ensure_idx(c, c->idx_used + tot));
+    CK(c, exclusive_scan_u64(c->lane_cnt + lo, c->lane_off + lo, cnt, reinterpret_cast<uint64_t *>(&c->ctl->total),
+                             c->ws, c->st));
     CK(c, launch_commit_scatter(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, lo, hi, c->lane_off,
-                                c->lane_fill, c->idx_used, c->idx, c->st));
-    CK(c, launch_commit_segments(c->spair + c->bp0, lo, hi, c->lane_cnt, c->lane_off, c->idx_used, c->seg_start,
+                                c->lane_fill, c->idx_ctr, c->idx, c->st));
+    CK(c, launch_commit_segments(c->spair + c->bp0, lo, hi, c->lane_cnt, c->lane_off, c->idx_ctr, c->seg_start,
                                  c->seg_len, c->st));
-    c->idx_used += tot;
+    CK(c, launch_idx_advance(c->idx_ctr, &c->ctl->total, c->st));
     return SKIM_OK;
 }
 
@@ -567,12 +585,11 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
             if (best != ~0ull) {
                 const uint32_t p = static_cast<uint32_t>(best >> 32);
                 const uint32_t x = static_cast<uint32_t>(best & 0xffffffffu);
-                const uint64_t idx_base = c->idx_used;
                 RC(commit_lanes(c, c->blo, p));
                 if (c->rec_tau) {
                     CK(c, cudaMemcpyAsync(c->rec_tau + c->rec_j, c->srank + c->bp0 + p, sizeof(uint64_t),
                                           cudaMemcpyDeviceToDevice, c->st));
-                    CK(c, launch_second_size(c->idx, idx_base, c->lane_off, c->lane_cnt, p, c->size, c->n, x,
+                    CK(c, launch_second_size(c->idx, c->idx_ctr + 1, c->lane_off, c->lane_cnt, p, c->size, c->n, x,
                                              c->rec_kp + c->rec_j, c->st));
                 }
                 RC(residual(c, x, cov_out));
@@ -792,7 +809,7 @@ int skim_destroy(skim_ctx *c) {
     dfree(c, c->lcnt); dfree(c, c->full); dfree(c, c->X); dfree(c, c->xlen);
     dfree(c, c->covered); dfree(c, c->seg_start); dfree(c, c->pend_trav); dfree(c, c->pend_erase);
     dfree(c, c->size); dfree(c, c->seg_len); dfree(c, c->idx); dfree(c, c->chosen);
-    dfree(c, c->rec_tau); dfree(c, c->rec_kp);
+    dfree(c, c->rec_tau); dfree(c, c->rec_kp); dfree(c, c->idx_ctr);
     dfree(c, c->rmask); dfree(c, c->fmask); dfree(c, c->loff); dfree(c, c->rlive); dfree(c, c->rrow); dfree(c, c->rev2fwd);
     dfree(c, c->foff); dfree(c, c->flive);
     dfree(c, c->pieces);

@@ -167,18 +167,20 @@ cudaError_t launch_commit_count(const uint64_t *rec_key, const uint32_t *rec_val
                                 uint64_t *lane_cnt, DevCtl *ctl, cudaStream_t s);
 cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
                                   const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi,
-                                  const uint64_t *lane_off, uint32_t *lane_fill, uint64_t idx_base,
+                                  const uint64_t *lane_off, uint32_t *lane_fill, const uint64_t *idx_ctr,
                                   uint32_t *idx_nodes, cudaStream_t s);
 cudaError_t launch_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32_t hi, const uint64_t *lane_cnt,
-                                   const uint64_t *lane_off, uint64_t idx_base, uint64_t *seg_start,
+                                   const uint64_t *lane_off, const uint64_t *idx_ctr, uint64_t *seg_start,
                                    uint32_t *seg_len, cudaStream_t s);
+// idx_ctr[1] = idx_ctr[0]; idx_ctr[0] += *total (the index entries a commit added)
+cudaError_t launch_idx_advance(uint64_t *idx_ctr, const unsigned long long *total, cudaStream_t s);
 cudaError_t launch_refilter(const uint32_t *lane_pair, uint32_t lo, uint32_t B, uint32_t l, const uint64_t *covered,
                             uint64_t *alive, cudaStream_t s);
 cudaError_t launch_argmax_size(const uint32_t *size, uint32_t n, DevCtl *ctl, cudaStream_t s);
 cudaError_t launch_min_unchosen(const uint8_t *chosen, uint32_t n, DevCtl *ctl, cudaStream_t s);
 // Section 4.3.2: k' = max size over v != x with the stop lane p taken out
 // (sizes are restored); atomicMax into *out, which the caller zeroes.
-cudaError_t launch_second_size(const uint32_t *idx_nodes, uint64_t idx_base, const uint64_t *lane_off,
+cudaError_t launch_second_size(const uint32_t *idx_nodes, const uint64_t *idx_base, const uint64_t *lane_off,
                                const uint64_t *lane_cnt, uint32_t p, uint32_t *size, uint32_t n, uint32_t x,
                                uint32_t *out, cudaStream_t s);
 
