@@ -29,18 +29,6 @@ __global__ void k_check_edges(const uint32_t *src, const uint32_t *dst, uint64_t
     }
 }
 
-__global__ void k_degree_count(const uint32_t *idx, uint64_t m, uint64_t *deg) {
-    for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < m;
-         e += static_cast<uint64_t>(gridDim.x) * blockDim.x)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&deg[idx[e]]), 1ull);
-}
-
-__global__ void k_u64_to_u32(const uint64_t *in, uint32_t *out, size_t n) {
-    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<size_t>(gridDim.x) * blockDim.x)
-        out[i] = static_cast<uint32_t>(in[i]);
-}
-
 // Keys for the reverse CSR: (src << 32 | dst).  The input is sorted by
 // (src, dst), so a stable sort on the dst bits alone yields (dst, src) order.
 __global__ void k_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint64_t m, uint64_t *key, uint32_t *val) {
@@ -94,18 +82,6 @@ __global__ void k_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr)
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint32_t d = rptr[v + 1] - rptr[v];
         thr[v] = d ? (~0ull) / d : 0ull;
-    }
-}
-
-__global__ void k_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_t n, uint64_t coin_key, int reverse,
-                              uint64_t *he) {
-    // one warp per row
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
-        for (uint32_t e = ptr[v] + lane; e < ptr[v + 1]; e += 32) {
-            const uint32_t c = col[e];
-            he[e] = reverse ? edge_state(coin_key, c, v) : edge_state(coin_key, v, c);
-        }
     }
 }
 
@@ -303,15 +279,6 @@ __global__ void k_piece_fill(const uint32_t *ptr, const uint32_t *col, const uin
         uint64_t p1 = lane + 32 < l ? off[base + lane + 32] + c[lane + 32] : 0;
         warp_fill(mask, col, e0, e1, p0, p1, live);
     }
-}
-
-__global__ void k_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out) {
-    unsigned long long best = 0;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        best = max(best, static_cast<unsigned long long>(ptr[v + 1] - ptr[v]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_down_sync(kFull, best, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
 }
 
 // ---- rank order ---------------------------------------------------------
@@ -559,17 +526,6 @@ cudaError_t launch_check_edges(const uint32_t *src, const uint32_t *dst, uint64_
     k_check_edges<<<grid_for(m, 256), 256, 0, s>>>(src, dst, m, n, bad);
     return cudaGetLastError();
 }
-cudaError_t launch_degree_count(const uint32_t *idx, uint64_t m, uint64_t *deg, cudaStream_t s) {
-    if (m == 0) return cudaSuccess;
-    note_launch();
-    k_degree_count<<<grid_for(m, 256), 256, 0, s>>>(idx, m, deg);
-    return cudaGetLastError();
-}
-cudaError_t launch_u64_to_u32(const uint64_t *in, uint32_t *out, size_t n, cudaStream_t s) {
-    note_launch();
-    k_u64_to_u32<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
-    return cudaGetLastError();
-}
 cudaError_t launch_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint64_t m, uint64_t *key, uint32_t *val,
                                  cudaStream_t s) {
     if (m == 0) return cudaSuccess;
@@ -599,12 +555,6 @@ cudaError_t launch_edge_states_both(const uint32_t *rcol, const uint32_t *rrow, 
 cudaError_t launch_wc_thresholds(const uint32_t *rptr, uint32_t n, uint64_t *thr, cudaStream_t s) {
     note_launch();
     k_wc_thresholds<<<grid_for(n, 256), 256, 0, s>>>(rptr, n, thr);
-    return cudaGetLastError();
-}
-cudaError_t launch_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_t n, uint64_t coin_key, int reverse,
-                               uint64_t *he, cudaStream_t s) {
-    note_launch();
-    k_edge_states<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(ptr, col, n, coin_key, reverse, he);
     return cudaGetLastError();
 }
 
@@ -656,12 +606,6 @@ cudaError_t launch_live_fill(const uint32_t *ptr, const uint32_t *col, const uin
     k_live_fill<<<grid_for(static_cast<size_t>(n) * 32, 256), 256, 0, s>>>(ptr, col, mask, n, l, off, live);
     note_launch();
     k_piece_fill<<<piece_grid(m), 256, 0, s>>>(ptr, col, mask, l, off, live, P);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out, cudaStream_t s) {
-    note_launch();
-    k_max_degree<<<grid_for(n, 256), 256, 0, s>>>(ptr, n, out);
     return cudaGetLastError();
 }
 

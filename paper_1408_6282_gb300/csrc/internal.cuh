@@ -67,13 +67,11 @@ struct TravArgs {
 // graph.cu
 cudaError_t launch_check_edges(const uint32_t *src, const uint32_t *dst, uint64_t m, uint32_t n, unsigned *bad,
                                cudaStream_t s);
-cudaError_t launch_degree_count(const uint32_t *idx, uint64_t m, uint64_t *deg, cudaStream_t s);
 // ptr[v] = first index with row[index] >= v, for v = 0..n (row sorted)
 cudaError_t launch_row_ptr(const uint32_t *row, uint64_t m, uint32_t n, uint32_t *ptr, cudaStream_t s);
 // rhe[e] = fhe[rev2fwd[e]] = edge_state(coin_key, rcol[e], rrow[e]) over the reverse CSR
 cudaError_t launch_edge_states_both(const uint32_t *rcol, const uint32_t *rrow, const uint32_t *rev2fwd, uint64_t m,
                                     uint64_t coin_key, uint64_t *rhe, uint64_t *fhe, cudaStream_t s);
-cudaError_t launch_u64_to_u32(const uint64_t *in, uint32_t *out, size_t n, cudaStream_t s);
 cudaError_t launch_make_rev_keys(const uint32_t *src, const uint32_t *dst, uint64_t m, uint64_t *key, uint32_t *val,
                                  cudaStream_t s);
 cudaError_t launch_split_rev(const uint64_t *key, const uint32_t *val, uint64_t m, uint32_t *rcol, uint32_t *rrow,
@@ -96,9 +94,6 @@ cudaError_t launch_live_count(const uint32_t *ptr, const uint64_t *mask, uint32_
                               uint64_t *off, void *pieces_ws, cudaStream_t s);
 cudaError_t launch_live_fill(const uint32_t *ptr, const uint32_t *col, const uint64_t *mask, uint32_t n, uint64_t m,
                              uint32_t l, const uint64_t *off, uint32_t *live, void *pieces_ws, cudaStream_t s);
-cudaError_t launch_edge_states(const uint32_t *ptr, const uint32_t *col, uint32_t n, uint64_t coin_key, int reverse,
-                               uint64_t *he, cudaStream_t s);
-cudaError_t launch_max_degree(const uint32_t *ptr, uint32_t n, unsigned long long *out, cudaStream_t s);
 
 // Rank order of all pairs: bucket by the top bits, then sort each bucket.
 // rank of pair x = v*l+i is fmix(rank_key + G*x), or fmix(rbase[v] + G*i)
@@ -215,6 +210,5 @@ cudaError_t launch_query_multi(const uint64_t *X, const uint32_t *xlen, uint32_t
                                const uint32_t *seeds, const uint64_t *offsets, const uint64_t *table_off,
                                const uint64_t *chunk_off, uint32_t q, uint64_t total_slots, uint64_t total_seeds,
                                uint32_t total_chunks, const QueryScratch &qs, double *out, cudaStream_t s);
-
 
 }  // namespace skim
