@@ -17,7 +17,6 @@
 // and the inverted index), the rest stay valid for the next step because a
 // search from an uncovered pair never meets a covered node.
 #include "internal.cuh"
-#include "prims.cuh"
 
 namespace skim {
 
