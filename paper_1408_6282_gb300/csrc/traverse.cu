@@ -481,7 +481,7 @@ SKIM_DEV Desc shfl_desc(const Desc &d, int src) {
 #define SKIM_UNROLL 1
 #endif
 #ifndef SKIM_TRAV_MIN_BLOCKS
-#define SKIM_TRAV_MIN_BLOCKS 4
+#define SKIM_TRAV_MIN_BLOCKS 3
 #endif
 constexpr int kUnroll = SKIM_UNROLL;  // edges per lane per step: independent hash chains
 
