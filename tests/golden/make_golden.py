@@ -11,6 +11,13 @@ For a named workload this runs the oracle once and stores, in
 No value here comes from the GPU path.
 
 usage: python tests/golden/make_golden.py WORKLOAD [--skip-sketches] [--skip-skim]
+       python tests/golden/make_golden.py batched256 [--jobs J]
+
+``batched256`` is the many-graph workload: 256 R-MAT graphs (scale uniform in
+10..16, edge factor uniform in 8..32), trivalency probabilities, l = 64,
+k = 32, every graph with keys of its own.  For each graph the oracle builds its
+sketches alone and the file stores the graph's digest, the sketch digest and
+the oracle's counters (``batched256_trivalency.json``).
 """
 from __future__ import annotations
 
@@ -49,7 +56,42 @@ def query_sets(w: synth.Workload, n: int, count: int = 24):
     return [synth.uniform_seed_set(n, int(s), ks.query, q).tolist() for q, s in enumerate(sizes)]
 
 
+BATCHED_L, BATCHED_K, BATCHED_MODEL = 64, 32, 2
+
+
+def _batched_one(spec):
+    scale, ef, key = spec
+    g = synth.rmat(scale, ef, key)
+    ks = synth.Keys.from_seed(key)
+    pb = oracle.Problem(g.n, g.src, g.dst, BATCHED_L, BATCHED_K, BATCHED_MODEL, 0.0, ks.coin, ks.rank, ks.prob)
+    t = time.time()
+    x, ln, cnt = oracle.build_sketches(pb)
+    return {"scale": scale, "edge_factor": ef, "key": str(key), "n": g.n, "m": g.m, "graph_sha256": g.digest(),
+            "sketch_sha256": sketch_digest(x, ln), "counters": cnt, "oracle_seconds": time.time() - t}
+
+
+def batched_main(jobs: int):
+    import multiprocessing as mp
+    specs = synth.batched_graph_specs(256)
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(jobs) as pool:
+        graphs = pool.map(_batched_one, specs, chunksize=1)
+    res = {"workload": "batched256_trivalency", "graphs": len(specs), "l": BATCHED_L, "k": BATCHED_K,
+           "prob_model": BATCHED_MODEL, "spec": "synth.batched_graph_specs(256); keys synth.Keys.from_seed(key)",
+           "per_graph": graphs, "oracle_seconds": sum(g["oracle_seconds"] for g in graphs)}
+    out_path = os.path.join(HERE, "batched256_trivalency.json")
+    json.dump(res, open(out_path + ".tmp", "w"), indent=1)
+    os.replace(out_path + ".tmp", out_path)
+    print(f"[batched256] wrote {out_path} ({time.time() - t0:.1f}s wall)", flush=True)
+
+
 def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "batched256":
+        ap = argparse.ArgumentParser()
+        ap.add_argument("workload")
+        ap.add_argument("--jobs", type=int, default=max(1, (os.cpu_count() or 2) - 2))
+        batched_main(ap.parse_args().jobs)
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("workload", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--skip-sketches", action="store_true")
