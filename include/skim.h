@@ -141,8 +141,17 @@ int skim_rank_order(skim_ctx *ctx);
  * time it.  Restarts SKIM (as skim_greedy_reset); sketches are unaffected (the
  * coins do not change).  The IC model (SKIM_RANKS_IC_MODEL) has an instance
  * per rank position and draws coins during the searches instead, as does a
- * context with 2^32 or more live (edge, instance) pairs. */
+ * context with 2^31 or more live (edge, instance) pairs. */
 int skim_instances(skim_ctx *ctx);
+
+/* Choose how searches draw the live edges (Section 2).  on = 1 (the default):
+ * walk the materialised live rows of skim_instances where they exist.
+ * on = 0: evaluate every edge's coin for the lanes that reach it during the
+ * search (the hash above; no instance is stored), as the IC model and contexts
+ * with 2^31 or more live pairs always do.  Both give bit-identical sketches,
+ * seeds and coverages.  Takes effect at the next build or SKIM call and
+ * restarts SKIM (as skim_greedy_reset). */
+int skim_set_live_rows(skim_ctx *ctx, int on);
 
 /* live_pairs: live (edge, instance) pairs of the last skim_instances;
  * materialised: 1 if searches use the materialised instances (host outputs). */
@@ -158,6 +167,12 @@ int skim_build_sketches(skim_ctx *ctx);
  * n*k uint64), len_out[v] = |X_v| (n uint32).  out_on_device selects the
  * memory kind of both outputs.  SKIM_ENOTBUILT before skim_build_sketches(). */
 int skim_get_sketches(skim_ctx *ctx, uint64_t *x_out, uint32_t *len_out, int out_on_device);
+
+/* One node's sketch (Eq. combinedrs): out_k[j] = j-th smallest rank of X_v for
+ * j < *out_len (out_k (host) must hold k entries; entries past *out_len are
+ * left untouched), *out_len = |X_v| <= k (host).
+ * Errors: SKIM_EINVAL (null pointer, v >= n), SKIM_ENOTBUILT. */
+int skim_get_sketch(skim_ctx *ctx, uint32_t v, uint64_t *out_k, uint32_t *out_len);
 
 /* Device pointers to the resident sketches (valid until the next build or
  * destroy), for callers that keep them on the GPU. */
@@ -287,6 +302,14 @@ int skim_set_timing(skim_ctx *ctx, int on);
 int skim_kernel_launches(uint64_t *out);
 int skim_kernel_times(skim_ctx *ctx, double *ms_out, uint64_t *launches_out, uint32_t count, int reset);
 
+/* Bound of every device-side wait of this context's searches: a warp that
+ * sees no progress for `ns` nanoseconds (default 2e9) gives up, every warp of
+ * the search then returns, and the call reports SKIM_ETIMEOUT (the context
+ * is then unusable; destroy it).  A short limit makes the waits give up on
+ * purpose, which is how failure handling is tested.  Errors: SKIM_EINVAL
+ * (null context, ns = 0). */
+int skim_set_wait_limit_ns(skim_ctx *ctx, uint64_t ns);
+
 /* Shape of a context: nodes n, sketch size k, instances l (host outputs). */
 int skim_context_shape(skim_ctx *ctx, uint32_t *n, uint32_t *k, uint32_t *l);
 
@@ -337,19 +360,29 @@ int skim_server_stop(skim_server *srv);
  *   x_dev, len_dev  sketches in device memory, as skim_get_sketches lays them
  *                   out (n*k ranks row-major, n lengths), e.g. from
  *                   skim_sketch_pointers();
+ *   rank_mode       SKIM_RANKS_* of the context the sketches came from: a
+ *                   threshold h reads as in skim_oracle_query (uniform: 2^64/h
+ *                   per rank, divided by l; permutation: (n*l-1)/h, divided
+ *                   by l; IC model: n/h, nothing for a sketch that is not
+ *                   full, l must be 1);
  *   seeds_dev       n_seeds node ids in device memory (duplicates allowed);
  *   est_dev         one double in device memory; receives the estimate, or a
  *                   quiet NaN if a seed id is >= n.
  * Limit: 2*n_seeds*(k-1)+2 <= 2^18 (n_seeds <= 2080 for k = 64); larger
  * queries return SKIM_ERANGE.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls on a device
- * share the array: calls whose work overlaps on the GPU (other streams,
- * other host threads) race and must be serialised by the caller.
- * Errors: SKIM_EINVAL (null pointer, k or l out of range), SKIM_ERANGE,
- * SKIM_ECUDA. */
+ * array's device address (cudaGetSymbolAddress) with that device current and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture, and do not use this entry after cudaDeviceReset() on that
+ * device (the kept address would be stale).  All calls on a device share the
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  A CUDA error already
+ * pending on the calling thread is left in place and reported as SKIM_ECUDA
+ * without a launch.
+ * Errors: SKIM_EINVAL (null pointer, k, l or rank_mode out of range),
+ * SKIM_ERANGE, SKIM_ECUDA. */
 int skim_union_estimate_static(const uint64_t *x_dev, const uint32_t *len_dev, uint32_t n, uint32_t k, uint32_t l,
-                               const uint32_t *seeds_dev, uint32_t n_seeds, double *est_dev, void *stream);
+                               uint32_t rank_mode, const uint32_t *seeds_dev, uint32_t n_seeds, double *est_dev,
+                               void *stream);
 
 int skim_destroy(skim_ctx *ctx);
 

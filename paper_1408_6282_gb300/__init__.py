@@ -61,6 +61,9 @@ def load():
     lib.skim_build_sketches.argtypes = [vp]
     lib.skim_get_sketches.argtypes = [vp, vp, vp, C.c_int]
     lib.skim_sketch_pointers.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
+    lib.skim_get_sketch.argtypes = [vp, u32, vp, vp]
+    lib.skim_set_wait_limit_ns.argtypes = [vp, u64]
+    lib.skim_set_live_rows.argtypes = [vp, C.c_int]
     lib.skim_greedy.argtypes = [vp, u32, vp, vp]
     lib.skim_greedy_reset.argtypes = [vp]
     lib.skim_greedy_ex.argtypes = [vp, u32, vp, vp, vp, vp]
@@ -77,7 +80,7 @@ def load():
     lib.skim_set_timing.argtypes = [vp, C.c_int]
     lib.skim_kernel_times.argtypes = [vp, vp, vp, u32, C.c_int]
     lib.skim_kernel_launches.argtypes = [vp]
-    lib.skim_union_estimate_static.argtypes = [vp, vp, u32, u32, u32, vp, u32, vp, vp]
+    lib.skim_union_estimate_static.argtypes = [vp, vp, u32, u32, u32, u32, vp, u32, vp, vp]
     lib.skim_context_shape.argtypes = [vp, vp, vp, vp]
     lib.skim_create_batch.argtypes = [vp, vp, u32, vp, C.POINTER(vp)]
     lib.skim_autotune_batch_lanes.argtypes = [vp, vp, u32, vp, vp]
@@ -154,6 +157,21 @@ def skim_get_sketches(ctx: int, x_out, len_out, out_on_device: int = 0):
     _check(load().skim_get_sketches(ctx, _ptr(x_out), _ptr(len_out), out_on_device), "skim_get_sketches")
 
 
+def skim_get_sketch(ctx: int, v: int, out_k: np.ndarray) -> int:
+    """X_v into out_k (host uint64, >= k entries); returns |X_v|."""
+    ln = np.zeros(1, np.uint32)
+    _check(load().skim_get_sketch(ctx, v, _ptr(out_k), _ptr(ln)), "skim_get_sketch")
+    return int(ln[0])
+
+
+def skim_set_wait_limit_ns(ctx: int, ns: int):
+    _check(load().skim_set_wait_limit_ns(ctx, ns), "skim_set_wait_limit_ns")
+
+
+def skim_set_live_rows(ctx: int, on: bool):
+    _check(load().skim_set_live_rows(ctx, 1 if on else 0), "skim_set_live_rows")
+
+
 def skim_sketch_pointers(ctx: int) -> tuple[int, int]:
     x, ln = C.c_void_p(), C.c_void_p()
     _check(load().skim_sketch_pointers(ctx, C.byref(x), C.byref(ln)), "skim_sketch_pointers")
@@ -225,10 +243,11 @@ def skim_kernel_launches() -> int:
 
 
 def skim_union_estimate_static(x_dev: int, len_dev: int, n: int, k: int, l: int, seeds_dev: int, n_seeds: int,
-                               est_dev: int, stream: int = 0):
-    """Allocation-free query (static scratch); all pointers are device addresses."""
-    _check(load().skim_union_estimate_static(x_dev, len_dev, n, k, l, seeds_dev or None, n_seeds, est_dev,
-                                             stream or None), "skim_union_estimate_static")
+                               est_dev: int, stream: int = 0, rank_mode: int = 0):
+    """Allocation-free query (static scratch); all pointers are device addresses.
+    rank_mode is the SKIM_RANKS_* reading of the context the sketches came from."""
+    _check(load().skim_union_estimate_static(x_dev, len_dev, n, k, l, rank_mode, seeds_dev or None, n_seeds,
+                                             est_dev, stream or None), "skim_union_estimate_static")
 
 
 def skim_server_start(ctx: int, max_inflight: int, scratch_slots: int, streams: int) -> int:
@@ -359,6 +378,18 @@ class Skim:
         ln = np.zeros(self.n, np.uint32)
         skim_get_sketches(self.ctx, x, ln, 0)
         return x, ln
+
+    def sketch(self, v: int) -> np.ndarray:
+        """X_v of one node (ascending ranks)."""
+        out = np.zeros(self.k, np.uint64)
+        return out[: skim_get_sketch(self.ctx, v, out)]
+
+    def set_live_rows(self, on: bool):
+        """Walk materialised live rows (True) or hash coins during the search (False)."""
+        skim_set_live_rows(self.ctx, on)
+
+    def set_wait_limit_ns(self, ns: int):
+        skim_set_wait_limit_ns(self.ctx, ns)
 
     def greedy(self, n_seeds: int) -> tuple[np.ndarray, np.ndarray]:
         seeds = np.zeros(max(1, n_seeds), np.uint32)

@@ -66,7 +66,7 @@ SKIM_DEV bool run_start(const uint64_t *rec_key, uint64_t r, uint32_t tbits) {
 // One step: offer `has` of node v at batch lane ln (one per warp lane).
 SKIM_DEV void accept_step(bool has, uint32_t v, uint64_t ln, const uint8_t *__restrict__ lane_inst,
                           const uint64_t *__restrict__ lane_rank, uint32_t l, uint32_t k, uint8_t *lcnt,
-                          uint64_t *full, uint64_t *X, uint32_t *xlen, unsigned long long &ins) {
+                          uint64_t *full, uint32_t *row_flag, uint64_t *X, uint32_t *xlen, unsigned long long &ins) {
     const uint32_t lane = threadIdx.x & 31;
     uint32_t i = 0, lc0 = 0, len0 = 0;
     if (has) {
@@ -89,7 +89,10 @@ SKIM_DEV void accept_step(bool has, uint32_t v, uint64_t ln, const uint8_t *__re
     if (has && rho == 0 && lc0 < k) {  // one lane per (v, i)
         const uint32_t c = min(k, lc0 + __popc(pvi));
         lcnt[static_cast<uint64_t>(v) * l + i] = static_cast<uint8_t>(c);
-        if (c == k) atomicOr(reinterpret_cast<unsigned long long *>(&full[v]), 1ull << i);
+        if (c == k) {
+            atomicOr(reinterpret_cast<unsigned long long *>(&full[v]), 1ull << i);
+            if (row_flag) atomicOr(&row_flag[static_cast<uint64_t>(v) * l + i], kRowFull);
+        }
     }
     if (has && (pv & lanemask_lt()) == 0) {  // one lane per v
         const uint32_t len = min(k, len0 + __popc(ab & pv));
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(256)
     k_accept(const uint64_t *__restrict__ rec_key, const uint32_t *__restrict__ rec_val,
              const uint64_t *__restrict__ hvals, uint64_t R, uint32_t tbits,
              const uint8_t *__restrict__ lane_inst, const uint64_t *__restrict__ lane_rank, uint32_t l, uint32_t k,
-             uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl) {
+             uint8_t *lcnt, uint64_t *full, uint32_t *row_flag, uint64_t *X, uint32_t *xlen, DevCtl *ctl) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t tmask = (1ull << tbits) - 1;
     unsigned long long ins = 0;
@@ -134,8 +137,8 @@ __global__ void __launch_bounds__(256)
             if (!__any_sync(kFull, __popcll(m) > 1)) {
                 // one offer per record (the common case)
                 const bool has = m != 0;
-                accept_step(has, vr, tr * 64 + (has ? __ffsll(m) - 1 : 0), lane_inst, lane_rank, l, k, lcnt, full, X,
-                            xlen, ins);
+                accept_step(has, vr, tr * 64 + (has ? __ffsll(m) - 1 : 0), lane_inst, lane_rank, l, k, lcnt, full,
+                            row_flag, X, xlen, ins);
             } else {
                 // offer o is bit (o - pre_s) of record s with pre_s <= o < pre_s + cnt_s
                 const uint32_t cnt = __popcll(m);
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(256)
                         for (uint32_t skip = o - ps; skip; skip--) x &= x - 1;
                         ln = ts * 64 + (__ffsll(x) - 1);
                     }
-                    accept_step(has, vs, ln, lane_inst, lane_rank, l, k, lcnt, full, X, xlen, ins);
+                    accept_step(has, vs, ln, lane_inst, lane_rank, l, k, lcnt, full, row_flag, X, xlen, ins);
                 }
             }
             if (actb != kFull) break;
@@ -172,14 +175,6 @@ __global__ void __launch_bounds__(256)
     }
     warp_add(&ctl->stats[kStInsert], ins);
 }
-
-// every slot of the visited table empty (16-byte slots: key all ones, bits 0)
-__global__ void k_table_init(uint64_t *table, uint64_t slots) {
-    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < slots;
-         i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
-        reinterpret_cast<ulonglong2 *>(table)[i] = make_ulonglong2(kEmptyKey, 0ull);
-}
-
 
 // lanes of word t inside [lo, hi] (inclusive), lo <= hi
 SKIM_DEV uint64_t range_mask(uint64_t t, uint32_t lo, uint32_t hi) {
@@ -381,16 +376,12 @@ cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_ran
 }
 cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, const uint64_t *hvals, uint64_t R,
                           uint32_t tbits, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l, uint32_t k,
-                          uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s) {
+                          uint8_t *lcnt, uint64_t *full, uint32_t *row_flag, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
+                          cudaStream_t s) {
     if (R == 0) return cudaSuccess;
     note_launch();
     k_accept<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, hvals, R, tbits, lane_inst, lane_rank, l, k,
-                                               lcnt, full, X, xlen, ctl);
-    return cudaGetLastError();
-}
-cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s) {
-    note_launch();
-    k_table_init<<<grid_for(slots, 256), 256, 0, s>>>(table, slots);
+                                               lcnt, full, row_flag, X, xlen, ctl);
     return cudaGetLastError();
 }
 cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,

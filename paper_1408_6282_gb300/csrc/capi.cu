@@ -42,7 +42,10 @@ struct skim_ctx {
     // materialised instances (Section 2): per-edge live masks in both CSR
     // orders and the node-major live in-neighbour rows of every (v, i)
     bool mat = false;
-    uint64_t *rmask = nullptr, *fmask = nullptr, *loff = nullptr, *foff = nullptr;
+    bool mat_wanted = true;  // skim_set_live_rows: walk materialised live rows when they exist
+    bool live_ready = false;  // the live rows of both directions are filled
+    uint64_t *rmask = nullptr, *fmask = nullptr;
+    uint32_t *loff = nullptr, *foff = nullptr;  // live-row offsets (kRowFull flags on loff)
     uint32_t *rlive = nullptr, *flive = nullptr;  // live in- and out-neighbour rows
     uint32_t *rrow = nullptr, *rev2fwd = nullptr;  // per reverse CSR edge: head, forward position
     void *pieces = nullptr;                         // workspace of the long-row passes
@@ -61,7 +64,6 @@ struct skim_ctx {
     uint64_t qcap = 0;
     uint64_t *hkeys = nullptr, *hvals = nullptr, *pend = nullptr;
     uint64_t hcap = 0;
-    uint64_t gen = 0;  // generation of the visited table's current keys
     uint64_t *rkey = nullptr, *rkey2 = nullptr;
     uint32_t *rval = nullptr, *rval2 = nullptr;
     uint64_t rcap = 0;
@@ -78,7 +80,7 @@ struct skim_ctx {
     uint64_t *alive = nullptr, *lane_cnt = nullptr, *lane_off = nullptr;
     uint32_t *lane_fill = nullptr;
     uint32_t lane_cap = 0;
-    int grid_rev = 0, grid_fwd = 0;
+    int grid_rev = 0, grid_fwd = 0, grid_ring = 0;
     uint64_t timeout_ns = 2000000000ull;
     // sketches
     uint8_t *lcnt = nullptr;
@@ -287,8 +289,10 @@ int reset_ctl(skim_ctx *c) {
     return SKIM_OK;
 }
 
-// every visited-table slot empty: keys all ones, lane bits zero
-cudaError_t clear_table(skim_ctx *c) { return launch_table_init(c->hkeys, c->hcap, c->st); }
+// the first `slots` visited-table slots empty (key and lane bits zero)
+cudaError_t clear_table(skim_ctx *c, uint64_t slots) {
+    return cudaMemsetAsync(c->hkeys, 0, std::min(slots, c->hcap) * 2 * sizeof(uint64_t), c->st);
+}
 
 // empty the work queue (cursors and slots) before another traversal round
 int reset_queue(skim_ctx *c, uint64_t used) {
@@ -334,12 +338,26 @@ TravArgs base_args(skim_ctx *c, bool forward) {
     return a;
 }
 
-// Run traversal rounds until the queue drains with nothing spilled.
-int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out) {
-    for (;;) {
+// Source lanes of a reverse batch taken by the per-warp-queue search.
+struct RevSources {
+    const uint32_t *lane_pair;
+    uint32_t B;
+    const uint64_t *covered;
+    uint64_t *alive;
+};
+
+// Run traversal rounds until the queue drains with nothing spilled.  With
+// `rs`, the reverse search over materialised rows (per-warp queues) takes the
+// batch's sources in its first round.
+int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out, const RevSources *rs = nullptr) {
+    for (bool first = true;; first = false) {
         {
             KTimer kt(c, forward ? SKIM_K_FWD : SKIM_K_REV);
-            CK(c, launch_traverse(a, forward, forward ? c->grid_fwd : c->grid_rev, c->st));
+            if (rs)
+                CK(c, launch_rev_ring(a, rs->lane_pair, rs->B, c->l, rs->covered, rs->alive, first, c->grid_ring,
+                                      c->st));
+            else
+                CK(c, launch_traverse(a, forward, forward ? c->grid_fwd : c->grid_rev, c->st));
         }
         RC(sync_ctl(c));
         const DevCtl &h = *c->hctl;
@@ -365,10 +383,12 @@ int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out) {
 constexpr uint64_t kNodeSortDensity = 4;
 
 #ifndef SKIM_TABLE_SLOTS
-#define SKIM_TABLE_SLOTS 8
+#define SKIM_TABLE_SLOTS 4
 #endif
-// visited-table slots per expected visit record of a batch
+// visited-table slots per expected visit record of a batch, and per lane when
+// the records per lane are not known yet
 constexpr double kTableSlots = SKIM_TABLE_SLOTS;
+constexpr uint64_t kTableSlotsPerLaneFirst = 32;
 
 int ensure_idx(skim_ctx *c, uint64_t need);
 
@@ -385,10 +405,12 @@ int node_buffers(skim_ctx *c) {
 
 // Reverse search of the batch of ranks [p0, p0+B).  mode_build: Algorithm 2
 // (pruned by local counts); otherwise SKIM (covered sources skipped).
-// est_per_lane: expected visit records per lane (0 = unknown).  The visited
-// table used is a power of two of about 8 slots per expected record (all of
-// it when unknown), so that a batch's table stays small enough for L2.
-// Returns SKIM_OK with *retry set if the batch overflowed its tables.
+// est_per_lane: expected visit records per lane (0 = unknown: 32 slots per
+// lane; negative: the batch is re-run after an overflow, the whole table).
+// The visited table used is a power of two of about 2 slots per expected
+// record, zeroed before the batch: small enough to stay in L2, so that its
+// compare-and-swaps rarely go to DRAM.  Returns SKIM_OK with *retry set if
+// the batch overflowed its tables.
 int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry, double est_per_lane) {
     *retry = false;
     const uint32_t T = (B + 63) / 64;
@@ -399,30 +421,57 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     if (!mode_build) CK(c, cudaMemsetAsync(c->alive, 0, T * sizeof(uint64_t), c->st));
     TravArgs a = base_args(c, false);
     a.tbits = tbits;
-    if (++c->gen >= kGenLimit) {  // generations used up: empty every slot once
-        CK(c, clear_table(c));
-        c->gen = 1;
-    }
-    a.hgen = c->gen << kGenShift;
-    if (est_per_lane > 0) {
-        const uint64_t want = pow2_at_least(std::max<uint64_t>(
-            1ull << 16, static_cast<uint64_t>(kTableSlots * est_per_lane * static_cast<double>(B))));
+    {
+        uint64_t want = c->hcap;
+        if (est_per_lane > 0)
+            want = static_cast<uint64_t>(kTableSlots * est_per_lane * static_cast<double>(B));
+        else if (est_per_lane == 0)
+            want = kTableSlotsPerLaneFirst * static_cast<uint64_t>(B);
+        want = pow2_at_least(std::max<uint64_t>(1ull << 16, want));
         a.hmask = std::min(want, c->hcap) - 1;
+        CK(c, clear_table(c, a.hmask + 1));
     }
     // IC-model searches are never pruned: every lane is its own instance
     a.prune = mode_build && c->rank_mode != SKIM_RANKS_IC_MODEL ? 1 : 0;
-    {
-        KTimer kt(c, SKIM_K_SOURCES);
-        CK(c, launch_rev_sources(a, c->spair + p0, B, c->l, mode_build ? nullptr : c->covered,
-                                 mode_build ? nullptr : c->alive, c->st));
-    }
     uint64_t R = 0;
-    RC(run_traversal(c, a, false, &R));
+#ifndef SKIM_REV_RING
+#define SKIM_REV_RING 1
+#endif
+    // SKIM_TRACE_BATCHES=1 in the environment: one line per batch on stderr
+    // (lanes, records, visits, device time of its searches)
+    static const bool trace = getenv("SKIM_TRACE_BATCHES") != nullptr;
+    cudaEvent_t tr0 = nullptr, tr1 = nullptr;
+    if (trace) {
+        cudaEventCreate(&tr0);
+        cudaEventCreate(&tr1);
+        cudaEventRecord(tr0, c->st);
+    }
+    if (c->mat && SKIM_REV_RING) {
+        const RevSources rs{c->spair + p0, B, mode_build ? nullptr : c->covered, mode_build ? nullptr : c->alive};
+        RC(run_traversal(c, a, false, &R, &rs));
+    } else {
+        {
+            KTimer kt(c, SKIM_K_SOURCES);
+            CK(c, launch_rev_sources(a, c->spair + p0, B, c->l, mode_build ? nullptr : c->covered,
+                                     mode_build ? nullptr : c->alive, c->st));
+        }
+        RC(run_traversal(c, a, false, &R));
+    }
+    if (trace) {
+        cudaEventRecord(tr1, c->st);
+        cudaEventSynchronize(tr1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, tr0, tr1);
+        fprintf(stderr, "skim batch %s p0=%llu B=%u records=%llu visits=%llu ms=%.4f\n", mode_build ? "build" : "skim",
+                static_cast<unsigned long long>(p0), B, static_cast<unsigned long long>(R),
+                static_cast<unsigned long long>(c->hctl->stats[kStRevVisits]), ms);
+        cudaEventDestroy(tr0);
+        cudaEventDestroy(tr1);
+    }
     const DevCtl &h = *c->hctl;
     if (h.err & kErrRetryable) {
         *retry = true;
         RC(reset_queue(c, h.q_tail.v));
-        CK(c, clear_table(c));
         CK(c, cudaMemsetAsync(c->pend, 0, c->hcap * sizeof(uint64_t), c->st));
         c->hstats[SKIM_STAT_RETRIES]++;
         return SKIM_OK;
@@ -633,7 +682,9 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
             if (retry) {
                 if (++c->retry_run > 48) return SKIM_ENOMEM;  // the tables cannot hold even small batches
                 c->skim_B = std::max<uint32_t>(64, B / 2);
-                c->vpl_est *= 4;  // more records than expected: a larger table too
+                // more records than expected: a larger table too (the whole
+                // table when there was no estimate yet)
+                c->vpl_est = c->vpl_est > 0 ? c->vpl_est * 4 : -1.0;
                 continue;
             }
             c->retry_run = 0;
@@ -678,6 +729,7 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
 // not fit 32-bit row offsets.
 int make_instances(skim_ctx *c) {
     c->mat = false;
+    c->live_ready = false;
     if (c->rank_mode == SKIM_RANKS_IC_MODEL) return SKIM_OK;
     KTimer kt(c, SKIM_K_INSTANCES);
     if (!c->loff) {
@@ -687,14 +739,20 @@ int make_instances(skim_ctx *c) {
         RC(dalloc(c, &c->foff, c->nl + 1));
         RC(dalloc_bytes(c, &c->pieces, live_pieces_bytes(c->m)));
     }
+    // counts per (v, i) scanned into 64-bit offsets, kept as 32-bit offsets
+    uint64_t *off = nullptr;
+    RC(dalloc(c, &off, c->nl + 1));
     CK(c, launch_live_masks(c->rrow, c->rcol, c->rhe, c->rtm1, c->rev2fwd, c->cm, c->m, c->l, c->rmask, c->fmask,
                             c->st));
-    CK(c, launch_live_count(c->rptr, c->rmask, c->n, c->m, c->l, c->loff, c->pieces, c->st));
-    CK(c, cudaMemsetAsync(c->loff + c->nl, 0, sizeof(uint64_t), c->st));
-    CK(c, exclusive_scan_u64(c->loff, c->loff, c->nl + 1, nullptr, c->ws, c->st));
-    CK(c, cudaMemcpyAsync(&c->live_total, c->loff + c->nl, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->st));
+    CK(c, launch_live_count(c->rptr, c->rmask, c->n, c->m, c->l, off, c->pieces, c->st));
+    CK(c, cudaMemsetAsync(off + c->nl, 0, sizeof(uint64_t), c->st));
+    CK(c, exclusive_scan_u64(off, off, c->nl + 1, nullptr, c->ws, c->st));
+    CK(c, cudaMemcpyAsync(&c->live_total, off + c->nl, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaStreamSynchronize(c->st));
-    if (c->live_total >= (1ull << 32)) return SKIM_OK;
+    if (c->live_total > kRowMask) {  // offsets would not fit 31 bits: coins are drawn in the searches
+        dfree(c, off);
+        return SKIM_OK;
+    }
     if (c->live_total > c->rlive_cap) {
         dfree(c, c->rlive);
         dfree(c, c->flive);
@@ -703,13 +761,17 @@ int make_instances(skim_ctx *c) {
         RC(dalloc(c, &c->flive, c->live_total));
         c->rlive_cap = c->live_total;
     }
-    CK(c, launch_live_fill(c->rptr, c->rcol, c->rmask, c->n, c->m, c->l, c->loff, c->rlive, c->pieces, c->st));
+    CK(c, launch_live_fill(c->rptr, c->rcol, c->rmask, c->n, c->m, c->l, off, c->rlive, c->pieces, c->st));
+    CK(c, launch_offsets_u32(off, c->nl, c->loff, c->st));
     // the same live pairs by tail: rows of live out-neighbours for the residual
-    CK(c, launch_live_count(c->fptr, c->fmask, c->n, c->m, c->l, c->foff, c->pieces, c->st));
-    CK(c, cudaMemsetAsync(c->foff + c->nl, 0, sizeof(uint64_t), c->st));
-    CK(c, exclusive_scan_u64(c->foff, c->foff, c->nl + 1, nullptr, c->ws, c->st));
-    CK(c, launch_live_fill(c->fptr, c->fcol, c->fmask, c->n, c->m, c->l, c->foff, c->flive, c->pieces, c->st));
-    c->mat = true;
+    CK(c, launch_live_count(c->fptr, c->fmask, c->n, c->m, c->l, off, c->pieces, c->st));
+    CK(c, cudaMemsetAsync(off + c->nl, 0, sizeof(uint64_t), c->st));
+    CK(c, exclusive_scan_u64(off, off, c->nl + 1, nullptr, c->ws, c->st));
+    CK(c, launch_live_fill(c->fptr, c->fcol, c->fmask, c->n, c->m, c->l, off, c->flive, c->pieces, c->st));
+    CK(c, launch_offsets_u32(off, c->nl, c->foff, c->st));
+    dfree(c, off);
+    c->live_ready = true;
+    c->mat = c->mat_wanted;
     return SKIM_OK;
 }
 
@@ -985,7 +1047,7 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         TRY(dalloc(c, &c->hkeys, 2 * c->hcap));
         c->hvals = c->hkeys + 1;
         TRY(dalloc(c, &c->pend, c->hcap));
-        TRYC(clear_table(c));
+        TRYC(clear_table(c, c->hcap));
         TRYC(cudaMemsetAsync(c->pend, 0, c->hcap * sizeof(uint64_t), c->st));
         TRY(dalloc(c, &c->rkey, c->rcap));
         TRY(dalloc(c, &c->rkey2, c->rcap + 1));  // radix sort's alternate keys; node placement's scratch
@@ -999,6 +1061,7 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         TRY(dalloc(c, &c->lane_off, c->lane_cap));
         TRY(dalloc(c, &c->lane_fill, c->lane_cap));
         c->grid_rev = traverse_grid(false);
+        c->grid_ring = rev_ring_grid();
         c->grid_fwd = traverse_grid(true);
         TRYC(cudaStreamSynchronize(c->st));
     }
@@ -1179,6 +1242,7 @@ int skim_build_sketches(skim_ctx *c) {
     }
     CK(c, cudaMemsetAsync(c->lcnt, 0, c->nl, c->st));
     CK(c, cudaMemsetAsync(c->full, 0, c->n * sizeof(uint64_t), c->st));
+    if (c->mat) CK(c, launch_clear_row_flags(c->loff, c->nl, c->st));
     CK(c, cudaMemsetAsync(c->X, 0, static_cast<size_t>(c->n) * c->k * sizeof(uint64_t), c->st));
     CK(c, cudaMemsetAsync(c->xlen, 0, c->n * sizeof(uint32_t), c->st));
     RC(reset_stats(c));
@@ -1194,13 +1258,13 @@ int skim_build_sketches(skim_ctx *c) {
         if (retry) {
             if (b <= 64) return SKIM_ENOMEM;  // even the smallest batch overflows the tables
             B = std::max<uint32_t>(64, b / 4);
-            rpl = 0;  // the whole table for the re-run
+            rpl = -1;  // the whole table for the re-run
             continue;
         }
         {
             KTimer kt(c, SKIM_K_ACCEPT);
             CK(c, launch_accept(c->rkey, c->rval, c->hvals, c->bR, c->btbits, c->lane_inst, c->srank + p0, c->l,
-                                c->k, c->lcnt, c->full, c->X, c->xlen, c->ctl, c->st));
+                                c->k, c->lcnt, c->full, c->mat ? c->loff : nullptr, c->X, c->xlen, c->ctl, c->st));
         }
         const uint64_t recs = c->bR;
         RC(clear_batch(c));
@@ -1231,6 +1295,45 @@ int skim_get_sketches(skim_ctx *c, uint64_t *x_out, uint32_t *len_out, int out_o
     CK(c, cudaMemcpyAsync(x_out, c->X, static_cast<size_t>(c->n) * c->k * sizeof(uint64_t), kind, c->st));
     CK(c, cudaMemcpyAsync(len_out, c->xlen, c->n * sizeof(uint32_t), kind, c->st));
     CK(c, cudaStreamSynchronize(c->st));
+    return SKIM_OK;
+}
+
+int skim_get_sketch(skim_ctx *c, uint32_t v, uint64_t *out_k, uint32_t *out_len) {
+    if (!c || !out_k || !out_len) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    if (!c->built) return SKIM_ENOTBUILT;
+    if (v >= c->n) return SKIM_EINVAL;
+    uint32_t len = 0;
+    CK(c, cudaMemcpyAsync(&len, c->xlen + v, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    if (len > c->k) return fail_cuda(c, cudaErrorIllegalState);
+    if (len)
+        CK(c, cudaMemcpyAsync(out_k, c->X + static_cast<size_t>(v) * c->k, len * sizeof(uint64_t),
+                              cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    *out_len = len;
+    return SKIM_OK;
+}
+
+int skim_set_wait_limit_ns(skim_ctx *c, uint64_t ns) {
+    if (!c || ns == 0) return SKIM_EINVAL;
+    c->timeout_ns = ns;
+    return SKIM_OK;
+}
+
+int skim_set_live_rows(skim_ctx *c, int on) {
+    if (!c) return SKIM_EINVAL;
+    if (c->broken) return SKIM_ECUDA;
+    if (c->batch_active) {
+        RC(commit_lanes(c, c->blo, c->bB - 1));
+        RC(clear_batch(c));
+        c->batch_active = false;
+    }
+    c->mat_wanted = on != 0;
+    // live rows exist only when they were generated (not for the IC model or
+    // 2^31 or more live pairs); turning them on again needs nothing else
+    c->mat = c->mat_wanted && c->live_ready;
+    c->sk_init = false;
     return SKIM_OK;
 }
 

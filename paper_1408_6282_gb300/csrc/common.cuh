@@ -22,12 +22,12 @@ inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_rel
 
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kEmptyKey = ~0ull;
-// Visited-table keys carry the generation of their batch in bits 51..62, so a
-// slot of an earlier batch counts as empty and no batch has to clear the
-// table (node << tbits | word stays below 2^51: node < 2^32, tbits <= 19).
-constexpr int kGenShift = 51;
-constexpr uint64_t kGenMask = 0xFFFull << kGenShift;
-constexpr uint64_t kGenLimit = 0xFFF;  // generations 1 .. kGenLimit - 1, then a full clear
+// Materialised live rows: 32-bit offsets into the row array; the top bit of
+// row r's start (r = v * l + i) says that the instance-local sketch of (v, i)
+// holds k ranks (Algorithm 2's pruning), so one load gives the row and the
+// pruning decision.  Offsets therefore stay below 2^31.
+constexpr uint32_t kRowMask = 0x7FFFFFFFu;
+constexpr uint32_t kRowFull = 0x80000000u;
 // key of the within-chunk node order of permutation ranks: fmix(rank_key ^ salt)
 constexpr uint64_t kPermSalt = 0x7065726d75746531ull;
 constexpr unsigned kFull = 0xffffffffu;
@@ -72,6 +72,10 @@ SKIM_HD uint32_t chunk_edges(uint32_t deg, uint64_t mask) {
     return want > floor_c ? want : floor_c;
 }
 
+// Materialised row items name the lane's instance too: w = inst << 25 |
+// word << 6 | lane bit (word < kMaxWords = 2^19).
+constexpr uint32_t kInstShift = 25;
+
 // Work item of the asynchronous traversals (16 bytes).  Reverse searches:
 // v = node, w = (lane word << 12) | chunk, mask = lanes of that word visiting
 // v.  Residual searches: w = chunk, mask = instances.  Index-erase items:
@@ -99,8 +103,12 @@ struct alignas(128) HotCounter {
 };
 
 // Device control block: queue cursors, counters, flags, reductions.
+// src_next, busy and beat serve the reverse searches with per-warp queues:
+// the next unclaimed source lane of the batch, the warps that hold work, and
+// a progress count that working warps advance now and then.
 struct DevCtl {
     HotCounter q_head, q_tail, q_done, rec_count;
+    HotCounter src_next, busy, beat;
     unsigned long long best;        // SKIM stop candidate: (lane << 32) | node
     unsigned long long ix_cov;      // pairs newly covered by the residual search
     unsigned long long argmax;      // (size << 32) | ~node

@@ -609,6 +609,32 @@ cudaError_t launch_live_fill(const uint32_t *ptr, const uint32_t *col, const uin
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_offsets_u32(const uint64_t *off, uint64_t count, uint32_t *off32) {
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r <= count;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        off32[r] = static_cast<uint32_t>(off[r]);
+}
+__global__ void k_clear_row_flags(uint32_t *off32, uint64_t count) {
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < count;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        off32[r] &= kRowMask;
+}
+}  // namespace
+
+cudaError_t launch_offsets_u32(const uint64_t *off, uint64_t count, uint32_t *off32, cudaStream_t s) {
+    note_launch();
+    k_offsets_u32<<<grid_for(count + 1, 256), 256, 0, s>>>(off, count, off32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_row_flags(uint32_t *off32, uint64_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    note_launch();
+    k_clear_row_flags<<<grid_for(count, 256), 256, 0, s>>>(off32, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_node_graph(const uint32_t *node_off, uint32_t count, uint32_t *node_graph, cudaStream_t s) {
     note_launch();
     k_node_graph<<<count < 4096 ? count : 4096, 256, 0, s>>>(node_off, count, node_graph);

@@ -34,8 +34,7 @@ struct TravArgs {
     // reverse searches (lanes = ranks of a batch)
     uint64_t *hkeys;
     uint64_t *hvals;
-    uint64_t hmask;
-    uint64_t hgen;              // generation of this batch's table keys, already shifted (kGenShift)
+    uint64_t hmask;             // the batch's table prefix (slots - 1), cleared before the batch
     uint64_t *rec_key;
     uint32_t *rec_val;
     uint64_t rcap;
@@ -57,10 +56,11 @@ struct TravArgs {
     uint64_t *pend_trav;        // per node: instances whose expansion was spilled
     uint64_t *pend_erase;       // per node: instances whose index erasure was spilled
     // materialised instances (mat != 0): reverse searches walk the live
-    // in-neighbours of (node v, instance i), col[loff[v*l+i] .. loff[v*l+i+1]);
-    // forward searches test the per-edge live masks lmask (bit i = live in i)
+    // in-neighbours of (node v, instance i), col[loff[v*l+i] .. loff[v*l+i+1])
+    // (offsets masked by kRowMask; kRowFull on a row start marks a full local
+    // sketch), forward searches the live out-neighbours the same way
     int mat;
-    const uint64_t *loff;
+    const uint32_t *loff;
     const uint64_t *lmask;
 };
 
@@ -94,6 +94,10 @@ cudaError_t launch_live_count(const uint32_t *ptr, const uint64_t *mask, uint32_
                               uint64_t *off, void *pieces_ws, cudaStream_t s);
 cudaError_t launch_live_fill(const uint32_t *ptr, const uint32_t *col, const uint64_t *mask, uint32_t n, uint64_t m,
                              uint32_t l, const uint64_t *off, uint32_t *live, void *pieces_ws, cudaStream_t s);
+// off32[r] = off[r] for r <= count (offsets below 2^31; no row flagged full)
+cudaError_t launch_offsets_u32(const uint64_t *off, uint64_t count, uint32_t *off32, cudaStream_t s);
+// clear the full flags (kRowFull) of rows 0 .. count - 1
+cudaError_t launch_clear_row_flags(uint32_t *off32, uint64_t count, cudaStream_t s);
 
 // Rank order of all pairs: bucket by the top bits, then sort each bucket.
 // rank of pair x = v*l+i is fmix(rank_key + G*x), or fmix(rbase[v] + G*i)
@@ -135,6 +139,14 @@ cudaError_t launch_traverse(const TravArgs &a, bool forward, int grid, cudaStrea
 cudaError_t launch_respill_rev(const TravArgs &a, uint64_t R, cudaStream_t s);
 cudaError_t launch_respill_fwd(const TravArgs &a, uint32_t n, cudaStream_t s);
 int traverse_grid(bool forward);  // resident blocks for the persistent traversal
+// Reverse searches over materialised live rows with per-warp queues in shared
+// memory (Algorithms 1 and 2): the batch's source lanes are taken by the
+// kernel itself (sources = false: an earlier launch took them; covered/alive
+// as for launch_rev_sources).  The source cursor DevCtl::src_next must be zero
+// before the first launch of a batch.
+int rev_ring_grid();
+cudaError_t launch_rev_ring(const TravArgs &a, const uint32_t *lane_pair, uint32_t B, uint32_t l,
+                            const uint64_t *covered, uint64_t *alive, bool sources, int grid, cudaStream_t s);
 
 // batch.cu
 cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_rank, uint32_t B, uint32_t l,
@@ -143,10 +155,12 @@ cudaError_t launch_lane_inst(const uint32_t *lane_pair, const uint64_t *lane_ran
 // starts: R + 1 uint32 of scratch; scan_ws: scan workspace for R + 1 entries.
 // Algorithm 2's acceptance of a batch's sorted records; record r's lane bits
 // are hvals[2 * rec_val[r]].
+// row_flag (may be null): live-row offsets whose kRowFull bit is set with the
+// full bit of (v, i).
 cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, const uint64_t *hvals, uint64_t R,
                           uint32_t tbits, const uint8_t *lane_inst, const uint64_t *lane_rank, uint32_t l, uint32_t k,
-                          uint8_t *lcnt, uint64_t *full, uint64_t *X, uint32_t *xlen, DevCtl *ctl, cudaStream_t s);
-cudaError_t launch_table_init(uint64_t *table, uint64_t slots, cudaStream_t s);
+                          uint8_t *lcnt, uint64_t *full, uint32_t *row_flag, uint64_t *X, uint32_t *xlen, DevCtl *ctl,
+                          cudaStream_t s);
 
 // recsort.cu: order a batch's R records by key, node by node.  cnt: n + 1
 // counters, all zero on entry and on return; off: n + 1 node offsets (out);

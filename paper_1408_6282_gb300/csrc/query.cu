@@ -312,7 +312,7 @@ constexpr int kMaxDevices = 64;
 uint64_t *g_static_ptr[kMaxDevices] = {};  // device address of g_static_table, per device
 
 __global__ void __launch_bounds__(kQThreads) k_query_static(const uint64_t *X, const uint32_t *xlen, uint32_t n,
-                                                            uint32_t k, uint32_t l, const uint32_t *seeds,
+                                                            uint32_t k, QueryTerms terms, const uint32_t *seeds,
                                                             uint32_t s, uint64_t *table, uint64_t H, double *out) {
     __shared__ unsigned long long top_tau;
     __shared__ int top_used, bad;
@@ -363,8 +363,14 @@ __global__ void __launch_bounds__(kQThreads) k_query_static(const uint64_t *X, c
     __syncthreads();
     U192 acc{{0, 0, 0}};
     for (uint64_t i = threadIdx.x; i < H; i += blockDim.x)
-        if (tk[i] != kEmptyKey) add192(acc, to_fixed(inv_tau(tv[i])));
-    if (threadIdx.x == 0 && top_used) add192(acc, to_fixed(inv_tau(top_tau)));
+        if (tk[i] != kEmptyKey) {
+            const double v = term_of(terms, tv[i]);
+            if (v != 0.0) add192(acc, to_fixed(v));
+        }
+    if (threadIdx.x == 0 && top_used) {
+        const double v = term_of(terms, top_tau);
+        if (v != 0.0) add192(acc, to_fixed(v));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         U192 other;
@@ -376,7 +382,7 @@ __global__ void __launch_bounds__(kQThreads) k_query_static(const uint64_t *X, c
     if (threadIdx.x == 0) {
         U192 tot{{0, 0, 0}};
         for (int w = 0; w < kQThreads / 32; w++) add192(tot, wsum[w]);
-        out[0] = bad ? __longlong_as_double(0x7ff8000000000000ll) : fixed_to_double(tot) / static_cast<double>(l);
+        out[0] = bad ? __longlong_as_double(0x7ff8000000000000ll) : fixed_to_double(tot) / terms.div;
     }
 }
 
@@ -384,11 +390,18 @@ __global__ void __launch_bounds__(kQThreads) k_query_static(const uint64_t *X, c
 }  // namespace skim
 
 extern "C" int skim_union_estimate_static(const uint64_t *x_dev, const uint32_t *len_dev, uint32_t n, uint32_t k,
-                                          uint32_t l, const uint32_t *seeds_dev, uint32_t n_seeds, double *est_dev,
-                                          void *stream) {
+                                          uint32_t l, uint32_t rank_mode, const uint32_t *seeds_dev,
+                                          uint32_t n_seeds, double *est_dev, void *stream) {
     using namespace skim;
     if (!x_dev || !len_dev || !est_dev || (n_seeds && !seeds_dev)) return SKIM_EINVAL;
     if (n == 0 || k < 2 || k > 255 || l == 0 || l > 64) return SKIM_EINVAL;
+    if (rank_mode > SKIM_RANKS_IC_MODEL || (rank_mode == SKIM_RANKS_IC_MODEL && l != 1)) return SKIM_EINVAL;
+    // the same reading of a threshold as the context queries (query_terms_of)
+    QueryTerms terms{0, 0.0, static_cast<double>(l)};
+    if (rank_mode == SKIM_RANKS_PERMUTATION)
+        terms = QueryTerms{1, static_cast<double>(static_cast<uint64_t>(n) * l - 1), static_cast<double>(l)};
+    else if (rank_mode == SKIM_RANKS_IC_MODEL)
+        terms = QueryTerms{2, static_cast<double>(n), 1.0};
     uint64_t H = 64;
     const uint64_t need = 2ull * n_seeds * (k - 1) + 2;
     while (H < need) H <<= 1;
@@ -408,8 +421,15 @@ extern "C" int skim_union_estimate_static(const uint64_t *x_dev, const uint32_t 
         }
         table = g_static_ptr[dev];
     }
+    // An error left pending by the caller's earlier work is not ours to
+    // consume: report it and leave it in place.
+    if (cudaPeekAtLastError() != cudaSuccess) return SKIM_ECUDA;
     note_launch();
-    k_query_static<<<1, kQThreads, 0, static_cast<cudaStream_t>(stream)>>>(x_dev, len_dev, n, k, l, seeds_dev,
+    k_query_static<<<1, kQThreads, 0, static_cast<cudaStream_t>(stream)>>>(x_dev, len_dev, n, k, terms, seeds_dev,
                                                                            n_seeds, table, H, est_dev);
-    return cudaGetLastError() == cudaSuccess ? SKIM_OK : SKIM_ECUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();  // the launch's own error
+        return SKIM_ECUDA;
+    }
+    return SKIM_OK;
 }

@@ -66,38 +66,54 @@ SKIM_DEV bool cas_slot(uint64_t *slot, uint64_t ek, uint64_t eb, uint64_t nk, ui
 
 // Insert-or-merge of (key, bits) into the visited table.  Returns false if the
 // probe limit is hit.  *old = bits present before, *slot = table slot,
-// *first = this call created the entry.  Slot h keeps its key at hkeys[2h] and
-// its bits at hvals[2h] (hvals = hkeys + 1): both in one 16-byte sector.  Keys
-// carry the batch's generation gen (already shifted); a slot holding another
-// generation's key, or none, is free and is claimed by a 16-byte CAS that sets
-// key and bits together (so no other lane can OR bits into a stale word).
-SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t gen, uint64_t key, uint64_t bits,
-                      uint64_t *old, uint64_t *slot, bool *first) {
-    key |= gen;
-    uint64_t h = fmix(key) & hmask;
+// *first = this call created the entry.  Slot h keeps key + 1 at hkeys[2h] and
+// its bits at hvals[2h] (hvals = hkeys + 1): both in one 16-byte sector.  The
+// batch's part of the table is zeroed before the batch (0 = empty).  The
+// caller has loaded the first slot (h, k, b): an empty slot is claimed by a
+// 16-byte compare-and-swap that writes key and bits together (so no other lane
+// can OR bits into a half-written entry); a slot with this key gets the bits
+// ORed in (nothing to do when they are there already); another key moves the
+// probe on.  Every pass (a lost CAS, a step) counts against the probe limit.
+SKIM_DEV bool hash_or_from(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t key, uint64_t bits,
+                           uint64_t h, uint64_t k, uint64_t b, uint64_t *old, uint64_t *slot, bool *first) {
+    const uint64_t stored = key + 1;
     for (int p = 0; p < kMaxProbe; p++) {
-        uint64_t k, b;
-        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(k), "=l"(b) : "l"(&hkeys[2 * h]) : "memory");
-        if (k != key && (k == kEmptyKey || (k & kGenMask) != gen)) {
+        if (k == 0) {
             uint64_t ok, ob;
-            if (cas_slot(&hkeys[2 * h], k, b, key, bits, &ok, &ob)) {
+            if (cas_slot(&hkeys[2 * h], 0, 0, stored, bits, &ok, &ob)) {
                 *first = true;
                 *slot = h;
                 *old = 0;
                 return true;
             }
-            k = ok;  // someone else changed the slot: look at what is there now
-            if (k != key && (k == kEmptyKey || (k & kGenMask) != gen)) continue;  // still free: try again
+            k = ok;  // someone else claimed it first: look at what it holds now
+            b = ob;
+            continue;
         }
-        if (k == key) {
+        if (k == stored) {
             *first = false;
             *slot = h;
-            *old = atomicOr(reinterpret_cast<unsigned long long *>(&hvals[2 * h]), bits);
+            *old = (b & bits) == bits ? b : atomicOr(reinterpret_cast<unsigned long long *>(&hvals[2 * h]), bits);
             return true;
         }
         h = (h + 1) & hmask;
+        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(k), "=l"(b) : "l"(&hkeys[2 * h]) : "memory");
     }
     return false;
+}
+
+SKIM_DEV uint64_t table_slot(uint64_t key, uint64_t hmask) { return fmix(key) & hmask; }
+
+SKIM_DEV void load_slot(const uint64_t *hkeys, uint64_t h, uint64_t *k, uint64_t *b) {
+    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(*k), "=l"(*b) : "l"(&hkeys[2 * h]) : "memory");
+}
+
+SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t key, uint64_t bits, uint64_t *old,
+                      uint64_t *slot, bool *first) {
+    const uint64_t h = table_slot(key, hmask);
+    uint64_t k, b;
+    load_slot(hkeys, h, &k, &b);
+    return hash_or_from(hkeys, hvals, hmask, key, bits, h, k, b, old, slot, first);
 }
 
 SKIM_DEV uint32_t n_chunks(uint32_t deg) { return (deg + kChunk - 1) / kChunk; }
@@ -168,15 +184,20 @@ SKIM_DEV bool spill_if_full(const TravArgs &A, unsigned long long s, uint32_t ni
 // Live in-neighbour row of (u, lane j of word t) in the materialised instances.
 SKIM_DEV uint32_t live_row_len(const TravArgs &A, uint32_t u, uint32_t t, int j) {
     const uint64_t r = static_cast<uint64_t>(u) * A.l + A.lane_inst[static_cast<size_t>(t) * 64 + j];
-    return static_cast<uint32_t>(A.loff[r + 1] - A.loff[r]);
+    return (A.loff[r + 1] & kRowMask) - (A.loff[r] & kRowMask);
 }
 
 // A materialised reverse item names its row directly: v = first entry of the
-// chunk, w = (word << 6 | lane bit), mask = entries in the chunk (1..kChunk),
-// so that the consumer needs no lookup before it reads the row.
-SKIM_DEV void write_row_items(const TravArgs &A, unsigned long long s, uint64_t b0, uint64_t b1, uint32_t t, int j) {
+// chunk, w = (instance << 25 | word << 6 | lane bit), mask = entries in the
+// chunk (1..kChunk), so that the consumer needs no lookup before it reads the
+// row.  Residual items carry word 0 and the instance as the lane bit.
+SKIM_DEV uint32_t row_item_w(uint32_t t, int j, uint32_t inst) {
+    return (inst << kInstShift) | (t << 6) | static_cast<uint32_t>(j);
+}
+SKIM_DEV void write_row_items(const TravArgs &A, unsigned long long s, uint64_t b0, uint64_t b1, uint32_t t, int j,
+                              uint32_t inst) {
     for (uint64_t e = b0, q = 0; e < b1; e += kChunk, q++)
-        write_item(A, s + q, static_cast<uint32_t>(e), (t << 6) | static_cast<uint32_t>(j),
+        write_item(A, s + q, static_cast<uint32_t>(e), row_item_w(t, j, inst),
                    b1 - e < kChunk ? b1 - e : static_cast<uint64_t>(kChunk));
 }
 
@@ -201,9 +222,10 @@ SKIM_DEV void push_rev(const TravArgs &A, Acc &acc, uint32_t u, uint32_t t, uint
         uint32_t c = 0;
         for (uint64_t m = nb; m; m &= m - 1) {
             const int j = __ffsll(m) - 1;
-            const uint64_t r = static_cast<uint64_t>(u) * A.l + A.lane_inst[static_cast<size_t>(t) * 64 + j];
-            const uint64_t b0 = A.loff[r], b1 = A.loff[r + 1];
-            write_row_items(A, s + c, b0, b1, t, j);
+            const uint32_t inst = A.lane_inst[static_cast<size_t>(t) * 64 + j];
+            const uint64_t r = static_cast<uint64_t>(u) * A.l + inst;
+            const uint64_t b0 = A.loff[r] & kRowMask, b1 = A.loff[r + 1] & kRowMask;
+            write_row_items(A, s + c, b0, b1, t, j, inst);
             c += n_chunks(static_cast<uint32_t>(b1 - b0));
         }
     } else {
@@ -221,7 +243,7 @@ SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32
     if (act && bits) {
         uint64_t old;
         uint64_t key = (static_cast<uint64_t>(u) << A.tbits) | t;
-        if (hash_or(A.hkeys, A.hvals, A.hmask, A.hgen, key, bits, &old, &slot, &first)) {
+        if (hash_or(A.hkeys, A.hvals, A.hmask, key, bits, &old, &slot, &first)) {
             nb = bits & ~old;
         } else {
             atomicOr(&A.ctl->err, kErrHash);
@@ -249,55 +271,76 @@ SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32
     push_rev<MAT>(A, acc, u, t, nb, slot);
 }
 
+// Where a reverse search puts what it finds.  GlobalSink: visit records by
+// one atomic per warp step, row items into the global queue.  RingSink (the
+// per-warp-queue search below): records staged in shared memory, row items
+// into the warp's own ring, the global queue only when the ring is full.
+struct GlobalSink {
+    // Warp-collective: lanes with `first` created table entry (key, slot).
+    SKIM_DEV void record(const TravArgs &A, bool first, uint64_t key, uint64_t slot) {
+        const unsigned ball = __ballot_sync(kFull, first);
+        if (!ball) return;
+        unsigned long long base = 0;
+        if ((threadIdx.x & 31) == 0) base = atomicAdd(&A.ctl->rec_count.v, static_cast<unsigned long long>(__popc(ball)));
+        base = __shfl_sync(kFull, base, 0);
+        if (first) {
+            const unsigned long long r = base + __popc(ball & lanemask_lt());
+            if (r < A.rcap) {
+                A.rec_key[r] = key;
+                A.rec_val[r] = static_cast<uint32_t>(slot);
+            } else {
+                atomicOr(&A.ctl->err, kErrRecords);
+            }
+        }
+    }
+    // Warp-collective: lanes with ni > 0 queue the ni chunks of row [b0, b1)
+    // for lane j of word t (instance inst); a full queue parks the lane bit.
+    SKIM_DEV void rows(const TravArgs &A, Acc &acc, uint32_t ni, uint64_t b0, uint64_t b1, uint32_t t, int j,
+                       uint32_t inst, uint64_t slot) {
+        if (!__any_sync(kFull, ni != 0)) return;
+        const unsigned long long s = reserve_slots(A, acc, ni);
+        if (ni && spill_if_full(A, s, ni)) {
+            atomicOr(reinterpret_cast<unsigned long long *>(&A.pend[slot]), 1ull << j);
+            return;
+        }
+        if (ni) write_row_items(A, s, b0, b1, t, j, inst);
+    }
+};
+
 // Warp-collective, materialised reverse searches: lanes with `act` reach node
 // u for lane j of word t (instance inst).  The row bounds of (u, inst) and the
 // pruning word are loaded together, before the visited-table update.
-SKIM_DEV void emit_rev_mat(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32_t t, int j, uint32_t inst) {
+template <class SK>
+SKIM_DEV void emit_rev_mat(const TravArgs &A, Acc &acc, SK &sk, bool act, uint32_t u, uint32_t t, int j,
+                           uint32_t inst) {
     if (!__any_sync(kFull, act)) return;
-    uint64_t b0 = 0, b1 = 0;
+    const uint64_t key = (static_cast<uint64_t>(u) << A.tbits) | t;
+    uint64_t b0 = 0, b1 = 0, h0 = 0, k0 = 0, v0 = 0;
     if (act) {
+        // the first visited-table slot, and the row of (u, inst) with
+        // Algorithm 2's pruning flag: independent loads, in flight together
+        h0 = table_slot(key, A.hmask);
+        load_slot(A.hkeys, h0, &k0, &v0);
         const uint64_t r = static_cast<uint64_t>(u) * A.l + inst;
-        b0 = A.loff[r];
-        b1 = A.loff[r + 1];
-        if (A.prune && ((A.full[u] >> inst) & 1ull)) act = false;  // Algorithm 2: local sketch full
+        const uint32_t w0 = A.loff[r], w1 = A.loff[r + 1];
+        b0 = w0 & kRowMask;
+        b1 = w1 & kRowMask;
+        if (A.prune && (w0 & kRowFull)) act = false;  // Algorithm 2: local sketch full
     }
     const uint64_t bit = 1ull << j;
     bool fresh = false, first = false;
     uint64_t slot = 0;
     if (act) {
         uint64_t old;
-        const uint64_t key = (static_cast<uint64_t>(u) << A.tbits) | t;
-        if (hash_or(A.hkeys, A.hvals, A.hmask, A.hgen, key, bit, &old, &slot, &first))
+        if (hash_or_from(A.hkeys, A.hvals, A.hmask, key, bit, h0, k0, v0, &old, &slot, &first))
             fresh = !(old & bit);
         else
             atomicOr(&A.ctl->err, kErrHash);
     }
-    {
-        unsigned ball = __ballot_sync(kFull, first);
-        if (ball) {
-            unsigned long long base = 0;
-            if ((threadIdx.x & 31) == 0) base = atomicAdd(&A.ctl->rec_count.v, static_cast<unsigned long long>(__popc(ball)));
-            base = __shfl_sync(kFull, base, 0);
-            if (first) {
-                unsigned long long r = base + __popc(ball & lanemask_lt());
-                if (r < A.rcap) {
-                    A.rec_key[r] = (static_cast<uint64_t>(u) << A.tbits) | t;
-                    A.rec_val[r] = static_cast<uint32_t>(slot);
-                } else {
-                    atomicOr(&A.ctl->err, kErrRecords);
-                }
-            }
-        }
-    }
+    sk.record(A, first, key, slot);
     acc.visits += fresh ? 1 : 0;
     const uint32_t ni = fresh ? n_chunks(static_cast<uint32_t>(b1 - b0)) : 0;
-    if (!__any_sync(kFull, ni != 0)) return;
-    unsigned long long s = reserve_slots(A, acc, ni);
-    if (ni && spill_if_full(A, s, ni)) {
-        atomicOr(reinterpret_cast<unsigned long long *>(&A.pend[slot]), bit);
-        return;
-    }
-    if (ni) write_row_items(A, s, b0, b1, t, j);
+    sk.rows(A, acc, ni, b0, b1, t, j, inst, slot);
 }
 
 // Row bounds, index length and index start of one pair (w, i), loaded ahead
@@ -341,7 +384,7 @@ SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, u
             const int i = __ffsll(m) - 1;
             const uint64_t r = static_cast<uint64_t>(w) * A.l + i;
             const uint64_t b0 = pre.ok ? pre.b0 : A.loff[r], b1 = pre.ok ? pre.b1 : A.loff[r + 1];
-            write_row_items(A, s + c, b0, b1, 0, i);
+            write_row_items(A, s + c, b0, b1, 0, i, 0);
             c += n_chunks(static_cast<uint32_t>(b1 - b0));
         }
     } else if (trav) {
@@ -447,12 +490,12 @@ SKIM_DEV Desc describe(const TravArgs &A, bool have, const Item &it) {
     }
     const uint32_t chunk = it.w & ((1u << kChunkBits) - 1);
     if (MAT) {  // one lane (instance) and a chunk of its row (write_row_items)
-        const uint32_t t = it.w >> 6, j = it.w & 63u;
+        const uint32_t t = (it.w >> 6) & (kMaxWords - 1), j = it.w & 63u;
         d.begin = it.v;
         d.cnt = static_cast<uint32_t>(it.mask);
         d.mask = 1ull << j;
         d.w = t << kChunkBits;
-        d.inst = FWD ? j : A.lane_inst[static_cast<size_t>(t) * 64 + j];
+        d.inst = FWD ? j : it.w >> kInstShift;
         return d;
     }
     const uint32_t e0 = A.ptr[it.v], e1 = A.ptr[it.v + 1];
@@ -544,15 +587,15 @@ SKIM_DEV uint64_t prune_full(const TravArgs &A, const Desc &d, uint32_t u, uint6
 }
 
 // Hand the live results of one step to the emitters (warp-collective).
-template <bool FWD, bool MAT>
-SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, const Desc &d, const uint64_t *lv, const uint32_t *tg) {
+template <bool FWD, bool MAT, class SK>
+SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, SK &sk, const Desc &d, const uint64_t *lv, const uint32_t *tg) {
 #pragma unroll
     for (int q = 0; q < kUnroll; q++) {
         uint64_t live = lv[q];
         if (FWD) {
             emit_fwd<MAT>(A, acc, live != 0, tg[q], live);
         } else if (MAT) {
-            emit_rev_mat(A, acc, live != 0, tg[q], d.w >> kChunkBits, __ffsll(d.mask) - 1, d.inst);
+            emit_rev_mat(A, acc, sk, live != 0, tg[q], d.w >> kChunkBits, __ffsll(d.mask) - 1, d.inst);
         } else {
             if (live && A.prune) live = prune_full(A, d, tg[q], live);
             emit_rev<MAT>(A, acc, live != 0, tg[q], d.w >> kChunkBits, live);
@@ -563,8 +606,8 @@ SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, const Desc &d, const uint64
 // Expand entries [k0, k0 + kUnroll*stride) of item d, entry k at index
 // begin + k for k < cnt (stride = 32 when the warp shares the item, 1 when
 // the lane owns it).  Warp-collective.
-template <bool FWD, bool MAT>
-SKIM_DEV void expand_step(const TravArgs &A, Acc &acc, const Desc &d, uint32_t k0, uint32_t stride, bool own,
+template <bool FWD, bool MAT, class SK>
+SKIM_DEV void expand_step(const TravArgs &A, Acc &acc, SK &sk, const Desc &d, uint32_t k0, uint32_t stride, bool own,
                           const uint64_t *ginst) {
     uint64_t lv[kUnroll];
     uint32_t tg[kUnroll];
@@ -583,14 +626,14 @@ SKIM_DEV void expand_step(const TravArgs &A, Acc &acc, const Desc &d, uint32_t k
     uint64_t anyl = 0;
 #pragma unroll
     for (int q = 0; q < kUnroll; q++) anyl |= lv[q];
-    if (__any_sync(kFull, anyl != 0)) emit_step<FWD, MAT>(A, acc, d, lv, tg);
+    if (__any_sync(kFull, anyl != 0)) emit_step<FWD, MAT>(A, acc, sk, d, lv, tg);
 }
 
 // Expand the items held by the lanes with `have`: an item of 32 or more
 // entries is swept by the whole warp (lane = entry), smaller items by their
 // own lane.
-template <bool FWD, bool MAT>
-SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &it, const uint64_t *ginst) {
+template <bool FWD, bool MAT, class SK>
+SKIM_DEV void process_items(const TravArgs &A, Acc &acc, SK &sk, bool have, const Item &it, const uint64_t *ginst) {
     const int lane = threadIdx.x & 31;
     Desc d = describe<FWD, MAT>(A, have, it);
     if (d.cnt && !d.erase) {
@@ -609,7 +652,7 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
         const Desc b = shfl_desc(d, src);
 #if SKIM_PREFETCH
         if (FWD && b.erase) {  // index-erase items
-            for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD, MAT>(A, acc, b, k0 + lane, 32, true, ginst);
+            for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD, MAT>(A, acc, sk, b, k0 + lane, 32, true, ginst);
         } else {
             // one step ahead: the next edge's column and key are in flight
             // while the current coin is computed
@@ -633,20 +676,20 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, bool have, const Item &
                     lv[0] = edge_live_xh<FWD, MAT>(A, b, b.begin + k, x, h, ginst);
                     tg[0] = x;
                 }
-                if (__any_sync(kFull, lv[0] != 0)) emit_step<FWD, MAT>(A, acc, b, lv, tg);
+                if (__any_sync(kFull, lv[0] != 0)) emit_step<FWD, MAT>(A, acc, sk, b, lv, tg);
                 x = xn;
                 h = hn;
             }
         }
 #else
-        for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD, MAT>(A, acc, b, k0 + lane, 32, true, ginst);
+        for (uint32_t k0 = 0; k0 < b.cnt; k0 += 32 * kUnroll) expand_step<FWD, MAT>(A, acc, sk, b, k0 + lane, 32, true, ginst);
 #endif
     }
     const uint32_t mine = d.cnt < 32 ? d.cnt : 0;
     uint32_t steps = (mine + kUnroll - 1) / kUnroll;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) steps = max(steps, __shfl_xor_sync(kFull, steps, o));
-    for (uint32_t st = 0; st < steps; st++) expand_step<FWD, MAT>(A, acc, d, st * kUnroll, 1, mine != 0, ginst);
+    for (uint32_t st = 0; st < steps; st++) expand_step<FWD, MAT>(A, acc, sk, d, st * kUnroll, 1, mine != 0, ginst);
 }
 
 // Items a warp finishes before it adds them to the shared done count with one
@@ -661,6 +704,7 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
     const int lane = threadIdx.x & 31;
     DevCtl *C = A.ctl;
     Acc acc;
+    GlobalSink gsink;
     uint64_t t_progress = globaltimer();
     unsigned long long seen_done = ld_volatile(&C->q_done.v);
     // items this warp has finished but not yet added to the done count: added
@@ -690,7 +734,7 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
             }
             const unsigned hb = __ballot_sync(kFull, have);
             if (hb) {
-                process_items<FWD, MAT>(A, acc, have, it, ginst);
+                process_items<FWD, MAT>(A, acc, gsink, have, it, ginst);
                 // The drain test reads done, then tail, so the slots reserved
                 // while processing must be counted in tail before these items
                 // count as done.  No fence is needed: lane 0 made every
@@ -758,10 +802,387 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
     flush_acc(A, acc, FWD);
 }
 
+// ---- Reverse searches over materialised live rows, with per-warp queues ----
+//
+// The global queue above costs every item a 16-byte write and read in global
+// memory and an atomic on a cursor that every warp shares.  Here each warp
+// keeps the row items it creates in a ring of its own in shared memory and
+// takes its next items from there, and stages its visit records in shared
+// memory, writing them 32 or more at a time with one atomic.  The batch's
+// first level (its source lanes) is claimed 32 lanes at a time by warps whose
+// ring is empty.  A warp whose ring would overflow hands the step's items to
+// the global queue instead; once the sources are used up a warp keeps at most
+// kRingKeepTail items, so that idle warps share the last, long searches.  An
+// idle warp claims global items only below the queue's reserved end (a slot
+// there is written by a running warp right after its reservation), so no
+// warp waits on a warp that is not running and the grid need not be resident
+// all at once.  A warp leaves once no warp holds work (DevCtl::busy counts the
+// warps that may) and neither the global queue nor the sources have any.
+// Every wait is bounded as above; working warps advance DevCtl::beat now and
+// then, so an idle warp counts a long search as progress.
+#ifndef SKIM_RING_KEEP
+#define SKIM_RING_KEEP 256
+#endif
+#ifndef SKIM_RING_KEEP_TAIL
+#define SKIM_RING_KEEP_TAIL 64
+#endif
+#ifndef SKIM_RING_IDLE_NS
+#define SKIM_RING_IDLE_NS 4096
+#endif
+constexpr uint32_t kRingCap = 256;                      // items per warp ring (a power of two)
+constexpr uint32_t kRingKeep = SKIM_RING_KEEP;          // items a warp keeps while sources remain
+constexpr uint32_t kRingKeepTail = SKIM_RING_KEEP_TAIL; // items a warp keeps once the sources are used up
+constexpr uint32_t kRecStage = 64;                      // staged records per warp
+constexpr int kRingThreads = 256;
+constexpr unsigned kRingIdleMaxNs = SKIM_RING_IDLE_NS;  // longest sleep of an idle warp between polls
+static_assert(kRingKeep <= kRingCap && kRingKeepTail <= kRingCap, "ring limits");
+
+struct RingSink {
+    Item *ring;
+    uint64_t *rk;
+    uint32_t *rs;
+    uint32_t rh, rt, nrec, keep;  // warp-uniform: ring head and tail, staged records, ring limit
+
+    // Warp-collective: write the staged records.
+    SKIM_DEV void flush(const TravArgs &A) {
+        __syncwarp();
+        if (nrec == 0) return;
+        const uint32_t lane = threadIdx.x & 31;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&A.ctl->rec_count.v, static_cast<unsigned long long>(nrec));
+        base = __shfl_sync(kFull, base, 0);
+        for (uint32_t q = lane; q < nrec; q += 32) {
+            const unsigned long long r = base + q;
+            if (r < A.rcap) {
+                A.rec_key[r] = rk[q];
+                A.rec_val[r] = rs[q];
+            } else {
+                atomicOr(&A.ctl->err, kErrRecords);
+            }
+        }
+        __syncwarp();
+        nrec = 0;
+    }
+    // Warp-collective; nrec < 32 on entry, so the stage (64) never overflows.
+    SKIM_DEV void record(const TravArgs &A, bool first, uint64_t key, uint64_t slot) {
+        const unsigned ball = __ballot_sync(kFull, first);
+        if (!ball) return;
+        if (first) {
+            const uint32_t at = nrec + __popc(ball & lanemask_lt());
+            rk[at] = key;
+            rs[at] = static_cast<uint32_t>(slot);
+        }
+        nrec += __popc(ball);
+        if (nrec >= 32) flush(A);
+    }
+    // Warp-collective: the lanes whose items fit below the ring limit (in lane
+    // order) put them in the ring; the others hand theirs to the global queue.
+    SKIM_DEV void rows(const TravArgs &A, Acc &acc, uint32_t ni, uint64_t b0, uint64_t b1, uint32_t t, int j,
+                       uint32_t inst, uint64_t slot) {
+        unsigned long long tot;
+        const unsigned long long ex = warp_excl_scan(ni, &tot);
+        if (tot == 0) return;
+        const uint32_t used = rt - rh;
+        const uint32_t room = keep > used ? keep - used : 0;
+        const bool local = ni && ex + ni <= room;
+        const unsigned lb = __ballot_sync(kFull, local);
+        if (local) {
+            const uint32_t w = row_item_w(t, j, inst);
+            uint32_t at = rt + static_cast<uint32_t>(ex);
+            for (uint64_t e = b0; e < b1; e += kChunk, at++) {
+                Item it;
+                it.v = static_cast<uint32_t>(e);
+                it.w = w;
+                it.mask = b1 - e < kChunk ? b1 - e : static_cast<uint64_t>(kChunk);
+                ring[at & (kRingCap - 1)] = it;
+            }
+        }
+        // the local lanes form a prefix in lane order: their items fill the
+        // ring from rt on without gaps
+        unsigned long long ltot = 0;
+        if (lb) ltot = __shfl_sync(kFull, ex + ni, 31 - __clz(lb));
+        rt += static_cast<uint32_t>(ltot);
+        __syncwarp();
+        if (ltot < tot) GlobalSink{}.rows(A, acc, local ? 0 : ni, b0, b1, t, j, inst, slot);
+    }
+};
+
+// Warp-collective: expand the row items held by the lanes with `have`.  An
+// item of 32 or more entries is swept by the whole warp (lane = entry, the
+// next entry's id loaded while the current one is visited); the entries of
+// the smaller items are spread over the lanes, 32 per round, so that a warp
+// does not loop as long as its longest small row with most lanes idle.
+SKIM_DEV void ring_expand(const TravArgs &A, Acc &acc, RingSink &sk, bool have, const Item &it) {
+    const uint32_t lane = threadIdx.x & 31;
+    const Desc d = describe<false, true>(A, have, it);
+    acc.edges += d.cnt;
+    const uint32_t dj = d.cnt ? static_cast<uint32_t>(__ffsll(d.mask) - 1) : 0;
+    unsigned big = __ballot_sync(kFull, d.cnt >= 32);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const uint32_t bb = __shfl_sync(kFull, d.begin, src), bc = __shfl_sync(kFull, d.cnt, src);
+        const uint32_t bt = __shfl_sync(kFull, d.w, src) >> kChunkBits, bj = __shfl_sync(kFull, dj, src);
+        const uint32_t bi = __shfl_sync(kFull, d.inst, src);
+        uint32_t x = lane < bc ? A.col[bb + lane] : 0;
+        for (uint32_t k0 = 0; k0 < bc; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            const uint32_t xn = k + 32 < bc ? A.col[bb + k + 32] : 0;
+            emit_rev_mat(A, acc, sk, k < bc, x, bt, static_cast<int>(bj), bi);
+            x = xn;
+        }
+    }
+    const uint32_t c = d.cnt < 32 ? d.cnt : 0;
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= static_cast<uint32_t>(o)) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    for (uint32_t g = 0; g < total; g += 32) {
+        const uint32_t o = g + lane;
+        // owner: the first lane whose inclusive count exceeds o
+        uint32_t sl = 0;
+#pragma unroll
+        for (uint32_t step = 16; step > 0; step >>= 1) {
+            const uint32_t v = __shfl_sync(kFull, incl, sl + step - 1);
+            if (v <= o) sl += step;
+        }
+        const uint32_t sb = __shfl_sync(kFull, d.begin, sl), sp = __shfl_sync(kFull, incl - c, sl);
+        const uint32_t st = __shfl_sync(kFull, d.w, sl) >> kChunkBits, sj = __shfl_sync(kFull, dj, sl);
+        const uint32_t si = __shfl_sync(kFull, d.inst, sl);
+        const bool has = o < total;
+        const uint32_t x = has ? A.col[sb + (o - sp)] : 0;
+        emit_rev_mat(A, acc, sk, has, x, st, static_cast<int>(sj), si);
+    }
+}
+
+// Source lanes of a batch for the searches with per-warp queues.
+struct RingSrc {
+    const uint32_t *lane_pair;  // pair id v*l + i of every lane
+    uint32_t B, l;
+    const uint64_t *covered;    // SKIM: covered pairs are skipped (null: Algorithm 2)
+    uint64_t *alive;            // SKIM: per word, the lanes whose source pair is uncovered
+    int sources;                // 0: the sources were taken by an earlier launch
+};
+
+// Warp-collective: claim up to `want` global items (lanes first .. first +
+// got - 1 receive them; `it`/`have` of the other lanes are left as they are).
+// Returns the number claimed (0 if there were none or another warp won).
+SKIM_DEV uint32_t ring_claim_global(const TravArgs &A, uint32_t first, uint32_t want, Item &it, bool &have) {
+    const uint32_t lane = threadIdx.x & 31;
+    unsigned long long h = 0, got = 0;
+    if (lane == 0) {
+        h = ld_volatile(&A.ctl->q_head.v);
+        const unsigned long long t = ld_volatile(&A.ctl->q_tail.v);
+        const unsigned long long lim = t < A.qcap ? t : A.qcap;
+        if (h < lim) {
+            const unsigned long long n = lim - h < want ? lim - h : want;
+            got = atomicCAS(&A.ctl->q_head.v, h, h + n) == h ? n : 0;
+        }
+    }
+    h = __shfl_sync(kFull, h, 0);
+    got = __shfl_sync(kFull, got, 0);
+    if (!got) return 0;
+    bool pending = lane >= first && lane < first + got;
+    const unsigned long long slot = h + (lane - first);
+    const uint64_t t0 = globaltimer();
+    while (__any_sync(kFull, pending)) {
+        if (pending && read_item(A, slot, &it)) {
+            pending = false;
+            have = true;
+        }
+        if (pending && globaltimer() - t0 > A.timeout_ns) {  // a reserved slot is written right away
+            atomicOr(&A.ctl->err, kErrTimeout);
+            pending = false;
+        }
+        if (__any_sync(kFull, pending)) __nanosleep(32);
+    }
+    return static_cast<uint32_t>(got);
+}
+
+// Warp-collective: claim up to 32 global items below lim (head h was read
+// just before); false if another warp claimed them first.
+SKIM_DEV bool ring_take_global(const TravArgs &A, Acc &acc, RingSink &sk, unsigned long long h,
+                               unsigned long long lim) {
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned long long n = lim - h < 32 ? lim - h : 32;
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicCAS(&A.ctl->q_head.v, h, h + n) == h ? n : 0;
+    got = __shfl_sync(kFull, got, 0);
+    if (!got) return false;
+    Item it{0, 0, 0};
+    bool pending = lane < got, have = false;
+    const uint64_t t0 = globaltimer();
+    while (__any_sync(kFull, pending)) {
+        if (pending && read_item(A, h + lane, &it)) {
+            pending = false;
+            have = true;
+        }
+        if (pending && globaltimer() - t0 > A.timeout_ns) {  // a reserved slot is written right away
+            atomicOr(&A.ctl->err, kErrTimeout);
+            pending = false;
+        }
+        if (__any_sync(kFull, pending)) __nanosleep(32);
+    }
+    ring_expand(A, acc, sk, have, it);
+    return true;
+}
+
+// Warp-collective: claim the next 32 source lanes of the batch and visit
+// their nodes (Algorithm 2 prunes a full local sketch; SKIM skips a covered
+// pair and marks the others alive).  False once the sources are used up.
+SKIM_DEV bool ring_take_sources(const TravArgs &A, Acc &acc, RingSink &sk, const RingSrc &S) {
+    const uint32_t lane = threadIdx.x & 31;
+    unsigned long long j0 = 0;
+    if (lane == 0) j0 = atomicAdd(&A.ctl->src_next.v, 32ull);
+    j0 = __shfl_sync(kFull, j0, 0);
+    if (j0 >= S.B) return false;
+    const uint32_t j = static_cast<uint32_t>(j0) + lane;
+    bool act = j < S.B;
+    uint32_t u = 0, i = 0;
+    if (act) {
+        const uint32_t pr = S.lane_pair[j];
+        u = pr / S.l;
+        i = pr % S.l;
+        if (S.covered && ((S.covered[u] >> i) & 1ull)) act = false;
+    }
+    if (S.alive) {
+        const unsigned b = __ballot_sync(kFull, act);
+        if (lane == 0 && b)
+            atomicOr(reinterpret_cast<unsigned long long *>(&S.alive[j0 >> 6]),
+                     static_cast<unsigned long long>(b) << (((j0 >> 5) & 1) * 32));
+    }
+    emit_rev_mat(A, acc, sk, act, u, j >> 6, static_cast<int>(j & 63), i);
+    return true;
+}
+
+#ifndef SKIM_RING_MIN_BLOCKS
+#define SKIM_RING_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(kRingThreads, SKIM_RING_MIN_BLOCKS) k_rev_ring(TravArgs A, RingSrc S) {
+    __shared__ Item s_ring[kRingThreads / 32][kRingCap];
+    __shared__ uint64_t s_rk[kRingThreads / 32][kRecStage];
+    __shared__ uint32_t s_rs[kRingThreads / 32][kRecStage];
+    const uint32_t wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    DevCtl *C = A.ctl;
+    RingSink sk{s_ring[wib], s_rk[wib], s_rs[wib], 0, 0, 0, kRingKeep};
+    Acc acc;
+    bool src_done = !S.sources, busy = false;
+    uint64_t t_progress = globaltimer();
+    unsigned long long seen = 0;
+    unsigned backoff = 32;
+    uint32_t steps = 0;
+    for (;;) {
+        const uint32_t avail = sk.rt - sk.rh;
+        // While sources remain, a ring that holds less than a full step takes
+        // the next 32 source lanes first, so that steps run with full warps.
+        if (avail < 32 && !src_done) {
+            if (!busy) {
+                if (lane == 0) {
+                    atomicAdd(&C->busy.v, 1ull);
+                    __threadfence();  // counted before the claim below
+                }
+                busy = true;
+            }
+            if (ring_take_sources(A, acc, sk, S)) continue;
+            src_done = true;
+        }
+        if (avail) {
+            const uint32_t nt = avail < 32 ? avail : 32;
+            Item it{0, 0, 0};
+            bool have = lane < nt;
+            if (have) it = sk.ring[(sk.rh + lane) & (kRingCap - 1)];
+            __syncwarp();
+            sk.rh += nt;
+            sk.keep = src_done ? kRingKeepTail : kRingKeep;
+            // once the sources are used up, a partial step takes handed-over
+            // items too
+            if (src_done && nt < 32) ring_claim_global(A, nt, 32 - nt, it, have);
+            ring_expand(A, acc, sk, have, it);
+            if ((++steps & 63) == 0 && lane == 0) atomicAdd(&C->beat.v, 1ull);
+            continue;
+        }
+        // the ring is empty and the sources are used up: items other warps
+        // handed over
+        unsigned long long h = 0, t = 0;
+        if (lane == 0) {
+            h = ld_volatile(&C->q_head.v);
+            t = ld_volatile(&C->q_tail.v);
+        }
+        h = __shfl_sync(kFull, h, 0);
+        t = __shfl_sync(kFull, t, 0);
+        const unsigned long long lim = t < A.qcap ? t : A.qcap;
+        if (h < lim) {
+            if (!busy) {
+                if (lane == 0) {
+                    atomicAdd(&C->busy.v, 1ull);
+                    __threadfence();
+                }
+                busy = true;
+            }
+            if (ring_take_global(A, acc, sk, h, lim)) {
+                backoff = 32;
+                continue;
+            }
+        }
+        // nothing to do: records out, no longer counted as holding work
+        sk.flush(A);
+        if (busy) {
+            if (lane == 0) {
+                __threadfence();  // pushes of this warp are visible before the count drops
+                atomicAdd(&C->busy.v, ~0ull);
+            }
+            busy = false;
+        }
+        int fin = 0;
+        if (lane == 0) {
+            __threadfence();
+            const unsigned long long b = ld_volatile(&C->busy.v);
+            __threadfence();
+            const unsigned long long h2 = ld_volatile(&C->q_head.v), t2 = ld_volatile(&C->q_tail.v);
+            const unsigned long long s2 = ld_volatile(&C->src_next.v);
+            const bool no_src = !S.sources || s2 >= S.B;
+            if (b == 0 && h2 >= (t2 < A.qcap ? t2 : A.qcap) && no_src) fin = 1;
+            // progress anywhere: a claim, a push, a source, a working warp's beat
+            const unsigned long long now = ld_volatile(&C->beat.v) + h2 * 3 + t2 * 5 + s2 * 7 + b * 11;
+            if (now != seen) {
+                seen = now;
+                t_progress = globaltimer();
+            }
+            if (*reinterpret_cast<volatile unsigned *>(&C->err) & kErrTimeout) fin = 2;
+            if (!fin && globaltimer() - t_progress > A.timeout_ns) {
+                atomicOr(&C->err, kErrTimeout);
+                fin = 2;
+            }
+        }
+        fin = __shfl_sync(kFull, fin, 0);
+        if (fin) break;
+        // idle warps poll the shared cursors rarely, so that the working
+        // warps' atomics on them are not held up
+        __nanosleep(backoff);
+        if (backoff < kRingIdleMaxNs) backoff <<= 1;
+    }
+    sk.flush(A);
+    flush_acc(A, acc, false);
+}
+
 }  // namespace
 
+// Grid of the global-queue kernel k_traverse.  Its claims are interleaved
+// over all warps of the grid (claim c of a warp covers a fixed set of slots),
+// and a warp keeps its claim until the slot is written or the queue drains,
+// so every block of the grid must be resident at once: a block that cannot
+// start leaves slots below the tail unclaimed, and the resident warps then
+// wait until the time limit and the call returns SKIM_ETIMEOUT (no hang).  So
+// the grid is at most the blocks that fit on the device by the occupancy of
+// every instantiation that may be launched with it, and another kernel that
+// occupies SMs at the same time (another stream of this process, another
+// context) can break it the same way.  The reverse searches over materialised
+// rows (k_rev_ring) have no such requirement.
 int traverse_grid(bool forward) {
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0, per = 0, per2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // A residual search starts from one seed and stays narrow: one block per
@@ -769,8 +1190,27 @@ int traverse_grid(bool forward) {
     // fill the machine: as many blocks as fit.
     if (forward) return sms;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_traverse<false, false>, kTravThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_traverse<false, true>, kTravThreads, 0);
+    if (per2 < per) per = per2;
     if (per < 1) per = 1;
     return sms * per;
+}
+
+int rev_ring_grid() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rev_ring, kRingThreads, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_rev_ring(const TravArgs &a, const uint32_t *lane_pair, uint32_t B, uint32_t l,
+                            const uint64_t *covered, uint64_t *alive, bool sources, int grid, cudaStream_t s) {
+    note_launch();
+    const RingSrc src{lane_pair, B, l, covered, alive, sources ? 1 : 0};
+    k_rev_ring<<<grid, kRingThreads, 0, s>>>(a, src);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_traverse(const TravArgs &a, bool forward, int grid, cudaStream_t s) {
@@ -817,8 +1257,9 @@ __global__ void k_rev_sources(TravArgs A, const uint32_t *lane_pair, uint32_t B,
                 atomicOr(reinterpret_cast<unsigned long long *>(&alive[w >> 1]), bits);
             }
         }
+        GlobalSink gsink;
         if (A.mat)
-            emit_rev_mat(A, acc, act, u, j >> 6, static_cast<int>(j & 63), i);
+            emit_rev_mat(A, acc, gsink, act, u, j >> 6, static_cast<int>(j & 63), i);
         else
             emit_rev<false>(A, acc, act, u, j >> 6, 1ull << (j & 63));
     }

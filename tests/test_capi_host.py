@@ -54,6 +54,18 @@ def test_strerror_and_argument_errors_without_gpu():
                 pkg.skim_params(4, 4, 3, 0.1, 0, 0, 0, 0, 0), pkg.skim_params(4, 4, 0, 0.1, 0, 0, 0, 0, 3),
                 pkg.skim_params(4, 4, 0, 0.1, 0, 0, 0, 0, 2)):  # bad rank mode; IC model needs l = 1
         assert lib.skim_create(ctypes.byref(g), ctypes.byref(bad), None, ctypes.byref(out)) == -1
+    # entry points on a null context, checked before any device call
+    buf = (ctypes.c_uint64 * 8)()
+    ln = ctypes.c_uint32()
+    assert lib.skim_get_sketch(None, 0, buf, ctypes.byref(ln)) == -1
+    assert lib.skim_set_wait_limit_ns(None, 1000) == -1
+    assert lib.skim_set_live_rows(None, 0) == -1
+    # the allocation-free query rejects null pointers and unknown rank readings
+    d = ctypes.c_double()
+    assert lib.skim_union_estimate_static(None, None, 4, 4, 4, 0, None, 0, ctypes.byref(d), None) == -1
+    assert lib.skim_union_estimate_static(buf, buf, 4, 4, 4, 3, None, 0, ctypes.byref(d), None) == -1
+    assert lib.skim_union_estimate_static(buf, buf, 4, 4, 4, 2, None, 0, ctypes.byref(d), None) == -1  # IC: l = 1
+    assert lib.skim_union_estimate_static(buf, buf, 4, 1, 4, 0, None, 0, ctypes.byref(d), None) == -1  # k < 2
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):

@@ -53,3 +53,47 @@ def test_batch_matches_each_graph_alone(bl):
         sk.build_sketches()
         x2, ln2 = sk.sketches()
         assert np.array_equal(x2, x) and np.array_equal(ln2, ln)
+
+
+def _digest(x, ln):
+    import hashlib
+    x = np.array(x, dtype=np.uint64, copy=True)
+    k = x.shape[1]
+    x[np.arange(k)[None, :] >= ln[:, None].astype(np.int64)] = 0
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(ln, dtype="<u4").tobytes())
+    h.update(np.ascontiguousarray(x, dtype="<u8").tobytes())
+    return h.hexdigest()
+
+
+@pytest.mark.parametrize("bl", [0, 1 << 20])
+def test_batched256_trivalency_matches_oracle(bl):
+    """The many-graph workload at its own size: 256 R-MAT graphs (scale 10..16,
+    edge factor 8..32, about 4.7M nodes and 79M edges in all), trivalency
+    probabilities, l = 64, k = 32, in one context.  Batches of 2M (default)
+    and 1M lanes hold tens of millions of visit records, so the records are
+    placed node by node.  Every graph's slice of the sketches must hash to the
+    digest the oracle stored for that graph built alone."""
+    import json
+    import os
+
+    import paper_1408_6282_gb300 as pkg
+    from paper_1408_6282_gb300 import build as b
+    b.build()
+    path = os.path.join(os.path.dirname(__file__), "golden", "batched256_trivalency.json")
+    gold = json.load(open(path))
+    specs = synth.batched_graph_specs(256)
+    gl = [synth.rmat(sc, ef, key, device="cuda") for sc, ef, key in specs]
+    for gr, gg, (sc, ef, key) in zip(gl, gold["per_graph"], specs):
+        assert (gg["scale"], gg["edge_factor"], int(gg["key"])) == (sc, ef, key)
+        assert gr.digest() == gg["graph_sha256"]
+    keys = [synth.Keys.from_seed(key) for _, _, key in specs]
+    sk = pkg.Skim.batch([(gr.n, gr.src, gr.dst) for gr in gl], gold["l"], gold["k"], [gold["prob_model"]] * 256,
+                        [0.0] * 256, [kk.coin for kk in keys], [kk.rank for kk in keys], [kk.prob for kk in keys],
+                        batch_lanes=bl)
+    with sk:
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        bad = [g for g, gg in enumerate(gold["per_graph"])
+               if _digest(x[sk.offsets[g]:sk.offsets[g + 1]], ln[sk.offsets[g]:sk.offsets[g + 1]]) != gg["sketch_sha256"]]
+        assert not bad, bad

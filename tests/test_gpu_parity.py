@@ -91,6 +91,32 @@ def test_small_graphs_sketches_skim_queries(pkg, name, mk, l, k, model, p, bl):
             assert _close(a, oracle.union_estimate(ox, oln, l, q))
 
 
+@pytest.mark.parametrize("name,mk", SMALL)
+@pytest.mark.parametrize("l,k,model,p,bl", [CONF[1], CONF[3], CONF[5], CONF[6]])
+def test_small_graphs_coins_hashed_in_the_search(pkg, name, mk, l, k, model, p, bl):
+    """No instance stored: every search hashes the coins of the edges its lanes
+    reach (Section 2's coins, evaluated on the fly).  Bit-exact as above, and
+    switching the live rows back on gives the same results."""
+    g = mk()
+    pb, sk = _both(pkg, g, l, k, model, p, 11, bl)
+    with sk:
+        ox, oln, _ = oracle.build_sketches(pb)
+        s = min(g.n, 25)
+        os_, oc, otau, okp, _ = oracle.skim_stops(pb, s)
+        for rows in (False, True):
+            sk.set_live_rows(rows)
+            sk.build_sketches()
+            x, ln = sk.sketches()
+            assert np.array_equal(ln, oln) and np.array_equal(x, ox), rows
+            seeds, cov, tau, kp = sk.greedy_stops(s)
+            assert np.array_equal(seeds, os_) and np.array_equal(cov, oc), rows
+            assert np.array_equal(tau, otau) and np.array_equal(kp, okp), rows
+            if not rows:
+                st = sk.stats()
+                assert st["rev_coins"] > 0 or g.m == 0  # the coins were drawn in the search
+            assert sk.instance_stats()[1] == (rows and True)
+
+
 @pytest.mark.parametrize("bl", [0, 64, 1024])
 def test_skim_full_permutation_and_resume(pkg, bl):
     g = synth.random_small_graph(200, 1200, 8)
@@ -198,6 +224,22 @@ def test_contexts_on_pooled_memory(pkg):
             x, ln = sk.sketches()
             assert _digest(x, ln) == gold["sketches"]["sha256"]
             _check_skim(sk, gold["skim"], w.seeds)
+
+
+def test_rmat18_wc_coins_hashed_in_the_search(pkg):
+    """R-MAT scale 18, weighted cascade, l = k = 64 with no instance stored:
+    the searches hash every reached edge's coins; sketches, 50 seeds, their
+    thresholds and k' against the stored oracle values."""
+    gold = _golden("rmat18_wc")
+    w = synth.WORKLOADS["rmat18_wc"]
+    g = w.graph(device="cuda")
+    ks = w.keys()
+    with pkg.Skim(g.n, g.src, g.dst, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob) as sk:
+        sk.set_live_rows(False)
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        assert _digest(x, ln) == gold["sketches"]["sha256"]
+        _check_skim(sk, gold["skim"], w.seeds)
 
 
 def test_rmat18_wc_sketches_large_batches(pkg):
