@@ -3,14 +3,20 @@
 
 One step = one pass over the whole hot path on R-MAT scale 20 (edge factor
 16), weighted cascade, l = k = 64:
-  rank order of the n*l pairs -> all combined sketches (Algorithm 2)
-  -> 50 SKIM seeds with residual updates (Algorithm 1)
-  -> a batch of influence-oracle queries (Eq. unionest).
+  live-edge instances -> rank order of the n*l pairs -> all combined sketches
+  (Algorithm 2) -> 50 SKIM seeds with residual updates (Algorithm 1) -> a
+  batch of influence-oracle queries (Eq. unionest).
 
 value: edge-instance traversals per second, the traversal count being the
 oracle's sequential count for the step (stored next to the tests), so work
 the GPU does twice is not credited.  Also reported: seconds to 50 seeds,
-sketch-build seconds, oracle QPS and single-query p50/p99 latency.
+sketch-build seconds, live-edge and coin rates, oracle QPS and single-query
+p50/p99 latency, the roofline of the dominant kernel (with the random-gather
+ceiling measured in the same run), the same step with coins hashed in the
+searches, the influence oracle served over R-MAT scale 22 sketches (plain
+one-query form against continuous batching), 256 graphs built in one batch
+against one at a time, and R-MAT scale 24 (uniform p = 0.01): all sketches
+and 200 seeds.
 
 usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs its own replica (independent problems, no
@@ -127,14 +133,17 @@ def traffic_record(kernel: str, workload: str):
     return rec
 
 
-def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms, workload):
+def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms, workload, gather=None):
     """Roofline of one kernel group of the step, from its CUDA-event time and
     the algorithmic work of one step (the oracle's counts, so redundant GPU
     work is not credited).
 
-    rev_search  (memory): 16 B per reverse expansion (the two row bounds of
-                (v, i)) + 20 B per live in-edge (4 B neighbour id, 8 B read and
-                8 B write of its visited word).
+    rev_search  (memory): every candidate visit -- a batch's source lane or a
+                live in-edge walked -- reads a 4 B node or pair id, the 8 B
+                bounds of the live row of (v, i) (which carry Algorithm 2's
+                pruning flag) and reads and writes its 8 B visited word (16 B);
+                every expansion also writes its 12 B visit record.  Sources are
+                taken inside the search kernel, so their lanes count here.
     fwd_search  (memory): 16 B per forward expansion (the two row bounds of
                 (v, i)) + 20 B per live out-edge (4 B neighbour id, covered word
                 read and write) + 8 B per index entry erased (node id, size).
@@ -152,12 +161,26 @@ def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms, wo
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)", "frac": achieved / peak,
                 "traffic": None, "peak_note": "derived: 152 SMs x 64 int32 ops/clk x max SM clock",
                 "algorithmic_units": f"2 x {m} edges x {l} instances coins x {OPS_PER_COIN} ops", **common}
+    extra = {}
     if kname == "rev_search":
+        lanes = sk["ranks_consumed"] + sm["ranks_consumed"]
         E = sk["rev_expansions"] + sm["rev_expansions"]
         L = sk.get("rev_live_edges", 0) + sm.get("rev_live_edges", 0)
-        byts = 16 * E + 20 * L
-        units = f"{E} reverse expansions x 16 B + {L} live in-edges x 20 B per step"
-        key = "k_traverse_rev"
+        cand = lanes + L
+        byts = 28 * cand + 12 * E
+        units = (f"{cand} candidate visits ({lanes} source lanes + {L} live in-edges) x 28 B + {E} expansions "
+                 "x 12 B per step")
+        key = "k_rev_ring"
+        if gather:
+            # each candidate costs at least two independent random accesses
+            # (its row entry and its visited slot) and each live in-edge's id
+            # is a third: the count a random-access ceiling applies to
+            acc = 2 * cand + L
+            extra["random_access"] = {"achieved": acc / sec / 1e9, "peak": gather / 1e9, "unit": "G accesses/s",
+                                      "frac": acc / sec / gather,
+                                      "basis": "2 random accesses per candidate visit + 1 per live in-edge; peak = "
+                                               "random 8-byte gathers over a 4 GiB array (torch index_select) "
+                                               "timed in this run"}
     else:
         E, L, X = sm["fwd_expansions"], sm.get("fwd_live_edges", 0), sm["index_erased"]
         byts = 16 * E + 20 * L + 8 * X
@@ -170,7 +193,29 @@ def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms, wo
             "traffic_note": (f"DRAM bytes per launch ({trb['launch']}), from profiles/traffic.json") if trb
             else "no capture of the current source",
             "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-            "algorithmic_units": units, **common}
+            "algorithmic_units": units, **common, **extra}
+
+
+def gather_peak(device: str = "cuda") -> float:
+    """Random 8-byte loads per second over a 4 GiB array (the ceiling of a
+    kernel whose every access is an independent random one)."""
+    import torch
+    n = 1 << 29
+    a = torch.arange(n, dtype=torch.int64, device=device)
+    idx = torch.randint(0, n, (1 << 26,), device=device, dtype=torch.int64)
+    out = torch.empty(1 << 26, dtype=torch.int64, device=device)
+    for _ in range(3):
+        torch.index_select(a, 0, idx, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        torch.index_select(a, 0, idx, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    rate = 5 * idx.shape[0] / (e0.elapsed_time(e1) / 1000.0)
+    del a, idx, out
+    torch.cuda.empty_cache()
+    return rate
 
 
 def max_over_ranks(elapsed: float, dist=None, device="cpu") -> float:
@@ -200,6 +245,202 @@ def cpu_baseline(w, g, instances: int):
     return cnt["rev_edge_scans"] / dt, dt, cnt["rev_edge_scans"]
 
 
+def config5_object(pkg, stream, local):
+    """Large plain SKIM (R-MAT scale 24, uniform p = 0.01, l = k = 64): every
+    sketch (Algorithm 2) and 200 seeds (Algorithm 1) on the device-resident
+    graph, each timed with CUDA events, plus the reverse search's roofline."""
+    import torch
+    w = synth.WORKLOADS["rmat24_p01"]
+    gold = json.load(open(os.path.join(GOLDEN, f"{w.name}.json")))
+    a = time.perf_counter()
+    g = w.graph(device=f"cuda:{local}")
+    gen_s = time.perf_counter() - a
+    assert g.digest() == gold["graph_sha256"], "generated graph differs from the one the oracle counted"
+    ks = w.keys()
+    src_d = torch.from_numpy(g.src.view(np.int32)).cuda()
+    dst_d = torch.from_numpy(g.dst.view(np.int32)).cuda()
+    m = g.m
+    del g
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    sk = pkg.Skim(1 << w.n_or_scale, src_d, dst_d, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob,
+                  stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - a
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    sk.set_timing(True)
+    sk.kernel_times(reset=True)
+    ev[0].record(stream)
+    sk.build_sketches()
+    ev[1].record(stream)
+    seeds, cov = sk.greedy(w.seeds)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    kt = sk.kernel_times(reset=True)
+    build_s, greedy_s = ev[0].elapsed_time(ev[1]) / 1000.0, ev[1].elapsed_time(ev[2]) / 1000.0
+    ok = seeds.tolist() == gold["skim"]["seeds"] and [int(c) for c in cov] == gold["skim"]["cov"]
+    live_pairs, _ = sk.instance_stats()
+    out = {"workload": f"rmat24_p01: R-MAT scale 24 edge factor 16 ({m} edges after dedup), uniform p=0.01, "
+                       f"l={w.l}, k={w.k}, {w.seeds} seeds",
+           "graph_generation_s": gen_s, "context_s": create_s, "sketch_build_s": build_s,
+           "s_to_200_seeds": greedy_s, "build_plus_200_seeds_s": build_s + greedy_s, "seeds_match_oracle": ok,
+           "live_pairs": live_pairs, "kernel_ms": {k2: round(v[0], 3) for k2, v in kt.items()}}
+    sm = gold["skim"]["counters"]
+    skim_t = sm["rev_edge_scans"] + sm["fwd_edge_scans"]
+    out["skim_traversals_per_s"] = skim_t / greedy_s
+    if "sketches" in gold:
+        t_alg = gold["sketches"]["counters"]["rev_edge_scans"] + skim_t
+        out["traversals"] = t_alg
+        out["edge_instance_traversals_per_s"] = t_alg / (build_s + greedy_s)
+        out["oracle_seconds"] = gold["sketches"]["oracle_seconds"] + gold["skim"]["oracle_seconds"]
+        peak = json.load(open(PEAKS)).get("hbm_gbs", 6800.0) if os.path.exists(PEAKS) else 6800.0
+        total_ms = sum(v[0] for v in kt.values())
+        out["roofline"] = kernel_roofline("rev_search", kt, gold, m, w.l, 1, 2070.0, peak, total_ms, w.name)
+    else:
+        out["oracle_seconds"] = gold["skim"]["oracle_seconds"]
+    sk.close()
+    del src_d, dst_d
+    torch.cuda.empty_cache()
+    pkg.skim_release_memory()
+    return out
+
+
+def serving_config4_object(pkg, stream, local, args):
+    """The influence oracle served on R-MAT scale 22 (weighted cascade, l = k =
+    64) sketches resident on the device: the plain one-query form (one C-ABI
+    call per query, host seeds and result), one batched call, and Poisson
+    streams at swept rates through the continuous-batching server."""
+    import torch
+    w = synth.WORKLOADS["rmat22_wc"]
+    gold = json.load(open(os.path.join(GOLDEN, f"{w.name}.json")))
+    g = w.graph(device=f"cuda:{local}")
+    assert g.digest() == gold["graph_sha256"]
+    ks = w.keys()
+    src_d = torch.from_numpy(g.src.view(np.int32)).cuda()
+    dst_d = torch.from_numpy(g.dst.view(np.int32)).cuda()
+    out = {"workload": f"rmat22_wc: R-MAT scale 22 edge factor 16 ({g.m} edges after dedup), weighted cascade, "
+                       f"l={w.l}, k={w.k}; |S| = floor(10^(3U)) in 1..1000, seeds uniform"}
+    with pkg.Skim(g.n, src_d, dst_d, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob,
+                  stream=stream.cuda_stream) as sk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sk.build_sketches()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["sketch_build_s"] = e0.elapsed_time(e1) / 1000.0
+        est = sk.query_batch([q["seeds"] for q in gold["queries"]])
+        out["estimates_match_oracle"] = bool(all(abs(float(e) - q["estimate"]) <= 1e-12 * abs(q["estimate"])
+                                                 for q, e in zip(gold["queries"], est)))
+        qs = query_sets(w, g.n, args.queries)
+        # plain one-query form: one call per query, host seeds to host estimate
+        lat = []
+        for q in qs[: args.latency_queries]:
+            a = time.perf_counter()
+            sk.query(q)
+            lat.append((time.perf_counter() - a) * 1000.0)
+        lat.sort()
+        out["plain"] = {"qps": 1000.0 / (sum(lat) / len(lat)), "p50_ms": lat[len(lat) // 2],
+                        "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "queries": len(lat)}
+        a = time.perf_counter()
+        sk.query_batch(qs)
+        out["one_batch_call_qps"] = len(qs) / (time.perf_counter() - a)
+        serving = []
+        with sk.server(max_inflight=4096, scratch_slots=1 << 24, streams=4) as srv:
+            for rate in args.serve_rates:
+                arr = synth.poisson_arrivals(len(qs), rate, ks.query + int(rate))
+                g0, q0 = srv.stats()
+                t_a = time.perf_counter()
+                slat, sest = srv.replay(arr, qs)
+                wall = time.perf_counter() - t_a
+                g1, q1 = srv.stats()
+                slat = np.sort(slat) * 1000.0
+                serving.append({"offered_qps": rate, "qps": len(qs) / wall, "p50_ms": float(slat[len(slat) // 2]),
+                                "p99_ms": float(slat[min(len(slat) - 1, int(0.99 * len(slat)))]),
+                                "mean_group": (q1 - q0) / max(1, g1 - g0)})
+        out["served"] = serving
+    del src_d, dst_d
+    torch.cuda.empty_cache()
+    return out
+
+
+def batched_object(pkg, stream, local, count):
+    """The batched form against one graph at a time on the same GPU, both
+    timed like for like: builds only (contexts created before the clock
+    starts), and everything (create, build, destroy)."""
+    import torch
+    specs = synth.batched_graph_specs(count)
+    gl = [synth.rmat(sc, ef, key, device=f"cuda:{local}") for sc, ef, key in specs]
+    gk = [synth.Keys.from_seed(key) for _, _, key in specs]
+    bl, bk = 64, 32
+    build_one = 0.0
+    torch.cuda.synchronize()
+    t_a = time.perf_counter()
+    for gr, kk in zip(gl, gk):
+        with pkg.Skim(gr.n, gr.src, gr.dst, bl, bk, 2, 0.0, kk.coin, kk.rank, kk.prob,
+                      stream=stream.cuda_stream) as one:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one.build_sketches()
+            e1.record(stream)
+            e1.synchronize()
+            build_one += e0.elapsed_time(e1) / 1000.0
+    torch.cuda.synchronize()
+    total_one = time.perf_counter() - t_a
+    t_a = time.perf_counter()
+    many = pkg.Skim.batch([(gr.n, gr.src, gr.dst) for gr in gl], bl, bk, [2] * len(gl), [0.0] * len(gl),
+                          [kk.coin for kk in gk], [kk.rank for kk in gk], [kk.prob for kk in gk],
+                          stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    create_many = time.perf_counter() - t_a
+    with many:
+        best, secs = many.autotune([1 << 18, 1 << 20, 1 << 21, 1 << 22])
+        many.build_sketches()  # warm, with the tuned lane count
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        many.build_sketches()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        build_many = e0.elapsed_time(e1) / 1000.0
+        bstats = many.stats()
+        t_a = time.perf_counter()
+    t_close = time.perf_counter() - t_a
+    return {"graphs": len(gl), "nodes": int(sum(gr.n for gr in gl)), "edges": int(sum(gr.m for gr in gl)),
+            "l": bl, "k": bk, "prob_model": "trivalency",
+            "builds_only": {"batched_s": build_many, "one_graph_at_a_time_s": build_one,
+                            "speedup": build_one / build_many},
+            "create_build_destroy": {"batched_s": create_many + build_many + t_close,
+                                     "one_graph_at_a_time_s": total_one,
+                                     "speedup": total_one / (create_many + build_many + t_close)},
+            "autotuned_batch_lanes": best, "autotune_s": [float(x) for x in secs],
+            "batches": bstats["batches"], "retries": bstats["retries"]}
+
+
+def coins_on_the_fly_object(sk, w, gold, stream):
+    """The same step's sketch build and SKIM seeds with no instance stored:
+    every search hashes the coins of the edges its lanes reach (Section 2's
+    coins evaluated on the fly), against the materialised live rows."""
+    import torch
+    sk.set_live_rows(False)
+    try:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        sk.build_sketches()
+        ev[1].record(stream)
+        st = sk.stats()
+        seeds, cov = sk.greedy(w.seeds)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        st2 = sk.stats()
+        b, gr = ev[0].elapsed_time(ev[1]) / 1000.0, ev[1].elapsed_time(ev[2]) / 1000.0
+        ok = seeds.tolist() == gold["skim"]["seeds"]
+        return {"sketch_build_s": b, "s_to_50_seeds": gr, "seeds_match_oracle": ok,
+                "build_coins": st["rev_coins"], "build_coins_per_s": st["rev_coins"] / b,
+                "skim_coins": st2["rev_coins"] + st2["fwd_coins"]}
+    finally:
+        sk.set_live_rows(True)
+
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle on a bounded sample of the workload."""
     if rank != 0:
@@ -219,7 +460,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": workload_desc(w, g), "parallelism": "none (CPU oracle)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -234,11 +476,13 @@ def main():
     ap.add_argument("--queries", type=int, default=1000)
     ap.add_argument("--latency-queries", type=int, default=300)
     ap.add_argument("--cpu-instances", type=int, default=2)
-    ap.add_argument("--serve-rates", type=float, nargs="*", default=[50000.0, 200000.0, 500000.0])
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[50000.0, 200000.0, 500000.0, 1000000.0])
     ap.add_argument("--batched-graphs", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--neighborhood-queries", type=int, default=300)
     ap.add_argument("--no-rank-modes", action="store_true")
+    ap.add_argument("--no-config5", dest="config5", action="store_false")
+    ap.add_argument("--no-on-the-fly", dest="on_the_fly", action="store_false")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -398,57 +642,16 @@ def main():
                     rec["s_to_50_seeds"] = time.perf_counter() - a
                 rank_modes[name] = rec
 
-    # serving: Poisson query streams replayed through the continuous-batching
-    # server on the same resident sketches, against the one-query-at-a-time form
-    serving = []
-    with sk.server(max_inflight=4096, scratch_slots=1 << 24, streams=4) as srv:
-        for rate in args.serve_rates:
-            arr = synth.poisson_arrivals(len(qs), rate, w.keys().query + int(rate))
-            g0, q0 = srv.stats()
-            t_a = time.perf_counter()
-            slat, sest = srv.replay(arr, qs)
-            wall = time.perf_counter() - t_a
-            g1, q1 = srv.stats()
-            slat = np.sort(slat) * 1000.0
-            serving.append({"offered_qps": rate, "qps": len(qs) / wall,
-                            "p50_ms": float(slat[len(slat) // 2]),
-                            "p99_ms": float(slat[min(len(slat) - 1, int(0.99 * len(slat)))]),
-                            "mean_group": (q1 - q0) / max(1, g1 - g0)})
+    # the same step with no instance stored (coins hashed in the searches)
+    on_the_fly = coins_on_the_fly_object(sk, w, gold, stream) if args.on_the_fly else None
+
+    # serving (config 4): the influence oracle over R-MAT 22 sketches, plain
+    # one-query form vs continuous batching
+    serving = serving_config4_object(pkg, stream, local, args) if args.serve_rates else None
 
     # batched form: many independent graphs in one context and one pass,
-    # against building them one context at a time on the same GPU
-    batched = None
-    if args.batched_graphs:
-        specs = synth.batched_graph_specs(args.batched_graphs)
-        gl = [synth.rmat(sc, ef, key, device=f"cuda:{local}") for sc, ef, key in specs]
-        gk = [synth.Keys.from_seed(key) for _, _, key in specs]
-        bl, bk = 64, 32
-        torch.cuda.synchronize()
-        t_a = time.perf_counter()
-        for gr, kk in zip(gl, gk):
-            with pkg.Skim(gr.n, gr.src, gr.dst, bl, bk, 2, 0.0, kk.coin, kk.rank, kk.prob,
-                          stream=stream.cuda_stream) as one:
-                one.build_sketches()
-        torch.cuda.synchronize()
-        t_plain = time.perf_counter() - t_a
-        many = pkg.Skim.batch([(gr.n, gr.src, gr.dst) for gr in gl], bl, bk, [2] * len(gl), [0.0] * len(gl),
-                              [kk.coin for kk in gk], [kk.rank for kk in gk], [kk.prob for kk in gk],
-                              stream=stream.cuda_stream)
-        with many:
-            best, secs = many.autotune([1 << 18, 1 << 20, 1 << 21, 1 << 22])
-            many.build_sketches()  # warm
-            torch.cuda.synchronize()
-            t_a = time.perf_counter()
-            many.build_sketches()
-            torch.cuda.synchronize()
-            t_batch = time.perf_counter() - t_a
-            bstats = many.stats()
-        batched = {"graphs": len(gl), "nodes": int(sum(gr.n for gr in gl)), "edges": int(sum(gr.m for gr in gl)),
-                   "batched_build_s": t_batch, "one_graph_at_a_time_s": t_plain, "speedup": t_plain / t_batch,
-                   "autotuned_batch_lanes": best, "autotune_s": [float(x) for x in secs],
-                   "batches": bstats["batches"], "retries": bstats["retries"], "coins": bstats["rev_coins"],
-                   "note": "one-at-a-time includes creating each context (CSR, rank order); batched is the "
-                           "build of the ready union context"}
+    # against one graph at a time on the same GPU
+    batched = batched_object(pkg, stream, local, args.batched_graphs) if args.batched_graphs else None
 
     # end to end through the C ABI with host buffers
     e2e_times = []
@@ -469,6 +672,11 @@ def main():
     e2e_t = max_over_ranks(statistics.median(e2e_times), dist, device="cuda")
     e2e_value = job_value(world, 1, t_alg, e2e_t)
 
+    sk.close()
+    # large plain SKIM (config 5) on the same GPU, after the step's context is gone
+    config5 = config5_object(pkg, stream, local) if args.config5 else None
+    gather = gather_peak() if rank == 0 else None
+
     # roofline of the dominant kernel group (largest device time per step)
     sm_max = (clk or {}).get("sm_max_mhz")
     if not sm_max:
@@ -476,7 +684,10 @@ def main():
     hbm_peak = json.load(open(PEAKS)).get("hbm_gbs", 6800.0) if os.path.exists(PEAKS) else 6800.0
     total_ms = sum(v[0] for v in kt.values())
     dominant = max(("rev_search", "fwd_search", "instances"), key=lambda kname: kt[kname][0])
-    roofline = kernel_roofline(dominant, kt, gold, g.m, w.l, args.steps, sm_max, hbm_peak, total_ms, w.name)
+    roofline = kernel_roofline(dominant, kt, gold, g.m, w.l, args.steps, sm_max, hbm_peak, total_ms, w.name,
+                               gather)
+    sk_c, sm_c = gold["sketches"]["counters"], gold["skim"]["counters"]
+    step_s = elapsed / args.steps
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1000.0, "higher_is_better": True,
@@ -492,8 +703,16 @@ def main():
             "oracle_qps": len(qs) / statistics.median(part["query"]),
             "query_p50_ms": lat[len(lat) // 2], "query_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "single_query_qps": 1000.0 / (sum(lat) / len(lat)),
-            "serving": serving,
+            "rates": {"live_edge_traversals_per_s": (sk_c["rev_live_edges"] + sm_c["rev_live_edges"]
+                                                     + sm_c["fwd_live_edges"]) / step_s,
+                      "reverse_expansions_per_s": (sk_c["rev_expansions"] + sm_c["rev_expansions"]) / step_s,
+                      "instance_coins_per_s": 2 * g.m * w.l / statistics.median(part["instances"]),
+                      "note": "live edges and expansions are the oracle's counts for the step; coins = 2 m l "
+                              "(both CSR orders) per instance generation"},
+            "coins_on_the_fly": on_the_fly,
+            "serving_config4": serving,
             "batched": batched,
+            "config5": config5,
             "adaptive_error": adaptive,
             "neighborhood_queries": neighborhood,
             "rank_modes": rank_modes,
@@ -504,10 +723,16 @@ def main():
             "roofline": roofline}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, trav = cpu_baseline(w, g, args.cpu_instances)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        full = gold["sketches"]["oracle_seconds"] + gold["skim"]["oracle_seconds"]
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                                "kind": "oracle",
                                 "sample": f"oracle Algorithm 2 on {args.cpu_instances} of the {w.l} instances of "
-                                          f"{w.name} ({trav} traversals in {dt:.1f} s), single thread"}
-    sk.close()
+                                          f"{w.name} ({trav} traversals in {dt:.1f} s), single thread of the "
+                                          f"host's {os.cpu_count()} cores",
+                                "full_step_oracle_s": full, "full_step_oracle_value": t_alg / full,
+                                "full_step_note": "the oracle's whole step (all sketches + 50 seeds), single "
+                                                  "thread, as stored by tests/golden/make_golden.py on the "
+                                                  "development host"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -388,7 +388,10 @@ constexpr uint64_t kNodeSortDensity = 4;
 // visited-table slots per expected visit record of a batch, and per lane when
 // the records per lane are not known yet
 constexpr double kTableSlots = SKIM_TABLE_SLOTS;
-constexpr uint64_t kTableSlotsPerLaneFirst = 32;
+#ifndef SKIM_RING_RECORDS_PER_LANE
+#define SKIM_RING_RECORDS_PER_LANE 8
+#endif
+constexpr double kRingRecordsPerLane = SKIM_RING_RECORDS_PER_LANE;
 
 int ensure_idx(skim_ctx *c, uint64_t need);
 
@@ -405,12 +408,15 @@ int node_buffers(skim_ctx *c) {
 
 // Reverse search of the batch of ranks [p0, p0+B).  mode_build: Algorithm 2
 // (pruned by local counts); otherwise SKIM (covered sources skipped).
-// est_per_lane: expected visit records per lane (0 = unknown: 32 slots per
-// lane; negative: the batch is re-run after an overflow, the whole table).
-// The visited table used is a power of two of about 2 slots per expected
-// record, zeroed before the batch: small enough to stay in L2, so that its
-// compare-and-swaps rarely go to DRAM.  Returns SKIM_OK with *retry set if
-// the batch overflowed its tables.
+// est_per_lane: expected visit records per lane (0 or negative = unknown, or
+// a re-run after an overflow: the whole table).  The visited table used is a
+// power of two of about 4 slots per expected record, zeroed before the batch:
+// small enough to stay in L2.  A batch of searches that stay small (at most
+// kRingRecordsPerLane expected records per lane) runs on the per-warp queues;
+// larger searches -- a lane that reaches thousands of nodes, as in the first
+// batches or on hub-heavy graphs -- spread over the whole GPU through the
+// global queue, whose atomic claims keep every warp fed.  Returns SKIM_OK
+// with *retry set if the batch overflowed its tables.
 int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry, double est_per_lane) {
     *retry = false;
     const uint32_t T = (B + 63) / 64;
@@ -425,8 +431,6 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         uint64_t want = c->hcap;
         if (est_per_lane > 0)
             want = static_cast<uint64_t>(kTableSlots * est_per_lane * static_cast<double>(B));
-        else if (est_per_lane == 0)
-            want = kTableSlotsPerLaneFirst * static_cast<uint64_t>(B);
         want = pow2_at_least(std::max<uint64_t>(1ull << 16, want));
         a.hmask = std::min(want, c->hcap) - 1;
         CK(c, clear_table(c, a.hmask + 1));
@@ -446,7 +450,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         cudaEventCreate(&tr1);
         cudaEventRecord(tr0, c->st);
     }
-    if (c->mat && SKIM_REV_RING) {
+    if (c->mat && SKIM_REV_RING && est_per_lane > 0 && est_per_lane <= kRingRecordsPerLane) {
         const RevSources rs{c->spair + p0, B, mode_build ? nullptr : c->covered, mode_build ? nullptr : c->alive};
         RC(run_traversal(c, a, false, &R, &rs));
     } else {

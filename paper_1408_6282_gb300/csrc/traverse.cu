@@ -26,7 +26,7 @@ namespace skim {
 namespace {
 
 constexpr int kTravThreads = 256;
-constexpr int kMaxProbe = 4096;
+constexpr int kMaxProbe = 512;  // the table is sized to a load of about 1/4: longer chains mean it is full
 
 // Live threshold of CSR edge idx = (u -> v); tm1_head is the item's value
 // for the models whose threshold depends on the head node only.
@@ -1101,7 +1101,19 @@ __global__ void __launch_bounds__(kRingThreads, SKIM_RING_MIN_BLOCKS) k_rev_ring
             // items too
             if (src_done && nt < 32) ring_claim_global(A, nt, 32 - nt, it, have);
             ring_expand(A, acc, sk, have, it);
-            if ((++steps & 63) == 0 && lane == 0) atomicAdd(&C->beat.v, 1ull);
+            if ((++steps & 15) == 0) {
+                // a batch that overflowed its tables is re-run with fewer
+                // lanes: stop working on it
+                unsigned e = 0;
+                if (lane == 0) {
+                    if ((steps & 63) == 0) atomicAdd(&C->beat.v, 1ull);
+                    e = *reinterpret_cast<volatile unsigned *>(&C->err);
+                }
+                if (__shfl_sync(kFull, e, 0) & (kErrRetryable | kErrTimeout)) {
+                    sk.rh = sk.rt;
+                    src_done = true;
+                }
+            }
             continue;
         }
         // the ring is empty and the sources are used up: items other warps
@@ -1151,7 +1163,7 @@ __global__ void __launch_bounds__(kRingThreads, SKIM_RING_MIN_BLOCKS) k_rev_ring
                 seen = now;
                 t_progress = globaltimer();
             }
-            if (*reinterpret_cast<volatile unsigned *>(&C->err) & kErrTimeout) fin = 2;
+            if (*reinterpret_cast<volatile unsigned *>(&C->err) & (kErrTimeout | kErrRetryable)) fin = 2;
             if (!fin && globaltimer() - t_progress > A.timeout_ns) {
                 atomicOr(&C->err, kErrTimeout);
                 fin = 2;
