@@ -393,8 +393,10 @@ def batched_object(pkg, stream, local, count):
     torch.cuda.synchronize()
     create_many = time.perf_counter() - t_a
     with many:
-        best, secs = many.autotune([1 << 18, 1 << 20, 1 << 21, 1 << 22])
-        many.build_sketches()  # warm, with the tuned lane count
+        grid = [(lanes, ring, 4) for lanes in (1 << 20, 1 << 21, 1 << 22) for ring in (0.0, 8.0)]
+        bi, secs = many.autotune_settings(grid)
+        best = many.tuning()
+        many.build_sketches()  # warm, with the tuned settings
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         many.build_sketches()
@@ -411,7 +413,7 @@ def batched_object(pkg, stream, local, count):
             "create_build_destroy": {"batched_s": create_many + build_many + t_close,
                                      "one_graph_at_a_time_s": total_one,
                                      "speedup": total_one / (create_many + build_many + t_close)},
-            "autotuned_batch_lanes": best, "autotune_s": [float(x) for x in secs],
+            "autotuned": best, "autotune_grid": grid, "autotune_s": [float(x) for x in secs],
             "batches": bstats["batches"], "retries": bstats["retries"]}
 
 

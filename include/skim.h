@@ -128,6 +128,36 @@ int skim_create_batch(const skim_graph *graphs, const skim_params *params, uint3
 int skim_autotune_batch_lanes(skim_ctx *ctx, const uint32_t *candidates, uint32_t count, uint32_t *best,
                               double *seconds);
 
+/* Switches of the rank-batched searches (Algorithms 1 and 2 run a batch of
+ * consecutive ranks as one search; none of these changes a result):
+ *   batch_lanes            ranks per batch, 0 = automatic (2M, or fewer when
+ *                          the previous batch's records per lane say so);
+ *   ring_records_per_lane  a batch whose searches are expected to leave at
+ *                          most this many visit records per lane (from the
+ *                          previous batch) runs with per-warp work queues in
+ *                          shared memory; larger searches share one global
+ *                          queue over the whole GPU (default 8; 0 = always
+ *                          the global queue);
+ *   node_sort_density      a batch's visit records are placed node by node
+ *                          (counting pass over the n nodes) when
+ *                          n <= node_sort_density * records, else radix
+ *                          sorted (default 4; >= 1). */
+typedef struct {
+    uint32_t batch_lanes;
+    double ring_records_per_lane;
+    uint32_t node_sort_density;
+} skim_tuning;
+int skim_get_tuning(skim_ctx *ctx, skim_tuning *out);
+int skim_set_tuning(skim_ctx *ctx, const skim_tuning *t);
+
+/* Autotuner over whole settings: builds the sketches once per candidate
+ * (host array of count settings), keeps the fastest for later builds and
+ * writes its index to *best (count if every build failed; the settings are
+ * then left as they were).  seconds (host, optional): each candidate's build
+ * time.  Errors: SKIM_EINVAL for a candidate with a negative records
+ * threshold or a zero density; a failing build's code. */
+int skim_autotune(skim_ctx *ctx, const skim_tuning *candidates, uint32_t count, uint32_t *best, double *seconds);
+
 /* Recompute the rank order of the n*l pairs (done by skim_create; exposed so
  * that a caller can time it).  Restarts SKIM (as skim_greedy_reset); the
  * sketches are unaffected (the ranks themselves do not change). */

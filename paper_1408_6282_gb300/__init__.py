@@ -38,6 +38,11 @@ class skim_graph(C.Structure):
                 ("on_device", C.c_int)]
 
 
+class skim_tuning(C.Structure):
+    _fields_ = [("batch_lanes", C.c_uint32), ("ring_records_per_lane", C.c_double),
+                ("node_sort_density", C.c_uint32)]
+
+
 class skim_params(C.Structure):
     _fields_ = [("l", C.c_uint32), ("k", C.c_uint32), ("prob_model", C.c_int), ("p", C.c_double),
                 ("coin_key", C.c_uint64), ("rank_key", C.c_uint64), ("prob_key", C.c_uint64),
@@ -62,6 +67,9 @@ def load():
     lib.skim_get_sketches.argtypes = [vp, vp, vp, C.c_int]
     lib.skim_sketch_pointers.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
     lib.skim_get_sketch.argtypes = [vp, u32, vp, vp]
+    lib.skim_get_tuning.argtypes = [vp, C.POINTER(skim_tuning)]
+    lib.skim_set_tuning.argtypes = [vp, C.POINTER(skim_tuning)]
+    lib.skim_autotune.argtypes = [vp, C.POINTER(skim_tuning), u32, vp, vp]
     lib.skim_set_wait_limit_ns.argtypes = [vp, u64]
     lib.skim_set_live_rows.argtypes = [vp, C.c_int]
     lib.skim_greedy.argtypes = [vp, u32, vp, vp]
@@ -352,6 +360,25 @@ class Skim:
 
     def autotune(self, candidates) -> tuple[int, np.ndarray]:
         return skim_autotune_batch_lanes(self.ctx, candidates)
+
+    def tuning(self) -> dict:
+        t = skim_tuning()
+        _check(load().skim_get_tuning(self.ctx, C.byref(t)), "skim_get_tuning")
+        return {"batch_lanes": t.batch_lanes, "ring_records_per_lane": t.ring_records_per_lane,
+                "node_sort_density": t.node_sort_density}
+
+    def set_tuning(self, batch_lanes: int, ring_records_per_lane: float, node_sort_density: int):
+        t = skim_tuning(batch_lanes, ring_records_per_lane, node_sort_density)
+        _check(load().skim_set_tuning(self.ctx, C.byref(t)), "skim_set_tuning")
+
+    def autotune_settings(self, settings) -> tuple[int, np.ndarray]:
+        """settings: [(batch_lanes, ring_records_per_lane, node_sort_density), ...];
+        returns (index of the fastest, seconds of each)."""
+        arr = (skim_tuning * len(settings))(*[skim_tuning(*x) for x in settings])
+        best = np.zeros(1, np.uint32)
+        secs = np.zeros(len(settings), np.float64)
+        _check(load().skim_autotune(self.ctx, arr, len(settings), _ptr(best), _ptr(secs)), "skim_autotune")
+        return int(best[0]), secs
 
     def close(self):
         if getattr(self, "ctx", None):

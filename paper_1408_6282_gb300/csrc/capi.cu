@@ -27,6 +27,11 @@ struct skim_ctx {
     uint64_t nl = 0;
     CoinModel cm{};
     uint32_t batch_cfg = 0;
+    // switches of the rank-batched search (skim_set_tuning): per-warp queues
+    // for batches of at most ring_rpl expected records per lane; records
+    // placed node by node when n <= node_density * records
+    double ring_rpl = 0;
+    uint32_t node_density = 0;
     // graph
     uint32_t *fptr = nullptr, *fcol = nullptr, *rptr = nullptr, *rcol = nullptr;
     uint64_t *thr_wc = nullptr;
@@ -450,7 +455,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         cudaEventCreate(&tr1);
         cudaEventRecord(tr0, c->st);
     }
-    if (c->mat && SKIM_REV_RING && est_per_lane > 0 && est_per_lane <= kRingRecordsPerLane) {
+    if (c->mat && SKIM_REV_RING && est_per_lane > 0 && est_per_lane <= c->ring_rpl) {
         const RevSources rs{c->spair + p0, B, mode_build ? nullptr : c->covered, mode_build ? nullptr : c->alive};
         RC(run_traversal(c, a, false, &R, &rs));
     } else {
@@ -490,7 +495,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     const int bits = bitlen(c->n - 1) + static_cast<int>(tbits);
     // records dense over the nodes: place them node by node (one pass over
     // the n node counters); sparse: radix sort over the key bits
-    c->bnode = static_cast<uint64_t>(c->n) <= kNodeSortDensity * R;
+    c->bnode = static_cast<uint64_t>(c->n) <= static_cast<uint64_t>(c->node_density) * R;
     if (c->bnode) RC(node_buffers(c));
     {
         KTimer kt(c, SKIM_K_SORT);
@@ -932,6 +937,8 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
     c->npos = npos;
     c->nbuild = nbuild;
     c->batch_cfg = prm->batch_lanes;
+    c->ring_rpl = kRingRecordsPerLane;
+    c->node_density = static_cast<uint32_t>(kNodeSortDensity);
     c->cm.model = prm->prob_model;
     c->cm.tm1_uniform = prm->prob_model == 0 ? tm1_of(prm->p) : 0;
     c->cm.tm1_class[0] = tm1_of(0.1);
@@ -1196,6 +1203,57 @@ int skim_autotune_batch_lanes(skim_ctx *c, const uint32_t *candidates, uint32_t 
     cudaEventDestroy(z);
     c->batch_cfg = best_b;
     *best = best_b;
+    return rc;
+}
+
+int skim_get_tuning(skim_ctx *c, skim_tuning *out) {
+    if (!c || !out) return SKIM_EINVAL;
+    out->batch_lanes = c->batch_cfg;
+    out->ring_records_per_lane = c->ring_rpl;
+    out->node_sort_density = c->node_density;
+    return SKIM_OK;
+}
+
+int skim_set_tuning(skim_ctx *c, const skim_tuning *t) {
+    if (!c || !t) return SKIM_EINVAL;
+    if (!(t->ring_records_per_lane >= 0.0) || t->node_sort_density == 0) return SKIM_EINVAL;
+    c->batch_cfg = t->batch_lanes;
+    c->ring_rpl = t->ring_records_per_lane;
+    c->node_density = t->node_sort_density;
+    return SKIM_OK;
+}
+
+int skim_autotune(skim_ctx *c, const skim_tuning *candidates, uint32_t count, uint32_t *best, double *seconds) {
+    if (!c || !candidates || !count || !best) return SKIM_EINVAL;
+    for (uint32_t i = 0; i < count; i++)
+        if (!(candidates[i].ring_records_per_lane >= 0.0) || candidates[i].node_sort_density == 0) return SKIM_EINVAL;
+    skim_tuning keep{};
+    skim_get_tuning(c, &keep);
+    double best_t = 1e300;
+    uint32_t best_i = count;
+    cudaEvent_t a = nullptr, z = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return fail_cuda(c, cudaGetLastError());
+    int rc = SKIM_OK;
+    for (uint32_t i = 0; i < count && rc == SKIM_OK; i++) {
+        skim_set_tuning(c, &candidates[i]);
+        if (c->batch_cfg) c->batch_cfg = std::max<uint32_t>(64, c->batch_cfg);
+        cudaEventRecord(a, c->st);
+        rc = skim_build_sketches(c);
+        cudaEventRecord(z, c->st);
+        cudaEventSynchronize(z);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, z);
+        if (seconds) seconds[i] = ms / 1000.0;
+        if (rc == SKIM_OK && ms < best_t) {
+            best_t = ms;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    skim_set_tuning(c, best_i < count ? &candidates[best_i] : &keep);
+    if (c->batch_cfg) c->batch_cfg = std::max<uint32_t>(64, c->batch_cfg);
+    *best = best_i;
     return rc;
 }
 

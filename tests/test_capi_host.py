@@ -60,6 +60,11 @@ def test_strerror_and_argument_errors_without_gpu():
     assert lib.skim_get_sketch(None, 0, buf, ctypes.byref(ln)) == -1
     assert lib.skim_set_wait_limit_ns(None, 1000) == -1
     assert lib.skim_set_live_rows(None, 0) == -1
+    t = pkg.skim_tuning(0, 8.0, 4)
+    assert lib.skim_set_tuning(None, ctypes.byref(t)) == -1
+    assert lib.skim_get_tuning(None, ctypes.byref(t)) == -1
+    best = ctypes.c_uint32()
+    assert lib.skim_autotune(None, ctypes.byref(t), 1, ctypes.byref(best), None) == -1
     # the allocation-free query rejects null pointers and unknown rank readings
     d = ctypes.c_double()
     assert lib.skim_union_estimate_static(None, None, 4, 4, 4, 0, None, 0, ctypes.byref(d), None) == -1

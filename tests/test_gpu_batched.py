@@ -53,6 +53,14 @@ def test_batch_matches_each_graph_alone(bl):
         sk.build_sketches()
         x2, ln2 = sk.sketches()
         assert np.array_equal(x2, x) and np.array_equal(ln2, ln)
+        # the autotuner over whole settings (lanes, queue switch, record order)
+        grid = [(256, 0.0, 4), (1024, 8.0, 1), (4096, 1e9, 1 << 20)]
+        bi, secs = sk.autotune_settings(grid)
+        assert 0 <= bi < len(grid) and np.all(secs > 0)
+        assert tuple(sk.tuning().values()) == grid[bi]
+        sk.build_sketches()
+        x3, ln3 = sk.sketches()
+        assert np.array_equal(x3, x) and np.array_equal(ln3, ln)
 
 
 def _digest(x, ln):

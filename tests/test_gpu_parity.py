@@ -117,6 +117,32 @@ def test_small_graphs_coins_hashed_in_the_search(pkg, name, mk, l, k, model, p, 
             assert sk.instance_stats()[1] == (rows and True)
 
 
+@pytest.mark.parametrize("ring", [0.0, 1e9])
+@pytest.mark.parametrize("name,mk,conf", [("rmat10", SMALL[-1][1], CONF[4]), ("er_dense", SMALL[7][1], (16, 16, 0, 0.1, 64)),
+                                          ("rmat12", lambda: synth.rmat(12, 16, 77), (64, 32, 1, 0.0, 2048))])
+def test_search_kernels_each_alone(pkg, ring, name, mk, conf):
+    """Every batch of reverse searches on the global queue (ring = 0), or every
+    batch whose records per lane are known on the per-warp queues (ring =
+    1e9), with records placed by node or radix sorted: each setting gives the
+    oracle's sketches and seeds."""
+    g = mk()
+    l, k, model, p, bl = conf
+    pb, sk = _both(pkg, g, l, k, model, p, 13, bl)
+    ox, oln, _ = oracle.build_sketches(pb)
+    os_, oc, otau, okp, _ = oracle.skim_stops(pb, min(g.n, 20))
+    with sk:
+        for density in (1, 1 << 30):
+            sk.set_tuning(bl, ring, density)
+            assert sk.tuning() == {"batch_lanes": bl, "ring_records_per_lane": ring, "node_sort_density": density}
+            sk.build_sketches()
+            x, ln = sk.sketches()
+            assert np.array_equal(ln, oln) and np.array_equal(x, ox), density
+            sk.greedy_reset()
+            seeds, cov, tau, kp = sk.greedy_stops(min(g.n, 20))
+            assert np.array_equal(seeds, os_) and np.array_equal(cov, oc), density
+            assert np.array_equal(tau, otau) and np.array_equal(kp, okp), density
+
+
 @pytest.mark.parametrize("bl", [0, 64, 1024])
 def test_skim_full_permutation_and_resume(pkg, bl):
     g = synth.random_small_graph(200, 1200, 8)
