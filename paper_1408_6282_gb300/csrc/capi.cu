@@ -539,6 +539,10 @@ int reset_stats(skim_ctx *c) {
 }
 
 constexpr double kSkimVisitBudget = 4.0e6;
+#ifndef SKIM_BUILD_GROWTH
+#define SKIM_BUILD_GROWTH 32
+#endif
+constexpr uint64_t kBuildGrowth = SKIM_BUILD_GROWTH;  // lanes of a build batch over the last one, at most
 
 uint32_t default_lanes(skim_ctx *c) {
     uint64_t b = c->batch_cfg ? c->batch_cfg : (1u << 21);
@@ -1332,12 +1336,14 @@ int skim_build_sketches(skim_ctx *c) {
         RC(clear_batch(c));
         p0 += b;
         c->hstats[SKIM_STAT_RANKS] += b;
-        // next batch: double, but keep the visit records near a quarter of
-        // the table (dense instances can give thousands of records per lane)
+        // next batch: up to kBuildGrowth times larger, but keep the visit
+        // records near a quarter of the table (dense instances can give
+        // thousands of records per lane).  Each batch costs at least the
+        // latency of its deepest search, so small batches are left quickly.
         const double per_lane = static_cast<double>(recs ? recs : 1) / b;
         rpl = per_lane;
         const uint64_t fit = static_cast<uint64_t>(static_cast<double>(c->rcap) / 4.0 / per_lane);
-        B = static_cast<uint32_t>(std::max<uint64_t>(64, std::min<uint64_t>({Bmax, 2ull * B, fit})));
+        B = static_cast<uint32_t>(std::max<uint64_t>(64, std::min<uint64_t>({Bmax, kBuildGrowth * B, fit})));
     }
     uint64_t batches = c->hstats[SKIM_STAT_BATCHES], ranks = c->hstats[SKIM_STAT_RANKS],
              retries = c->hstats[SKIM_STAT_RETRIES];
