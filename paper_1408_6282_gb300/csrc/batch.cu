@@ -219,7 +219,12 @@ __global__ void k_candidates(const uint64_t *rec_key, const uint32_t *rec_val, u
             const unsigned actb = __ballot_sync(kFull, act);
             if (!actb) break;
             const uint64_t v = key >> tbits, t = key & tmask;
-            if (act) m = hvals[2ull * rec_val[rr]] & alive[t] & range_mask(t, lo, 0xffffffffu);
+            // lanes of the record's word from lo on; its lane bits (a random
+            // table read) only when some are left
+            if (act) {
+                m = range_mask(t, lo, 0xffffffffu);
+                if (m) m &= hvals[2ull * rec_val[rr]] & alive[t];
+            }
             const uint32_t c = __popcll(m);
             // inclusive count of v's bits up to this record (runs are contiguous)
             uint32_t incl = c;
@@ -258,7 +263,9 @@ __global__ void k_commit_count(const uint64_t *rec_key, const uint32_t *rec_val,
          r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         const uint64_t key = rec_key[r];
         const uint64_t t = key & tmask;
-        uint64_t m = hvals[2ull * rec_val[r]] & alive[t] & range_mask(t, lo, hi);
+        uint64_t m = range_mask(t, lo, hi);
+        if (!m) continue;
+        m &= hvals[2ull * rec_val[r]] & alive[t];
         if (!m) continue;
         const uint32_t c = __popcll(m);
         atomicAdd(&size[key >> tbits], c);
@@ -282,7 +289,8 @@ __global__ void k_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_va
          r += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
         const uint64_t v = rec_key[r] >> tbits;
         const uint64_t t = rec_key[r] & tmask;
-        uint64_t m = hvals[2ull * rec_val[r]] & alive[t] & range_mask(t, lo, hi);
+        uint64_t m = range_mask(t, lo, hi);
+        if (m) m &= hvals[2ull * rec_val[r]] & alive[t];
         while (m) {
             int j = __ffsll(m) - 1;
             m &= m - 1;

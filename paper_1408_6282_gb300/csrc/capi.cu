@@ -538,7 +538,10 @@ int reset_stats(skim_ctx *c) {
     return SKIM_OK;
 }
 
-constexpr double kSkimVisitBudget = 4.0e6;
+#ifndef SKIM_VISIT_BUDGET
+#define SKIM_VISIT_BUDGET 4.0e6
+#endif
+constexpr double kSkimVisitBudget = SKIM_VISIT_BUDGET;  // visits a SKIM batch aims at
 #ifndef SKIM_BUILD_GROWTH
 #define SKIM_BUILD_GROWTH 32
 #endif
