@@ -312,8 +312,9 @@ def test_rmat22_wc_sketches_full_size(pkg):
 
 
 def test_rmat24_p01_skim_full_size(pkg):
-    """R-MAT scale 24, uniform p = 0.01, l = k = 64: 200 SKIM seeds against
-    stored oracle values."""
+    """R-MAT scale 24, uniform p = 0.01, l = k = 64: every sketch (where the
+    oracle's digest is stored), sampled rows, the query set and 200 SKIM seeds
+    against stored oracle values."""
     gold = _golden("rmat24_p01")
     if "skim" not in gold:
         pytest.skip("no stored seeds")
@@ -322,6 +323,16 @@ def test_rmat24_p01_skim_full_size(pkg):
     assert g.digest() == gold["graph_sha256"]
     ks = w.keys()
     with pkg.Skim(g.n, g.src, g.dst, w.l, w.k, w.prob_model, w.p, ks.coin, ks.rank, ks.prob) as sk:
+        if "sketches" in gold:
+            sk.build_sketches()
+            x, ln = sk.sketches()
+            for v, row in gold["sketches"]["sample_rows"].items():
+                assert [str(int(r)) for r in x[int(v), : ln[int(v)]]] == row
+            assert _digest(x, ln) == gold["sketches"]["sha256"]
+            del x, ln
+            est = sk.query_batch([q["seeds"] for q in gold["queries"]])
+            for q, e in zip(gold["queries"], est):
+                assert _close(float(e), q["estimate"])
         _check_skim(sk, gold["skim"], w.seeds)
 
 
