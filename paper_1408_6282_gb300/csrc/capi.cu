@@ -447,7 +447,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
 #define SKIM_REV_RING 1
 #endif
     // SKIM_TRACE_BATCHES=1 in the environment: one line per batch on stderr
-    // (lanes, records, visits, device time of its searches)
+    // (search kernel, lanes, records, visits, device time of its searches)
     static const bool trace = getenv("SKIM_TRACE_BATCHES") != nullptr;
     cudaEvent_t tr0 = nullptr, tr1 = nullptr;
     if (trace) {
@@ -455,7 +455,8 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         cudaEventCreate(&tr1);
         cudaEventRecord(tr0, c->st);
     }
-    if (c->mat && SKIM_REV_RING && est_per_lane > 0 && est_per_lane <= c->ring_rpl) {
+    const bool use_ring = c->mat && SKIM_REV_RING && est_per_lane > 0 && est_per_lane <= c->ring_rpl;
+    if (use_ring) {
         const RevSources rs{c->spair + p0, B, mode_build ? nullptr : c->covered, mode_build ? nullptr : c->alive};
         RC(run_traversal(c, a, false, &R, &rs));
     } else {
@@ -471,8 +472,8 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         cudaEventSynchronize(tr1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, tr0, tr1);
-        fprintf(stderr, "skim batch %s p0=%llu B=%u records=%llu visits=%llu ms=%.4f\n", mode_build ? "build" : "skim",
-                static_cast<unsigned long long>(p0), B, static_cast<unsigned long long>(R),
+        fprintf(stderr, "skim batch %s %s p0=%llu B=%u records=%llu visits=%llu ms=%.4f\n", mode_build ? "build" : "skim",
+                use_ring ? "ring" : "queue", static_cast<unsigned long long>(p0), B, static_cast<unsigned long long>(R),
                 static_cast<unsigned long long>(c->hctl->stats[kStRevVisits]), ms);
         cudaEventDestroy(tr0);
         cudaEventDestroy(tr1);
@@ -546,6 +547,10 @@ constexpr double kSkimVisitBudget = SKIM_VISIT_BUDGET;  // visits a SKIM batch a
 #define SKIM_BUILD_GROWTH 32
 #endif
 constexpr uint64_t kBuildGrowth = SKIM_BUILD_GROWTH;  // lanes of a build batch over the last one, at most
+#ifndef SKIM_BUILD_FIRST
+#define SKIM_BUILD_FIRST 256
+#endif
+constexpr uint32_t kBuildFirst = SKIM_BUILD_FIRST;  // lanes of the first build batch
 
 uint32_t default_lanes(skim_ctx *c) {
     uint64_t b = c->batch_cfg ? c->batch_cfg : (1u << 21);
@@ -1317,7 +1322,10 @@ int skim_build_sketches(skim_ctx *c) {
     RC(reset_stats(c));
     c->built = false;
     const uint32_t Bmax = default_lanes(c);
-    uint32_t B = std::min<uint32_t>(Bmax, 1u << 12);
+    // The first batch is small: the searches of the lowest ranks can each
+    // reach a large part of the graph (thousands of records per lane on
+    // hub-heavy graphs), and the next batch is sized from this one.
+    uint32_t B = std::min<uint32_t>(Bmax, kBuildFirst);
     uint64_t p0 = 0;
     double rpl = 0;  // records per lane of the last batch (0: unknown)
     while (p0 < c->nbuild) {

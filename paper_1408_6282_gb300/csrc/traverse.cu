@@ -692,120 +692,10 @@ SKIM_DEV void process_items(const TravArgs &A, Acc &acc, SK &sk, bool have, cons
     for (uint32_t st = 0; st < steps; st++) expand_step<FWD, MAT>(A, acc, sk, d, st * kUnroll, 1, mine != 0, ginst);
 }
 
-// Items a warp finishes before it adds them to the shared done count with one
-// atomic (the queue cursors are single words that every warp updates).
-constexpr unsigned long long kDoneBatch = 64;
-
-template <bool FWD, bool MAT>
-__global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse(TravArgs A) {
-    __shared__ uint64_t ginst[64];  // (i + 1) * G for instance i (residual searches)
-    if (threadIdx.x < 64) ginst[threadIdx.x] = kGolden * static_cast<uint64_t>(threadIdx.x + 1);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    DevCtl *C = A.ctl;
-    Acc acc;
-    GlobalSink gsink;
-    uint64_t t_progress = globaltimer();
-    unsigned long long seen_done = ld_volatile(&C->q_done.v);
-    // items this warp has finished but not yet added to the done count: added
-    // in batches, and always before the warp waits or leaves (a done count
-    // that lags only delays the drain test)
-    unsigned long long done_pend = 0;
-    bool done = false;
-    while (!done) {
-        // Claims are interleaved across warps: claim c of a grid with W warps
-        // takes, for lane l, queue slot (c / W) * 32W + l * W + (c mod W), so
-        // consecutive items go to different warps.  (With contiguous claims
-        // a narrow search - one seed - would run on a single warp.)
-        unsigned long long claim = 0;
-        if (lane == 0) claim = atomicAdd(&C->q_head.v, 1ull);
-        claim = __shfl_sync(kFull, claim, 0);
-        const unsigned long long W = static_cast<unsigned long long>(gridDim.x) * (blockDim.x / 32);
-        const unsigned long long slot = (claim / W) * 32 * W + static_cast<unsigned long long>(lane) * W + claim % W;
-        bool pending = slot < A.qcap;
-        bool empty = !pending;  // resolved without an item
-        unsigned backoff = 32, polls = 0;
-        for (;;) {
-            Item it{0, 0, 0};
-            bool have = false;
-            if (pending && read_item(A, slot, &it)) {
-                have = true;
-                pending = false;
-            }
-            const unsigned hb = __ballot_sync(kFull, have);
-            if (hb) {
-                process_items<FWD, MAT>(A, acc, gsink, have, it, ginst);
-                // The drain test reads done, then tail, so the slots reserved
-                // while processing must be counted in tail before these items
-                // count as done.  No fence is needed: lane 0 made every
-                // reservation of this warp with an atomic whose result it has
-                // already used, so that atomic has been performed at the point
-                // of coherence before this one is issued.  (Items themselves are
-                // found by their non-zero fields, not by ordering.)
-                acc.pushed = false;
-                done_pend += __popc(hb);
-                if (done_pend >= kDoneBatch) {
-                    if (lane == 0) atomicAdd(&C->q_done.v, done_pend);
-                    done_pend = 0;
-                }
-                t_progress = globaltimer();
-                backoff = 32;
-                polls = 0;
-            } else if (__any_sync(kFull, pending)) {
-                if (done_pend) {
-                    if (lane == 0) atomicAdd(&C->q_done.v, done_pend);
-                    done_pend = 0;
-                }
-                // nothing ready: items are still being written, more may be
-                // pushed, or the queue has drained.  The shared cursors are
-                // read only every 8th poll of the warp's own slots.
-                if ((++polls & 7) == 0) {
-                    unsigned long long d = ld_volatile(&C->q_done.v);
-                    __threadfence();
-                    unsigned long long tl = ld_volatile(&C->q_tail.v);
-                    if (d == tl && pending && slot >= tl) {
-                        pending = false;
-                        empty = true;
-                    }
-                    if (d != seen_done) {
-                        seen_done = d;
-                        t_progress = globaltimer();
-                    }
-                }
-                const bool other_gave_up =
-                    (polls & 7) == 0 && (*reinterpret_cast<volatile unsigned *>(&C->err) & kErrTimeout);
-                const bool gave_up = globaltimer() - t_progress > A.timeout_ns;
-                if (__any_sync(kFull, gave_up) && lane == 0) atomicOr(&C->err, kErrTimeout);
-                if (__any_sync(kFull, gave_up || other_gave_up)) {
-                    done = true;
-                    break;
-                }
-#ifndef SKIM_SPIN
-#define SKIM_SPIN 0
-#endif
-#if SKIM_SPIN == 0
-                __nanosleep(backoff);
-                if (backoff < 512) backoff <<= 1;
-#elif SKIM_SPIN == 2
-                {
-                    const long long t0 = clock64();
-                    while (clock64() - t0 < 256) {
-                    }
-                }
-#endif
-            }
-            if (!__any_sync(kFull, pending)) break;
-        }
-        if (__any_sync(kFull, empty)) done = true;
-    }
-    if (done_pend && lane == 0) atomicAdd(&C->q_done.v, done_pend);
-    flush_acc(A, acc, FWD);
-}
-
 // ---- Reverse searches over materialised live rows, with per-warp queues ----
 //
-// The global queue above costs every item a 16-byte write and read in global
-// memory and an atomic on a cursor that every warp shares.  Here each warp
+// The global queue (k_traverse, below) costs every item a 16-byte write and
+// read in global memory and an atomic on a cursor that every warp shares.  Here each warp
 // keeps the row items it creates in a ring of its own in shared memory and
 // takes its next items from there, and stages its visit records in shared
 // memory, writing them 32 or more at a time with one atomic.  The batch's
@@ -1178,6 +1068,143 @@ __global__ void __launch_bounds__(kRingThreads, SKIM_RING_MIN_BLOCKS) k_rev_ring
     }
     sk.flush(A);
     flush_acc(A, acc, false);
+}
+
+// ---- The global-queue search ----
+
+// Items a warp finishes before it adds them to the shared done count with one
+// atomic (the queue cursors are single words that every warp updates).
+constexpr unsigned long long kDoneBatch = 64;
+
+// Reverse searches over materialised rows (MAT) stage their visit records in
+// shared memory and spread the entries of small row items over the warp's
+// lanes, as the per-warp-queue search does (a RingSink whose ring limit is 0
+// puts every row item into the global queue).
+template <bool FWD, bool MAT>
+__global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse(TravArgs A) {
+    constexpr bool kStaged = !FWD && MAT;
+    __shared__ uint64_t ginst[64];  // (i + 1) * G for instance i (residual searches)
+    __shared__ uint64_t s_rk[kStaged ? kTravThreads / 32 : 1][kStaged ? kRecStage : 1];
+    __shared__ uint32_t s_rs[kStaged ? kTravThreads / 32 : 1][kStaged ? kRecStage : 1];
+    if (threadIdx.x < 64) ginst[threadIdx.x] = kGolden * static_cast<uint64_t>(threadIdx.x + 1);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    DevCtl *C = A.ctl;
+    Acc acc;
+    GlobalSink gsink;
+    const uint32_t wib = kStaged ? threadIdx.x >> 5 : 0;
+    RingSink ssink{nullptr, s_rk[wib], s_rs[wib], 0, 0, 0, 0};
+    uint64_t t_progress = globaltimer();
+    unsigned long long seen_done = ld_volatile(&C->q_done.v);
+    // items this warp has finished but not yet added to the done count: added
+    // in batches, and always before the warp waits or leaves (a done count
+    // that lags only delays the drain test)
+    unsigned long long done_pend = 0;
+    unsigned steps = 0;
+    bool done = false;
+    while (!done) {
+        // Claims are interleaved across warps: claim c of a grid with W warps
+        // takes, for lane l, queue slot (c / W) * 32W + l * W + (c mod W), so
+        // consecutive items go to different warps.  (With contiguous claims
+        // a narrow search - one seed - would run on a single warp.)
+        unsigned long long claim = 0;
+        if (lane == 0) claim = atomicAdd(&C->q_head.v, 1ull);
+        claim = __shfl_sync(kFull, claim, 0);
+        const unsigned long long W = static_cast<unsigned long long>(gridDim.x) * (blockDim.x / 32);
+        const unsigned long long slot = (claim / W) * 32 * W + static_cast<unsigned long long>(lane) * W + claim % W;
+        bool pending = slot < A.qcap;
+        bool empty = !pending;  // resolved without an item
+        unsigned backoff = 32, polls = 0;
+        for (;;) {
+            Item it{0, 0, 0};
+            bool have = false;
+            if (pending && read_item(A, slot, &it)) {
+                have = true;
+                pending = false;
+            }
+            const unsigned hb = __ballot_sync(kFull, have);
+            if (hb) {
+                if constexpr (kStaged)
+                    ring_expand(A, acc, ssink, have, it);
+                else
+                    process_items<FWD, MAT>(A, acc, gsink, have, it, ginst);
+                // The drain test reads done, then tail, so the slots reserved
+                // while processing must be counted in tail before these items
+                // count as done.  No fence is needed: lane 0 made every
+                // reservation of this warp with an atomic whose result it has
+                // already used, so that atomic has been performed at the point
+                // of coherence before this one is issued.  (Items themselves are
+                // found by their non-zero fields, not by ordering.)
+                acc.pushed = false;
+                done_pend += __popc(hb);
+                if (done_pend >= kDoneBatch) {
+                    if (lane == 0) atomicAdd(&C->q_done.v, done_pend);
+                    done_pend = 0;
+                }
+                t_progress = globaltimer();
+                backoff = 32;
+                polls = 0;
+                // a batch that overflowed its tables is re-run smaller: stop
+                // soon rather than finish a search whose result is dropped
+                if ((++steps & 15) == 0) {
+                    unsigned e = 0;
+                    if (lane == 0) e = *reinterpret_cast<volatile unsigned *>(&C->err);
+                    if (__shfl_sync(kFull, e, 0) & (kErrRetryable | kErrTimeout)) {
+                        done = true;
+                        break;
+                    }
+                }
+            } else if (__any_sync(kFull, pending)) {
+                if (done_pend) {
+                    if (lane == 0) atomicAdd(&C->q_done.v, done_pend);
+                    done_pend = 0;
+                }
+                // nothing ready: items are still being written, more may be
+                // pushed, or the queue has drained.  The shared cursors are
+                // read only every 8th poll of the warp's own slots.
+                if ((++polls & 7) == 0) {
+                    unsigned long long d = ld_volatile(&C->q_done.v);
+                    __threadfence();
+                    unsigned long long tl = ld_volatile(&C->q_tail.v);
+                    if (d == tl && pending && slot >= tl) {
+                        pending = false;
+                        empty = true;
+                    }
+                    if (d != seen_done) {
+                        seen_done = d;
+                        t_progress = globaltimer();
+                    }
+                }
+                // stop when another warp gave up or the batch overflowed
+                const bool stopped = (polls & 7) == 0 && (*reinterpret_cast<volatile unsigned *>(&C->err) &
+                                                          (kErrTimeout | kErrRetryable));
+                const bool gave_up = globaltimer() - t_progress > A.timeout_ns;
+                if (__any_sync(kFull, gave_up) && lane == 0) atomicOr(&C->err, kErrTimeout);
+                if (__any_sync(kFull, gave_up || stopped)) {
+                    done = true;
+                    break;
+                }
+#ifndef SKIM_SPIN
+#define SKIM_SPIN 0
+#endif
+#if SKIM_SPIN == 0
+                __nanosleep(backoff);
+                if (backoff < 512) backoff <<= 1;
+#elif SKIM_SPIN == 2
+                {
+                    const long long t0 = clock64();
+                    while (clock64() - t0 < 256) {
+                    }
+                }
+#endif
+            }
+            if (!__any_sync(kFull, pending)) break;
+        }
+        if (__any_sync(kFull, empty)) done = true;
+    }
+    if (done_pend && lane == 0) atomicAdd(&C->q_done.v, done_pend);
+    if constexpr (kStaged) ssink.flush(A);
+    flush_acc(A, acc, FWD);
 }
 
 }  // namespace
