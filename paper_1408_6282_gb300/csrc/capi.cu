@@ -397,6 +397,12 @@ constexpr double kTableSlots = SKIM_TABLE_SLOTS;
 #define SKIM_RING_RECORDS_PER_LANE 8
 #endif
 constexpr double kRingRecordsPerLane = SKIM_RING_RECORDS_PER_LANE;
+#ifndef SKIM_NODE_HASH_WORDS
+#define SKIM_NODE_HASH_WORDS 64
+#endif
+// batches of at most this many lane words place a node's visited-table
+// entries side by side (traverse.cu: table_slot)
+constexpr uint32_t kNodeHashWords = SKIM_NODE_HASH_WORDS;
 
 int ensure_idx(skim_ctx *c, uint64_t need);
 
@@ -432,6 +438,7 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     if (!mode_build) CK(c, cudaMemsetAsync(c->alive, 0, T * sizeof(uint64_t), c->st));
     TravArgs a = base_args(c, false);
     a.tbits = tbits;
+    a.hnode = T <= kNodeHashWords ? 1 : 0;
     {
         uint64_t want = c->hcap;
         if (est_per_lane > 0)

@@ -39,6 +39,7 @@ struct TravArgs {
     uint32_t *rec_val;
     uint64_t rcap;
     uint32_t tbits;             // record key = (node << tbits) | word
+    uint32_t hnode;             // visited-table slots grouped by node (batches of few words)
     const uint8_t *lane_inst;   // instance of every lane of the batch
     const uint64_t *lane_g;     // per lane: (instance + 1) * G, the lane's coin-stream offset
     const uint64_t *he;         // per CSR edge: state of its coin stream, fmix(coin_key ^ (u << 32 | v))

@@ -102,15 +102,24 @@ SKIM_DEV bool hash_or_from(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uin
     return false;
 }
 
-SKIM_DEV uint64_t table_slot(uint64_t key, uint64_t hmask) { return fmix(key) & hmask; }
+// First visited-table slot of entry key = u << tbits | t.  With hnode set
+// (batches of few words) the entries of one node for different words lie
+// side by side, so that the lanes of a batch that reach the same node touch
+// one or two cache lines of the table rather than one each; a batch of many
+// words hashes the whole key (a hub's entries would otherwise form long runs
+// that other keys must probe across).
+SKIM_DEV uint64_t table_slot(uint64_t key, uint32_t tbits, uint32_t hnode, uint64_t hmask) {
+    if (hnode) return (fmix(key >> tbits) + (key & ((1ull << tbits) - 1))) & hmask;
+    return fmix(key) & hmask;
+}
 
 SKIM_DEV void load_slot(const uint64_t *hkeys, uint64_t h, uint64_t *k, uint64_t *b) {
     asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(*k), "=l"(*b) : "l"(&hkeys[2 * h]) : "memory");
 }
 
-SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint64_t key, uint64_t bits, uint64_t *old,
-                      uint64_t *slot, bool *first) {
-    const uint64_t h = table_slot(key, hmask);
+SKIM_DEV bool hash_or(uint64_t *hkeys, uint64_t *hvals, uint64_t hmask, uint32_t tbits, uint32_t hnode, uint64_t key,
+                      uint64_t bits, uint64_t *old, uint64_t *slot, bool *first) {
+    const uint64_t h = table_slot(key, tbits, hnode, hmask);
     uint64_t k, b;
     load_slot(hkeys, h, &k, &b);
     return hash_or_from(hkeys, hvals, hmask, key, bits, h, k, b, old, slot, first);
@@ -243,7 +252,7 @@ SKIM_DEV void emit_rev(const TravArgs &A, Acc &acc, bool act, uint32_t u, uint32
     if (act && bits) {
         uint64_t old;
         uint64_t key = (static_cast<uint64_t>(u) << A.tbits) | t;
-        if (hash_or(A.hkeys, A.hvals, A.hmask, key, bits, &old, &slot, &first)) {
+        if (hash_or(A.hkeys, A.hvals, A.hmask, A.tbits, A.hnode, key, bits, &old, &slot, &first)) {
             nb = bits & ~old;
         } else {
             atomicOr(&A.ctl->err, kErrHash);
@@ -319,7 +328,7 @@ SKIM_DEV void emit_rev_mat(const TravArgs &A, Acc &acc, SK &sk, bool act, uint32
     if (act) {
         // the first visited-table slot, and the row of (u, inst) with
         // Algorithm 2's pruning flag: independent loads, in flight together
-        h0 = table_slot(key, A.hmask);
+        h0 = table_slot(key, A.tbits, A.hnode, A.hmask);
         load_slot(A.hkeys, h0, &k0, &v0);
         const uint64_t r = static_cast<uint64_t>(u) * A.l + inst;
         const uint32_t w0 = A.loff[r], w1 = A.loff[r + 1];
