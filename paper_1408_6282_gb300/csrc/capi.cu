@@ -406,6 +406,11 @@ constexpr uint32_t kNodeHashWords = SKIM_NODE_HASH_WORDS;
 
 int ensure_idx(skim_ctx *c, uint64_t need);
 
+bool trace_batches() {
+    static const bool on = getenv("SKIM_TRACE_BATCHES") != nullptr;
+    return on;
+}
+
 // Buffers of the per-node record placement; the counters start at zero.
 int node_buffers(skim_ctx *c) {
     if (c->ncnt) return SKIM_OK;
@@ -454,12 +459,14 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
 #define SKIM_REV_RING 1
 #endif
     // SKIM_TRACE_BATCHES=1 in the environment: one line per batch on stderr
-    // (search kernel, lanes, records, visits, device time of its searches)
-    static const bool trace = getenv("SKIM_TRACE_BATCHES") != nullptr;
-    cudaEvent_t tr0 = nullptr, tr1 = nullptr;
+    // (search kernel, lanes, records, visits, device time of its searches and
+    // of its record sort)
+    const bool trace = trace_batches();
+    cudaEvent_t tr0 = nullptr, tr1 = nullptr, tr2 = nullptr;
     if (trace) {
         cudaEventCreate(&tr0);
         cudaEventCreate(&tr1);
+        cudaEventCreate(&tr2);
         cudaEventRecord(tr0, c->st);
     }
     const bool use_ring = c->mat && SKIM_REV_RING && est_per_lane > 0 && est_per_lane <= c->ring_rpl;
@@ -474,23 +481,29 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         }
         RC(run_traversal(c, a, false, &R));
     }
-    if (trace) {
-        cudaEventRecord(tr1, c->st);
-        cudaEventSynchronize(tr1);
-        float ms = 0.f;
+    if (trace) cudaEventRecord(tr1, c->st);
+    const auto trace_line = [&]() {
+        if (!trace) return;
+        cudaEventRecord(tr2, c->st);
+        cudaEventSynchronize(tr2);
+        float ms = 0.f, ms_sort = 0.f;
         cudaEventElapsedTime(&ms, tr0, tr1);
-        fprintf(stderr, "skim batch %s %s p0=%llu B=%u records=%llu visits=%llu ms=%.4f\n", mode_build ? "build" : "skim",
-                use_ring ? "ring" : "queue", static_cast<unsigned long long>(p0), B, static_cast<unsigned long long>(R),
-                static_cast<unsigned long long>(c->hctl->stats[kStRevVisits]), ms);
+        cudaEventElapsedTime(&ms_sort, tr1, tr2);
+        fprintf(stderr, "skim batch %s %s p0=%llu B=%u records=%llu visits=%llu ms=%.4f sort_ms=%.4f\n",
+                mode_build ? "build" : "skim", use_ring ? "ring" : "queue", static_cast<unsigned long long>(p0), B,
+                static_cast<unsigned long long>(R), static_cast<unsigned long long>(c->hctl->stats[kStRevVisits]), ms,
+                ms_sort);
         cudaEventDestroy(tr0);
         cudaEventDestroy(tr1);
-    }
+        cudaEventDestroy(tr2);
+    };
     const DevCtl &h = *c->hctl;
     if (h.err & kErrRetryable) {
         *retry = true;
         RC(reset_queue(c, h.q_tail.v));
         CK(c, cudaMemsetAsync(c->pend, 0, c->hcap * sizeof(uint64_t), c->st));
         c->hstats[SKIM_STAT_RETRIES]++;
+        trace_line();
         return SKIM_OK;
     }
     RC(reset_queue(c, h.q_tail.v));
@@ -516,11 +529,12 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
     c->bR = R;
     c->btbits = tbits;
     c->hstats[SKIM_STAT_BATCHES]++;
+    trace_line();
     return SKIM_OK;
 }
 
-// Release the active batch's records.  Its table slots need no clearing: the
-// next batch's keys carry a new generation.
+// Release the active batch's records (the next batch zeroes the part of the
+// visited table it uses).
 int clear_batch(skim_ctx *c) {
     c->bR = 0;
     c->bnode = false;
@@ -640,9 +654,28 @@ int commit_lanes(skim_ctx *c, uint32_t lo, uint32_t hi) {
 int residual(skim_ctx *c, uint32_t x, uint64_t *cov) {
     RC(reset_ctl(c));
     TravArgs a = base_args(c, true);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    const uint64_t v0 = trace_batches() ? c->hctl->stats[kStFwdVisits] : 0;
+    if (trace_batches()) {
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        cudaEventRecord(t0, c->st);
+    }
     CK(c, launch_fwd_source(a, x, c->st));
     RC(run_traversal(c, a, true, nullptr));
     *cov = c->hctl->ix_cov;
+    if (trace_batches()) {  // one line per residual search
+        cudaEventRecord(t1, c->st);
+        cudaEventSynchronize(t1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        fprintf(stderr, "skim residual seed=%u visits=%llu edges=%llu cov=%llu ms=%.4f\n", x,
+                static_cast<unsigned long long>(c->hctl->stats[kStFwdVisits] - v0),
+                static_cast<unsigned long long>(c->hctl->stats[kStFwdEdges]), static_cast<unsigned long long>(*cov),
+                ms);
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+    }
     RC(reset_queue(c, c->hctl->q_tail.v));
     CK(c, cudaMemsetAsync(c->chosen + x, 1, 1, c->st));
     return SKIM_OK;
@@ -1014,7 +1047,11 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         // visit records per batch: a few per lane; sized generously so that
         // re-running a batch with fewer lanes stays rare
         const uint64_t lanes_max = std::min<uint64_t>(npos, prm->batch_lanes ? prm->batch_lanes : (1u << 21));
-        const uint64_t rcap = std::min<uint64_t>(std::max<uint64_t>(16ull * lanes_max, 1u << 20), 1ull << 26);
+#ifndef SKIM_RECORDS_PER_LANE
+#define SKIM_RECORDS_PER_LANE 16
+#endif
+        const uint64_t rcap =
+            std::min<uint64_t>(std::max<uint64_t>(SKIM_RECORDS_PER_LANE * lanes_max, 1u << 20), 1ull << 26);
         size_t ws = std::max({scan_workspace_bytes(static_cast<size_t>(n) + 1), scan_workspace_bytes(nl + 1),
                               scan_workspace_bytes(rcap + 1),
                               radix_workspace_bytes(m),
@@ -1347,8 +1384,23 @@ int skim_build_sketches(skim_ctx *c) {
         }
         {
             KTimer kt(c, SKIM_K_ACCEPT);
+            cudaEvent_t t0 = nullptr, t1 = nullptr;
+            if (trace_batches()) {
+                cudaEventCreate(&t0);
+                cudaEventCreate(&t1);
+                cudaEventRecord(t0, c->st);
+            }
             CK(c, launch_accept(c->rkey, c->rval, c->hvals, c->bR, c->btbits, c->lane_inst, c->srank + p0, c->l,
                                 c->k, c->lcnt, c->full, c->mat ? c->loff : nullptr, c->X, c->xlen, c->ctl, c->st));
+            if (trace_batches()) {
+                cudaEventRecord(t1, c->st);
+                cudaEventSynchronize(t1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, t0, t1);
+                fprintf(stderr, "skim accept p0=%llu ms=%.4f\n", static_cast<unsigned long long>(p0), ms);
+                cudaEventDestroy(t0);
+                cudaEventDestroy(t1);
+            }
         }
         const uint64_t recs = c->bR;
         RC(clear_batch(c));
@@ -1360,7 +1412,10 @@ int skim_build_sketches(skim_ctx *c) {
         // latency of its deepest search, so small batches are left quickly.
         const double per_lane = static_cast<double>(recs ? recs : 1) / b;
         rpl = per_lane;
-        const uint64_t fit = static_cast<uint64_t>(static_cast<double>(c->rcap) / 4.0 / per_lane);
+#ifndef SKIM_BUILD_FILL
+#define SKIM_BUILD_FILL 4.0
+#endif
+        const uint64_t fit = static_cast<uint64_t>(static_cast<double>(c->rcap) / SKIM_BUILD_FILL / per_lane);
         B = static_cast<uint32_t>(std::max<uint64_t>(64, std::min<uint64_t>({Bmax, kBuildGrowth * B, fit})));
     }
     uint64_t batches = c->hstats[SKIM_STAT_BATCHES], ranks = c->hstats[SKIM_STAT_RANKS],
