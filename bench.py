@@ -119,18 +119,20 @@ class Clocks:
 
 
 def traffic_record(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    this workload and the kernel's source has not changed since."""
+    """DRAM bytes per launch of a kernel group on a workload, from the
+    committed ncu summaries (profiles/traffic.json), if the kernels' source
+    has not changed since they were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path)).get(kernel)
-    if not rec or rec.get("workload") != workload:
-        return None
-    src = os.path.join(ROOT, "paper_1408_6282_gb300", "csrc", rec["source"])
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
-        return None
-    return rec
+    for rec in json.load(open(path)).get("records", []):
+        if rec.get("kernel") != kernel or rec.get("workload") != workload:
+            continue
+        src = os.path.join(ROOT, "paper_1408_6282_gb300", "csrc", rec["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+            return None
+        return rec
+    return None
 
 
 def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms, workload, gather=None):
@@ -170,7 +172,7 @@ def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms, wo
         byts = 28 * cand + 12 * E
         units = (f"{cand} candidate visits ({lanes} source lanes + {L} live in-edges) x 28 B + {E} expansions "
                  "x 12 B per step")
-        key = "k_rev_ring"
+        key = "rev_search"
         if gather:
             # each candidate costs at least two independent random accesses
             # (its row entry and its visited slot) and each live in-edge's id
@@ -185,7 +187,7 @@ def kernel_roofline(kname, kt, gold, m, l, steps, sm_max, hbm_peak, total_ms, wo
         E, L, X = sm["fwd_expansions"], sm.get("fwd_live_edges", 0), sm["index_erased"]
         byts = 16 * E + 20 * L + 8 * X
         units = f"{E} forward expansions x 16 B + {L} live out-edges x 20 B + {X} index entries x 8 B per step"
-        key = "k_traverse_fwd"
+        key = "fwd_search"
     achieved = byts / sec / 1e9
     trb = traffic_record(key, workload)
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,

@@ -357,6 +357,8 @@ WORKLOADS = {
     "rmat18_wc": Workload("rmat18_wc", 3, "rmat", 18, 16, 1, 0.0, 64, 64, 50),
     "rmat20_wc": Workload("rmat20_wc", 2, "rmat", 20, 16, 1, 0.0, 64, 64, 50),
     "rmat22_wc": Workload("rmat22_wc", 4, "rmat", 22, 16, 1, 0.0, 64, 64, 0),
+    # the hub-heavy searches of R-MAT 24 p = 0.01 at a sixteenth of its size
+    "rmat20_p01": Workload("rmat20_p01", 6, "rmat", 20, 16, 0, 0.01, 64, 64, 50),
     "rmat24_p01": Workload("rmat24_p01", 5, "rmat", 24, 16, 0, 0.01, 64, 64, 200),
 }
 

@@ -213,9 +213,10 @@ def _golden(name):
     return json.load(open(path))
 
 
-@pytest.mark.parametrize("name", ["rmat18_wc", "rmat20_wc"])
+@pytest.mark.parametrize("name", ["rmat18_wc", "rmat20_wc", "rmat20_p01"])
 def test_rmat_wc_full_size(pkg, name):
-    """R-MAT scale 18 and 20, weighted cascade, l = k = 64: every sketch, 50
+    """R-MAT scale 18 and 20 with weighted cascade, and scale 20 with uniform
+    p = 0.01 (hub-heavy searches, as at scale 24), l = k = 64: every sketch, 50
     SKIM seeds and the query set against stored oracle values."""
     gold = _golden(name)
     w = synth.WORKLOADS[name]
