@@ -67,11 +67,14 @@ def test_traffic_record_only_for_its_workload_and_source():
     import json
 
     import bench
-    recs = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
-    for kernel, rec in recs.items():
+    recs = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["records"]
+    assert recs
+    for rec in recs:
         src = os.path.join(bench.ROOT, "paper_1408_6282_gb300", "csrc", rec["source"])
         current = hashlib.sha256(open(src, "rb").read()).hexdigest() == rec["source_sha256"]
-        got = bench.traffic_record(kernel, rec["workload"])
+        got = bench.traffic_record(rec["kernel"], rec["workload"])
         assert (got is not None) == current
-        assert bench.traffic_record(kernel, rec["workload"] + "_other") is None
+        if got is not None:
+            assert got["dram_bytes_per_launch"] == rec["dram_bytes_per_launch"]
+        assert bench.traffic_record(rec["kernel"], rec["workload"] + "_other") is None
     assert bench.traffic_record("no_such_kernel", "rmat20_wc") is None
