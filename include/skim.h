@@ -138,10 +138,12 @@ int skim_autotune_batch_lanes(skim_ctx *ctx, const uint32_t *candidates, uint32_
  *                          shared memory; larger searches share one global
  *                          queue over the whole GPU (default 8; 0 = always
  *                          the global queue);
- *   node_sort_density      a batch's visit records are placed node by node
- *                          (counting pass over the n nodes) when
- *                          n <= node_sort_density * records, else radix
- *                          sorted (default 4; >= 1). */
+ *   node_sort_density      a batch's visit records are placed by node
+ *                          buckets (a counting pass over buckets of 2^s
+ *                          consecutive nodes, s chosen for about one bucket
+ *                          per record) when the buckets number at most
+ *                          node_sort_density * records, else radix sorted
+ *                          (default 4; 0 = always radix sorted). */
 typedef struct {
     uint32_t batch_lanes;
     double ring_records_per_lane;
@@ -155,7 +157,7 @@ int skim_set_tuning(skim_ctx *ctx, const skim_tuning *t);
  * writes its index to *best (count if every build failed; the settings are
  * then left as they were).  seconds (host, optional): each candidate's build
  * time.  Errors: SKIM_EINVAL for a candidate with a negative records
- * threshold or a zero density; a failing build's code. */
+ * threshold; a failing build's code. */
 int skim_autotune(skim_ctx *ctx, const skim_tuning *candidates, uint32_t count, uint32_t *best, double *seconds);
 
 /* Recompute the rank order of the n*l pairs (done by skim_create; exposed so

@@ -29,7 +29,7 @@ struct skim_ctx {
     uint32_t batch_cfg = 0;
     // switches of the rank-batched search (skim_set_tuning): per-warp queues
     // for batches of at most ring_rpl expected records per lane; records
-    // placed node by node when n <= node_density * records
+    // placed by node buckets when buckets <= node_density * records
     double ring_rpl = 0;
     uint32_t node_density = 0;
     // graph
@@ -382,10 +382,16 @@ int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out, const
     }
 }
 
-// A batch's records are placed node by node when there are at least n / 4
-// of them; below that the pass over the n node counters costs more than a
-// radix sort of the records.
+// A batch's records are placed by node (or node bucket) when there are at
+// least a quarter as many of them as buckets; below that the pass over the
+// counters costs more than a radix sort of the records.
 constexpr uint64_t kNodeSortDensity = 4;
+// widest low key part the per-node placement orders (its block pass marks
+// 2^kPlaceBits bits in shared memory)
+#ifndef SKIM_PLACE_BITS
+#define SKIM_PLACE_BITS 19
+#endif
+constexpr uint32_t kPlaceBits = SKIM_PLACE_BITS;
 
 #ifndef SKIM_TABLE_SLOTS
 #define SKIM_TABLE_SLOTS 4
@@ -514,14 +520,21 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         c->idx_bound += vis;
     }
     const int bits = bitlen(c->n - 1) + static_cast<int>(tbits);
-    // records dense over the nodes: place them node by node (one pass over
-    // the n node counters); sparse: radix sort over the key bits
-    c->bnode = static_cast<uint64_t>(c->n) <= static_cast<uint64_t>(c->node_density) * R;
+    // Records are placed node by node (one pass over per-node counters) when
+    // they are dense over the nodes.  Sparser batches are placed by buckets of
+    // 2^sb consecutive nodes instead, about one bucket per record: a bucket's
+    // records are put in (node, word) order as a node's are in word order,
+    // the key's low tbits + sb bits playing the word (at most kPlaceBits, the
+    // block pass's bitmap).  The rest is radix-sorted over the key bits.
+    uint32_t sb = 0;
+    while (sb + tbits < kPlaceBits && (static_cast<uint64_t>(c->n) >> sb) > std::max<uint64_t>(R, 1)) sb++;
+    const uint32_t nb = static_cast<uint32_t>((static_cast<uint64_t>(c->n) + (1ull << sb) - 1) >> sb);
+    c->bnode = static_cast<uint64_t>(nb) <= static_cast<uint64_t>(c->node_density) * R;
     if (c->bnode) RC(node_buffers(c));
     {
         KTimer kt(c, SKIM_K_SORT);
         if (c->bnode)
-            CK(c, launch_node_sort(c->rkey, c->rval, R, tbits, c->n, c->ncnt, c->noff, c->rkey2, c->nlist,
+            CK(c, launch_node_sort(c->rkey, c->rval, R, tbits + sb, nb, c->ncnt, c->noff, c->rkey2, c->nlist,
                                    c->nlist_cnt, c->ws, c->st));
         else
             CK(c, radix_sort_pairs(c->rkey, c->rval, c->rkey2, c->rval2, R, bits, c->ws, c->st));
@@ -1272,7 +1285,7 @@ int skim_get_tuning(skim_ctx *c, skim_tuning *out) {
 
 int skim_set_tuning(skim_ctx *c, const skim_tuning *t) {
     if (!c || !t) return SKIM_EINVAL;
-    if (!(t->ring_records_per_lane >= 0.0) || t->node_sort_density == 0) return SKIM_EINVAL;
+    if (!(t->ring_records_per_lane >= 0.0)) return SKIM_EINVAL;
     c->batch_cfg = t->batch_lanes;
     c->ring_rpl = t->ring_records_per_lane;
     c->node_density = t->node_sort_density;
@@ -1282,7 +1295,7 @@ int skim_set_tuning(skim_ctx *c, const skim_tuning *t) {
 int skim_autotune(skim_ctx *c, const skim_tuning *candidates, uint32_t count, uint32_t *best, double *seconds) {
     if (!c || !candidates || !count || !best) return SKIM_EINVAL;
     for (uint32_t i = 0; i < count; i++)
-        if (!(candidates[i].ring_records_per_lane >= 0.0) || candidates[i].node_sort_density == 0) return SKIM_EINVAL;
+        if (!(candidates[i].ring_records_per_lane >= 0.0)) return SKIM_EINVAL;
     skim_tuning keep{};
     skim_get_tuning(c, &keep);
     double best_t = 1e300;

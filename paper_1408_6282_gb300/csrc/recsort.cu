@@ -18,7 +18,10 @@
 //           the 2^tbits words (any s).
 //
 // The result is the same array a full sort gives (keys are distinct), and the
-// node offsets are left for the caller.
+// node offsets are left for the caller.  A caller may pass buckets of 2^s
+// consecutive nodes as the "nodes" (n / 2^s of them) and tbits + s as the
+// word bits: a bucket's records are then ordered by (node, word), which is the
+// key order too.
 #include "internal.cuh"
 #include "prims.cuh"
 

@@ -123,15 +123,15 @@ def test_small_graphs_coins_hashed_in_the_search(pkg, name, mk, l, k, model, p, 
 def test_search_kernels_each_alone(pkg, ring, name, mk, conf):
     """Every batch of reverse searches on the global queue (ring = 0), or every
     batch whose records per lane are known on the per-warp queues (ring =
-    1e9), with records placed by node or radix sorted: each setting gives the
-    oracle's sketches and seeds."""
+    1e9), with records radix sorted (density 0) or placed by node buckets:
+    each setting gives the oracle's sketches and seeds."""
     g = mk()
     l, k, model, p, bl = conf
     pb, sk = _both(pkg, g, l, k, model, p, 13, bl)
     ox, oln, _ = oracle.build_sketches(pb)
     os_, oc, otau, okp, _ = oracle.skim_stops(pb, min(g.n, 20))
     with sk:
-        for density in (1, 1 << 30):
+        for density in (0, 1, 1 << 30):
             sk.set_tuning(bl, ring, density)
             assert sk.tuning() == {"batch_lanes": bl, "ring_records_per_lane": ring, "node_sort_density": density}
             sk.build_sketches()
