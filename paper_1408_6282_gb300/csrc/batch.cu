@@ -186,14 +186,23 @@ SKIM_DEV uint64_t range_mask(uint64_t t, uint32_t lo, uint32_t hi) {
     return m;
 }
 
+// SKIM batches read a record's lane bits in every candidate scan and in both
+// commit passes: they are gathered once from the visited table, next to the
+// records, after the records are put in order.
+__global__ void k_gather_bits(const uint32_t *__restrict__ rec_val, const uint64_t *__restrict__ hvals, uint64_t R,
+                              uint64_t *__restrict__ rbits) {
+    for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
+         r += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+        rbits[r] = hvals[2ull * rec_val[r]];
+}
+
 // SKIM's stop: per node v the lane at which size[v] reaches k, i.e. the
 // need = k - size[v]-th uncovered lane bit (from lane lo on) of v's records in
 // rank order (a node already at k stops at its first record).  Warps own the
 // runs that start in 32-record windows, as in the acceptance; a segmented
 // scan over the lanes counts each node's bits in order.
-__global__ void k_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                             const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
-                             uint32_t k, DevCtl *ctl) {
+__global__ void k_candidates(const uint64_t *rec_key, const uint64_t *rbits, uint64_t R, uint32_t tbits,
+                             const uint64_t *alive, uint32_t lo, const uint32_t *size, uint32_t k, DevCtl *ctl) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t tmask = (1ull << tbits) - 1;
     const uint64_t warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -219,11 +228,11 @@ __global__ void k_candidates(const uint64_t *rec_key, const uint32_t *rec_val, u
             const unsigned actb = __ballot_sync(kFull, act);
             if (!actb) break;
             const uint64_t v = key >> tbits, t = key & tmask;
-            // lanes of the record's word from lo on; its lane bits (a random
-            // table read) only when some are left
+            // lanes of the record's word from lo on; its lane bits only when
+            // some are left
             if (act) {
                 m = range_mask(t, lo, 0xffffffffu);
-                if (m) m &= hvals[2ull * rec_val[rr]] & alive[t];
+                if (m) m &= rbits[rr] & alive[t];
             }
             const uint32_t c = __popcll(m);
             // inclusive count of v's bits up to this record (runs are contiguous)
@@ -254,8 +263,8 @@ __global__ void k_candidates(const uint64_t *rec_key, const uint32_t *rec_val, u
 // Commit of lanes [lo, hi]: size[v] += the committed uncovered lane bits of
 // v's records, and per lane the number of nodes it reaches (the index
 // segment lengths).  Additive, so one thread per record.
-__global__ void k_commit_count(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                               const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size,
+__global__ void k_commit_count(const uint64_t *rec_key, const uint64_t *rbits, uint64_t R, uint32_t tbits,
+                               const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size,
                                unsigned long long *lane_cnt, DevCtl *ctl) {
     const uint64_t tmask = (1ull << tbits) - 1;
     unsigned long long ins = 0;
@@ -265,7 +274,7 @@ __global__ void k_commit_count(const uint64_t *rec_key, const uint32_t *rec_val,
         const uint64_t t = key & tmask;
         uint64_t m = range_mask(t, lo, hi);
         if (!m) continue;
-        m &= hvals[2ull * rec_val[r]] & alive[t];
+        m &= rbits[r] & alive[t];
         if (!m) continue;
         const uint32_t c = __popcll(m);
         atomicAdd(&size[key >> tbits], c);
@@ -279,10 +288,9 @@ __global__ void k_commit_count(const uint64_t *rec_key, const uint32_t *rec_val,
     warp_add(&ctl->stats[kStInsert], ins);
 }
 
-__global__ void k_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                                 const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi,
-                                 const uint64_t *lane_off, uint32_t *lane_fill, const uint64_t *idx_ctr,
-                                 uint32_t *idx_nodes) {
+__global__ void k_commit_scatter(const uint64_t *rec_key, const uint64_t *rbits, uint64_t R, uint32_t tbits,
+                                 const uint64_t *alive, uint32_t lo, uint32_t hi, const uint64_t *lane_off,
+                                 uint32_t *lane_fill, const uint64_t *idx_ctr, uint32_t *idx_nodes) {
     const uint64_t tmask = (1ull << tbits) - 1;
     const uint64_t idx_base = idx_ctr[0];
     for (uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; r < R;
@@ -290,7 +298,7 @@ __global__ void k_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_va
         const uint64_t v = rec_key[r] >> tbits;
         const uint64_t t = rec_key[r] & tmask;
         uint64_t m = range_mask(t, lo, hi);
-        if (m) m &= hvals[2ull * rec_val[r]] & alive[t];
+        if (m) m &= rbits[r] & alive[t];
         while (m) {
             int j = __ffsll(m) - 1;
             m &= m - 1;
@@ -392,31 +400,37 @@ cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, cons
                                                lcnt, full, row_flag, X, xlen, ctl);
     return cudaGetLastError();
 }
-cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                              const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
-                              uint32_t k, DevCtl *ctl, cudaStream_t s) {
+cudaError_t launch_gather_bits(const uint32_t *rec_val, const uint64_t *hvals, uint64_t R, uint64_t *rbits,
+                               cudaStream_t s) {
     if (R == 0) return cudaSuccess;
     note_launch();
-    k_candidates<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, size, k, ctl);
+    k_gather_bits<<<grid_for(R, 256), 256, 0, s>>>(rec_val, hvals, R, rbits);
     return cudaGetLastError();
 }
-cudaError_t launch_commit_count(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                                const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size,
-                                uint64_t *lane_cnt, DevCtl *ctl, cudaStream_t s) {
+cudaError_t launch_candidates(const uint64_t *rec_key, const uint64_t *rbits, uint64_t R, uint32_t tbits,
+                              const uint64_t *alive, uint32_t lo, const uint32_t *size, uint32_t k, DevCtl *ctl,
+                              cudaStream_t s) {
     if (R == 0) return cudaSuccess;
     note_launch();
-    k_commit_count<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, hi, size,
+    k_candidates<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rbits, R, tbits, alive, lo, size, k, ctl);
+    return cudaGetLastError();
+}
+cudaError_t launch_commit_count(const uint64_t *rec_key, const uint64_t *rbits, uint64_t R, uint32_t tbits,
+                                const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size, uint64_t *lane_cnt,
+                                DevCtl *ctl, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    note_launch();
+    k_commit_count<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rbits, R, tbits, alive, lo, hi, size,
                                                     reinterpret_cast<unsigned long long *>(lane_cnt), ctl);
     return cudaGetLastError();
 }
-cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                                  const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi,
-                                  const uint64_t *lane_off, uint32_t *lane_fill, const uint64_t *idx_ctr,
-                                  uint32_t *idx_nodes, cudaStream_t s) {
+cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint64_t *rbits, uint64_t R, uint32_t tbits,
+                                  const uint64_t *alive, uint32_t lo, uint32_t hi, const uint64_t *lane_off,
+                                  uint32_t *lane_fill, const uint64_t *idx_ctr, uint32_t *idx_nodes, cudaStream_t s) {
     if (R == 0) return cudaSuccess;
     note_launch();
-    k_commit_scatter<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rec_val, R, tbits, hvals, alive, lo, hi, lane_off,
-                                                      lane_fill, idx_ctr, idx_nodes);
+    k_commit_scatter<<<grid_for(R, 256), 256, 0, s>>>(rec_key, rbits, R, tbits, alive, lo, hi, lane_off, lane_fill,
+                                                      idx_ctr, idx_nodes);
     return cudaGetLastError();
 }
 cudaError_t launch_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32_t hi, const uint64_t *lane_cnt,

@@ -71,6 +71,9 @@ struct skim_ctx {
     uint64_t hcap = 0;
     uint64_t *rkey = nullptr, *rkey2 = nullptr;
     uint32_t *rval = nullptr, *rval2 = nullptr;
+    // a SKIM batch's lane bits per record, gathered after the record order
+    // (the order's scratch rkey2, free until the next batch)
+    uint64_t *rbits = nullptr;
     uint64_t rcap = 0;
     // per-node placement of a batch's records (recsort.cu): counters (all
     // zero between batches), node offsets, node lists
@@ -539,6 +542,11 @@ int rev_batch(skim_ctx *c, uint64_t p0, uint32_t B, bool mode_build, bool *retry
         else
             CK(c, radix_sort_pairs(c->rkey, c->rval, c->rkey2, c->rval2, R, bits, c->ws, c->st));
     }
+    if (!mode_build) {
+        c->rbits = c->rkey2;
+        KTimer kt(c, SKIM_K_SORT);
+        CK(c, launch_gather_bits(c->rval, c->hvals, R, c->rbits, c->st));
+    }
     c->bR = R;
     c->btbits = tbits;
     c->hstats[SKIM_STAT_BATCHES]++;
@@ -651,11 +659,11 @@ int commit_lanes(skim_ctx *c, uint32_t lo, uint32_t hi) {
     CK(c, cudaMemsetAsync(c->lane_cnt + lo, 0, cnt * sizeof(uint64_t), c->st));
     CK(c, cudaMemsetAsync(c->lane_fill + lo, 0, cnt * sizeof(uint32_t), c->st));
     KTimer kt(c, SKIM_K_STEP);
-    CK(c, launch_commit_count(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, lo, hi, c->size, c->lane_cnt,
+    CK(c, launch_commit_count(c->rkey, c->rbits, c->bR, c->btbits, c->alive, lo, hi, c->size, c->lane_cnt,
                               c->ctl, c->st));
     CK(c, exclusive_scan_u64(c->lane_cnt + lo, c->lane_off + lo, cnt, reinterpret_cast<uint64_t *>(&c->ctl->total),
                              c->ws, c->st));
-    CK(c, launch_commit_scatter(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, lo, hi, c->lane_off,
+    CK(c, launch_commit_scatter(c->rkey, c->rbits, c->bR, c->btbits, c->alive, lo, hi, c->lane_off,
                                 c->lane_fill, c->idx_ctr, c->idx, c->st));
     CK(c, launch_commit_segments(c->spair + c->bp0, lo, hi, c->lane_cnt, c->lane_off, c->idx_ctr, c->seg_start,
                                  c->seg_len, c->st));
@@ -700,7 +708,7 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
             CK(c, cudaMemsetAsync(&c->ctl->best, 0xff, sizeof(unsigned long long), c->st));
             {
                 KTimer kt(c, SKIM_K_STEP);
-                CK(c, launch_candidates(c->rkey, c->rval, c->bR, c->btbits, c->hvals, c->alive, c->blo, c->size,
+                CK(c, launch_candidates(c->rkey, c->rbits, c->bR, c->btbits, c->alive, c->blo, c->size,
                                         c->k, c->ctl, c->st));
             }
             RC(sync_ctl(c));

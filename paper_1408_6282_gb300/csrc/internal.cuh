@@ -169,16 +169,19 @@ cudaError_t launch_accept(const uint64_t *rec_key, const uint32_t *rec_val, cons
 cudaError_t launch_node_sort(uint64_t *rec_key, uint32_t *rec_val, uint64_t R, uint32_t tbits, uint32_t n,
                              uint64_t *cnt, uint64_t *off, uint64_t *tmp, uint32_t *list, unsigned *nlist,
                              void *scan_ws, cudaStream_t s);
-cudaError_t launch_candidates(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                              const uint64_t *hvals, const uint64_t *alive, uint32_t lo, const uint32_t *size,
-                              uint32_t k, DevCtl *ctl, cudaStream_t s);
-cudaError_t launch_commit_count(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                                const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size,
-                                uint64_t *lane_cnt, DevCtl *ctl, cudaStream_t s);
-cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint32_t *rec_val, uint64_t R, uint32_t tbits,
-                                  const uint64_t *hvals, const uint64_t *alive, uint32_t lo, uint32_t hi,
-                                  const uint64_t *lane_off, uint32_t *lane_fill, const uint64_t *idx_ctr,
-                                  uint32_t *idx_nodes, cudaStream_t s);
+// SKIM batch: the records' lane bits gathered from the visited table into
+// rbits (R words), read by the three kernels below.
+cudaError_t launch_gather_bits(const uint32_t *rec_val, const uint64_t *hvals, uint64_t R, uint64_t *rbits,
+                               cudaStream_t s);
+cudaError_t launch_candidates(const uint64_t *rec_key, const uint64_t *rbits, uint64_t R, uint32_t tbits,
+                              const uint64_t *alive, uint32_t lo, const uint32_t *size, uint32_t k, DevCtl *ctl,
+                              cudaStream_t s);
+cudaError_t launch_commit_count(const uint64_t *rec_key, const uint64_t *rbits, uint64_t R, uint32_t tbits,
+                                const uint64_t *alive, uint32_t lo, uint32_t hi, uint32_t *size, uint64_t *lane_cnt,
+                                DevCtl *ctl, cudaStream_t s);
+cudaError_t launch_commit_scatter(const uint64_t *rec_key, const uint64_t *rbits, uint64_t R, uint32_t tbits,
+                                  const uint64_t *alive, uint32_t lo, uint32_t hi, const uint64_t *lane_off,
+                                  uint32_t *lane_fill, const uint64_t *idx_ctr, uint32_t *idx_nodes, cudaStream_t s);
 cudaError_t launch_commit_segments(const uint32_t *lane_pair, uint32_t lo, uint32_t hi, const uint64_t *lane_cnt,
                                    const uint64_t *lane_off, const uint64_t *idx_ctr, uint64_t *seg_start,
                                    uint32_t *seg_len, cudaStream_t s);
