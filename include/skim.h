@@ -70,7 +70,8 @@ typedef struct {
  *   rank_key   rank of pair (v,i) is fmix(rank_key + (v*l+i)*G), read as
  *              a real in [0,1) after scaling by 2^-64 (ranks never tie);
  *   prob_key   trivalency class of edge (u,v): fmix(prob_key ^ (u<<32|v)) % 3;
- *   batch_lanes  ranks per batched search, 0 = automatic;
+ *   batch_lanes  ranks per batched search, 0 = automatic (2M; 4M on graphs of
+ *              2^23 nodes or more);
  *   rank_mode  SKIM_RANKS_*: how the pairs are ordered and what a sketch holds.
  *     SKIM_RANKS_UNIFORM (0): the uniform 64-bit ranks above.
  *     SKIM_RANKS_PERMUTATION (1): structured permutation ranks (Section 3.1).
@@ -130,8 +131,9 @@ int skim_autotune_batch_lanes(skim_ctx *ctx, const uint32_t *candidates, uint32_
 
 /* Switches of the rank-batched searches (Algorithms 1 and 2 run a batch of
  * consecutive ranks as one search; none of these changes a result):
- *   batch_lanes            ranks per batch, 0 = automatic (2M, or fewer when
- *                          the previous batch's records per lane say so);
+ *   batch_lanes            ranks per batch, 0 = automatic (2M, 4M on graphs
+ *                          of 2^23 nodes or more, or fewer when the previous
+ *                          batch's records per lane say so);
  *   ring_records_per_lane  a batch whose searches are expected to leave at
  *                          most this many visit records per lane (from the
  *                          previous batch) runs with per-warp work queues in
