@@ -435,9 +435,10 @@ int node_buffers(skim_ctx *c) {
 // (pruned by local counts); otherwise SKIM (covered sources skipped).
 // est_per_lane: expected visit records per lane (0 or negative = unknown, or
 // a re-run after an overflow: the whole table).  The visited table used is a
-// power of two of about 4 slots per expected record, zeroed before the batch:
-// small enough to stay in L2.  A batch of searches that stay small (at most
-// kRingRecordsPerLane expected records per lane) runs on the per-warp queues;
+// power of two of about 4 slots per expected record, zeroed before the batch
+// (a batch touches only its own prefix of the table, and no slot needs a
+// generation tag).  A batch of searches that stay small (at most the tuned
+// ring_rpl expected records per lane) runs on the per-warp queues;
 // larger searches -- a lane that reaches thousands of nodes, as in the first
 // batches or on hub-heavy graphs -- spread over the whole GPU through the
 // global queue, whose atomic claims keep every warp fed.  Returns SKIM_OK
