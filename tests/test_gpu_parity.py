@@ -143,6 +143,29 @@ def test_search_kernels_each_alone(pkg, ring, name, mk, conf):
             assert np.array_equal(tau, otau) and np.array_equal(kp, okp), density
 
 
+@pytest.mark.parametrize("density", [0, 4])
+def test_record_order_hub_in_sparse_batches(pkg, density):
+    """A star of 100000 leaves with every edge live and k = 200: every lane's
+    reverse search reaches the centre until its local sketches fill, so the
+    second batch (8192 lanes) gives the centre a record in each of its 128 words
+    (the block pass of the record order) while the batch's records are sparse
+    over the nodes (placement by buckets of nodes, density 4) -- and the same
+    with the radix sort (density 0).  Sketches and seeds match the oracle."""
+    g = synth.star_out(100000)
+    l, k = 4, 200
+    pb, sk = _both(pkg, g, l, k, 0, 1.0, 21, 8192)
+    ox, oln, _ = oracle.build_sketches(pb)
+    os_, oc, otau, okp, _ = oracle.skim_stops(pb, 20)
+    with sk:
+        sk.set_tuning(8192, 8.0, density)
+        sk.build_sketches()
+        x, ln = sk.sketches()
+        assert np.array_equal(ln, oln) and np.array_equal(x, ox)
+        seeds, cov, tau, kp = sk.greedy_stops(20)
+        assert np.array_equal(seeds, os_) and np.array_equal(cov, oc)
+        assert np.array_equal(tau, otau) and np.array_equal(kp, okp)
+
+
 @pytest.mark.parametrize("bl", [0, 64, 1024])
 def test_skim_full_permutation_and_resume(pkg, bl):
     g = synth.random_small_graph(200, 1200, 8)
