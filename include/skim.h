@@ -299,7 +299,8 @@ int skim_oracle_query_batch(skim_ctx *ctx, const uint64_t *offsets, uint32_t q,
 #define SKIM_STAT_RETRIES 7         /* batches re-run with fewer lanes after a table overflow */
 #define SKIM_STAT_REV_EDGES 8       /* edges scanned by reverse searches (all lanes of an item share one scan) */
 #define SKIM_STAT_FWD_EDGES 9       /* edges scanned by residual searches */
-#define SKIM_STAT_COUNT 10
+#define SKIM_STAT_REQUEUES 10       /* searches resumed after a full work queue parked work */
+#define SKIM_STAT_COUNT 11
 int skim_get_stats(skim_ctx *ctx, uint64_t *out, uint32_t count);
 
 /* Kernel timing with CUDA events on the context's stream (off by default).

@@ -24,7 +24,7 @@ RANKS_UNIFORM, RANKS_PERMUTATION, RANKS_IC_MODEL = 0, 1, 2
 KERNEL_NAMES = ("rev_search", "fwd_search", "accept", "record_sort", "skim_step", "rank_order", "query", "setup",
                 "instances", "rev_sources")
 STAT_NAMES = ("rev_visits", "rev_coins", "insertions", "fwd_visits", "fwd_coins", "batches", "ranks", "retries",
-              "rev_edges", "fwd_edges")
+              "rev_edges", "fwd_edges", "requeues")
 
 
 class SkimError(RuntimeError):

@@ -376,6 +376,7 @@ int run_traversal(skim_ctx *c, TravArgs &a, bool forward, uint64_t *R_out, const
         if (R_out) *R_out = h.rec_count.v;
         if (h.err & kErrRetryable) return SKIM_OK;  // caller re-runs the batch
         if (!h.spill) return SKIM_OK;
+        c->hstats[SKIM_STAT_REQUEUES]++;
         RC(reset_queue(c, h.q_tail.v));
         KTimer kt(c, forward ? SKIM_K_FWD : SKIM_K_REV);
         if (forward)
@@ -1137,6 +1138,11 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
         c->rcap = rcap;
         c->hcap = pow2_at_least(2 * rcap);
         c->qcap = std::max<uint64_t>(rcap, 1u << 22);
+        // SKIM_QUEUE_ITEMS in the environment (a test hook): a queue of that
+        // many items, so that searches overflow it and park their work in
+        // the pending masks, which are re-queued after the queue drains
+        if (const char *qi = getenv("SKIM_QUEUE_ITEMS"))
+            c->qcap = std::max<uint64_t>(64, strtoull(qi, nullptr, 10));
         TRY(dalloc(c, &c->q, c->qcap));
         TRYC(cudaMemsetAsync(c->q, 0, c->qcap * sizeof(Item), c->st));
         // one array of 16-byte slots: key at [2h], lane bits at [2h + 1]

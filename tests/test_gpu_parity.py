@@ -117,6 +117,39 @@ def test_small_graphs_coins_hashed_in_the_search(pkg, name, mk, l, k, model, p, 
             assert sk.instance_stats()[1] == (rows and True)
 
 
+@pytest.mark.parametrize("items", [512, 8192])
+@pytest.mark.parametrize("ring", [0.0, 8.0])
+@pytest.mark.parametrize("name,mk,conf", [("rmat10", SMALL[-1][1], CONF[3]), ("er_dense", SMALL[7][1], CONF[2]),
+                                          ("chain", SMALL[0][1], CONF[6])])
+def test_queue_overflow_parks_and_requeues(pkg, monkeypatch, items, ring, name, mk, conf):
+    """A work queue far too small for the searches (SKIM_QUEUE_ITEMS): pushes
+    past its end park their work in the pending masks, which are queued again
+    once it drains, in reverse and residual searches, with stored instances
+    and with coins hashed in the search.  Results stay the oracle's."""
+    monkeypatch.setenv("SKIM_QUEUE_ITEMS", str(items))
+    g = mk()
+    l, k, model, p, bl = conf
+    pb, sk = _both(pkg, g, l, k, model, p, 17, bl)
+    monkeypatch.delenv("SKIM_QUEUE_ITEMS")
+    ox, oln, _ = oracle.build_sketches(pb)
+    s = min(g.n, 20)
+    os_, oc, otau, okp, _ = oracle.skim_stops(pb, s)
+    with sk:
+        sk.set_tuning(bl, ring, 4)
+        for rows in (True, False):
+            sk.set_live_rows(rows)
+            sk.build_sketches()
+            requeued = sk.stats()["requeues"]
+            x, ln = sk.sketches()
+            assert np.array_equal(ln, oln) and np.array_equal(x, ox), rows
+            sk.greedy_reset()
+            seeds, cov, tau, kp = sk.greedy_stops(s)
+            requeued += sk.stats()["requeues"]
+            assert requeued > 0 or items > 512, rows  # the small queue did overflow
+            assert np.array_equal(seeds, os_) and np.array_equal(cov, oc), rows
+            assert np.array_equal(tau, otau) and np.array_equal(kp, okp), rows
+
+
 @pytest.mark.parametrize("ring", [0.0, 1e9])
 @pytest.mark.parametrize("name,mk,conf", [("rmat10", SMALL[-1][1], CONF[4]), ("er_dense", SMALL[7][1], (16, 16, 0, 0.1, 64)),
                                           ("rmat12", lambda: synth.rmat(12, 16, 77), (64, 32, 1, 0.0, 2048))])
