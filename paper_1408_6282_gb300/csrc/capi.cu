@@ -1080,8 +1080,12 @@ int skim_create(const skim_graph *g, const skim_params *prm, void *stream, skim_
 #ifndef SKIM_RECORDS_PER_LANE
 #define SKIM_RECORDS_PER_LANE 16
 #endif
-        const uint64_t rcap =
+        uint64_t rcap =
             std::min<uint64_t>(std::max<uint64_t>(SKIM_RECORDS_PER_LANE * lanes_max, 1u << 20), 1ull << 26);
+        // SKIM_RECORD_ITEMS in the environment (a test hook): that many visit
+        // records (and twice as many table slots), so that batches overflow
+        // and are re-run with fewer lanes
+        if (const char *ri = getenv("SKIM_RECORD_ITEMS")) rcap = std::max<uint64_t>(64, strtoull(ri, nullptr, 10));
         size_t ws = std::max({scan_workspace_bytes(static_cast<size_t>(n) + 1), scan_workspace_bytes(nl + 1),
                               scan_workspace_bytes(rcap + 1),
                               radix_workspace_bytes(m),

@@ -150,6 +150,31 @@ def test_queue_overflow_parks_and_requeues(pkg, monkeypatch, items, ring, name, 
             assert np.array_equal(tau, otau) and np.array_equal(kp, okp), rows
 
 
+@pytest.mark.parametrize("name,mk,conf,records", [("er_sparse", SMALL[6][1], CONF[2], 2048)])
+def test_table_overflow_reruns_batches(pkg, monkeypatch, name, mk, conf, records):
+    """Record and visited tables far too small for the default batches
+    (SKIM_RECORD_ITEMS): overflowing build and SKIM batches stop early and are
+    re-run with fewer lanes.  Results stay the oracle's."""
+    monkeypatch.setenv("SKIM_RECORD_ITEMS", str(records))
+    g = mk()
+    l, k, model, p, bl = conf
+    pb, sk = _both(pkg, g, l, k, model, p, 19, 1 << 16)
+    monkeypatch.delenv("SKIM_RECORD_ITEMS")
+    ox, oln, _ = oracle.build_sketches(pb)
+    s = min(g.n, 20)
+    os_, oc, otau, okp, _ = oracle.skim_stops(pb, s)
+    with sk:
+        sk.build_sketches()
+        retried = sk.stats()["retries"]
+        x, ln = sk.sketches()
+        assert np.array_equal(ln, oln) and np.array_equal(x, ox)
+        seeds, cov, tau, kp = sk.greedy_stops(s)
+        retried += sk.stats()["retries"]
+        assert retried > 0  # the small tables did overflow
+        assert np.array_equal(seeds, os_) and np.array_equal(cov, oc)
+        assert np.array_equal(tau, otau) and np.array_equal(kp, okp)
+
+
 @pytest.mark.parametrize("ring", [0.0, 1e9])
 @pytest.mark.parametrize("name,mk,conf", [("rmat10", SMALL[-1][1], CONF[4]), ("er_dense", SMALL[7][1], (16, 16, 0, 0.1, 64)),
                                           ("rmat12", lambda: synth.rmat(12, 16, 77), (64, 32, 1, 0.0, 2048))])
