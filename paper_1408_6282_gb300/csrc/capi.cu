@@ -124,6 +124,11 @@ struct skim_ctx {
     uint64_t *rec_tau = nullptr;
     uint32_t *rec_kp = nullptr;
     uint32_t rec_j = 0;
+    // the residual search of the last seed, launched and not read back yet:
+    // the next read of the control block finishes it and stores its count of
+    // newly covered pairs at *pend_cov
+    bool pend_res = false;
+    uint64_t *pend_cov = nullptr;
     // queries
     uint64_t *qk = nullptr, *qv = nullptr;
     uint64_t qtcap = 0;
@@ -680,7 +685,51 @@ int commit_lanes(skim_ctx *c, uint32_t lo, uint32_t hi) {
     return SKIM_OK;
 }
 
-// Residual problem for seed x: forward search in every instance.
+// Finish the pending residual search, after a read of the control block that
+// followed it.  A search that parked work (its queue overflowed) resumes until
+// the queue drains; the lane filter launched after it then runs again, and
+// *again tells the caller that what it read back (stop candidate, argmax) was
+// computed before the search had finished.  Then the search's count of newly
+// covered pairs goes out and the queue is emptied.
+int finish_residual(skim_ctx *c, bool *again) {
+    *again = false;
+    if (!c->pend_res) return SKIM_OK;
+    c->pend_res = false;
+    const DevCtl &h = *c->hctl;
+    if (h.err & kErrTimeout) {
+        c->broken = true;
+        return SKIM_ETIMEOUT;
+    }
+    if (h.spill && !(h.err & kErrRetryable)) {
+        *again = true;
+        c->hstats[SKIM_STAT_REQUEUES]++;
+        RC(reset_queue(c, h.q_tail.v));
+        TravArgs a = base_args(c, true);
+        {
+            KTimer kt(c, SKIM_K_FWD);
+            CK(c, launch_respill_fwd(a, c->n, c->st));
+        }
+        RC(run_traversal(c, a, true, nullptr));
+        if (c->batch_active)
+            CK(c, launch_refilter(c->spair + c->bp0, c->blo, c->bB, c->l, c->covered, c->alive, c->st));
+    }
+    *c->pend_cov = c->hctl->ix_cov;
+    RC(reset_queue(c, c->hctl->q_tail.v));
+    return SKIM_OK;
+}
+
+// Wait for the pending residual search, if any, and finish it.
+int settle_residual(skim_ctx *c) {
+    if (!c->pend_res) return SKIM_OK;
+    RC(sync_ctl(c));
+    bool again = false;
+    return finish_residual(c, &again);
+}
+
+// Residual problem for seed x: forward search in every instance.  The search
+// is launched and not waited for: the host goes on to queue the next seed's
+// scan behind it, and the read-back of that scan finishes the search
+// (finish_residual), storing its count of newly covered pairs at *cov.
 int residual(skim_ctx *c, uint32_t x, uint64_t *cov) {
     RC(reset_ctl(c));
     TravArgs a = base_args(c, true);
@@ -692,9 +741,15 @@ int residual(skim_ctx *c, uint32_t x, uint64_t *cov) {
         cudaEventRecord(t0, c->st);
     }
     CK(c, launch_fwd_source(a, x, c->st));
-    RC(run_traversal(c, a, true, nullptr));
-    *cov = c->hctl->ix_cov;
-    if (trace_batches()) {  // one line per residual search
+    {
+        KTimer kt(c, SKIM_K_FWD);
+        CK(c, launch_traverse(a, true, c->grid_fwd, c->st));
+    }
+    CK(c, cudaMemsetAsync(c->chosen + x, 1, 1, c->st));
+    c->pend_res = true;
+    c->pend_cov = cov;
+    if (trace_batches()) {  // one line per residual search, waited for
+        RC(settle_residual(c));
         cudaEventRecord(t1, c->st);
         cudaEventSynchronize(t1);
         float ms = 0.f;
@@ -706,8 +761,6 @@ int residual(skim_ctx *c, uint32_t x, uint64_t *cov) {
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
     }
-    RC(reset_queue(c, c->hctl->q_tail.v));
-    CK(c, cudaMemsetAsync(c->chosen + x, 1, 1, c->st));
     return SKIM_OK;
 }
 
@@ -721,6 +774,11 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
                                         c->k, c->ctl, c->st));
             }
             RC(sync_ctl(c));
+            {
+                bool again = false;
+                RC(finish_residual(c, &again));
+                if (again) continue;  // the scan ran before the last seed's search had finished
+            }
             const uint64_t best = c->hctl->best;
             if (best != ~0ull) {
                 const uint32_t p = static_cast<uint32_t>(best >> 32);
@@ -749,6 +807,7 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
             continue;
         }
         if (c->cursor < c->nl) {
+            RC(settle_residual(c));  // a new batch resets the control block
             // A lane can cost a whole reverse search of a giant component,
             // and lanes past the next stop are wasted if the new seed covers
             // their source.  So a batch is sized to about kSkimVisitBudget
@@ -795,6 +854,11 @@ int next_seed(skim_ctx *c, uint32_t *x_out, uint64_t *cov_out) {
         CK(c, cudaMemsetAsync(&c->ctl->argmax, 0, sizeof(unsigned long long), c->st));
         CK(c, launch_argmax_size(c->size, c->n, c->ctl, c->st));
         RC(sync_ctl(c));
+        {
+            bool again = false;
+            RC(finish_residual(c, &again));
+            if (again) continue;  // the sizes were read before the last seed's search had finished
+        }
         uint64_t am = c->hctl->argmax;
         uint32_t x = 0xffffffffu - static_cast<uint32_t>(am & 0xffffffffu);
         if ((am >> 32) == 0) {
@@ -1533,17 +1597,23 @@ int skim_greedy_reset(skim_ctx *c) {
 
 namespace {
 
+// cov_out[j] is stored when seed j's residual search is finished: by the
+// read-back of seed j+1's scan, or before the call returns.
 int greedy_loop(skim_ctx *c, uint32_t n_seeds, uint32_t *seeds_out, uint64_t *cov_out) {
+    int rc = SKIM_OK;
     for (uint32_t j = 0; j < n_seeds; j++) {
         uint32_t x = 0;
-        uint64_t cov = 0;
         c->rec_j = j;
-        RC(next_seed(c, &x, &cov));
+        rc = next_seed(c, &x, cov_out + j);
+        if (rc != SKIM_OK) break;
         seeds_out[j] = x;
-        cov_out[j] = cov;
         c->nseeds++;
     }
-    return SKIM_OK;
+    if (rc == SKIM_OK) rc = settle_residual(c);
+    // an error return with a search still pending came from a failed CUDA
+    // call or wait, after which the context refuses further work
+    c->pend_res = false;
+    return rc;
 }
 
 }  // namespace
