@@ -18,7 +18,11 @@
 //
 // There are no BFS levels: warps claim items from one global queue, process
 // them, and push new items; the search ends when every pushed item is done.
+// Reverse searches of small batches use per-warp queues instead (k_rev_ring),
+// and residual searches keep a few items per block in shared memory (FwdRing).
 // Every wait is bounded by a timeout that sets an error flag.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace skim {
@@ -190,6 +194,209 @@ SKIM_DEV bool spill_if_full(const TravArgs &A, unsigned long long s, uint32_t ni
     return true;
 }
 
+// ---- Block-local work ring of the residual searches ----
+//
+// A residual search starts at one seed and, on sparse live graphs, is a long
+// and mostly narrow walk (tens of hops deep per instance), so its time is its
+// depth times the latency of one hop.  Through the global queue a hop is a
+// slot reservation, the item's write, a poll that finds it and its read, on
+// top of the row read and the covering OR.  So a block of the search over
+// materialised rows keeps up to kFwdKeep items in a ring in shared memory,
+// taken by its own warps; the items that do not fit go to the global queue,
+// which spreads a wide frontier over the grid.
+//
+// The ring is a bounded multi-producer multi-consumer queue: positions are
+// handed out by compare-and-swap on `tail` (reserved) and `head` (taken), and
+// slot i's sequence number says whether it is free for position p (seq = p)
+// or holds the item of position p (seq = p + 1).
+//
+// The search still ends by the global queue's drain test (done == tail).
+// While a ring holds unfinished items its block holds one reserved queue slot,
+// the token, which is written with a placeholder only after the last of them
+// is finished; whoever claims the slot counts it as done.  The token is
+// reserved before the items it covers are pushed, and the items' own pushes
+// are counted before they are finished, so the drain test cannot pass while a
+// ring holds work.  A token outlives its ring's work until a warp of the block
+// has found nothing to do for kFwdParkNs (the next items pushed to the ring
+// reuse it, without a reservation on the queue); a warp that leaves releases
+// it.  `state` packs the token with the count of unfinished items so that
+// both change together.
+#ifndef SKIM_FWD_KEEP
+#define SKIM_FWD_KEEP 8
+#endif
+constexpr uint32_t kFwdKeep = SKIM_FWD_KEEP;  // items a block's ring may hold (0: no ring)
+#ifndef SKIM_FWD_PARK_NS
+#define SKIM_FWD_PARK_NS 2000
+#endif
+constexpr uint64_t kFwdParkNs = SKIM_FWD_PARK_NS;  // idle time after which a warp frees its block's token
+constexpr unsigned long long kNoTok = 0xffffffffull;  // token field: none held
+constexpr uint32_t kFwdCap = kFwdKeep <= 64 ? 64 : 512;  // ring slots (a power of two, at least kFwdKeep)
+static_assert(kFwdKeep <= kFwdCap, "ring size");
+
+struct FwdRing {
+    ulonglong2 it[kFwdCap];    // .x = (w + 1) << 32 | (v + 1), .y = mask
+    unsigned seq[kFwdCap];
+    unsigned head, tail;
+    unsigned long long state;  // token slot (kNoTok: none) << 32 | unfinished items
+};
+
+SKIM_DEV unsigned ld_vol(const unsigned *p) { return *reinterpret_cast<const volatile unsigned *>(p); }
+SKIM_DEV void st_ring_item(ulonglong2 *p, uint64_t x, uint64_t y) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+    asm volatile("st.volatile.shared.v2.u64 [%0], {%1, %2};" ::"r"(a), "l"(x), "l"(y) : "memory");
+}
+SKIM_DEV void ld_ring_item(const ulonglong2 *p, uint64_t *x, uint64_t *y) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+    asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];" : "=l"(*x), "=l"(*y) : "r"(a) : "memory");
+}
+
+SKIM_DEV void ring_init(FwdRing *R) {
+    for (uint32_t i = threadIdx.x; i < kFwdCap; i += blockDim.x) R->seq[i] = i;
+    if (threadIdx.x == 0) {
+        R->head = R->tail = 0;
+        R->state = kNoTok << 32;
+    }
+}
+
+// Spin until *p == want; false (and the error flag) when the wait limit runs out.
+SKIM_DEV bool ring_wait(const TravArgs &A, const unsigned *p, unsigned want) {
+    if (ld_vol(p) == want) return true;
+    const uint64_t t0 = globaltimer();
+    for (unsigned k = 1;; k++) {
+        if (ld_vol(p) == want) return true;
+        if ((k & 63) == 0 && globaltimer() - t0 > A.timeout_ns) {
+            atomicOr(&A.ctl->err, kErrTimeout);
+            return false;
+        }
+    }
+}
+
+// Lane 0: free the block's token if its ring has no unfinished items (a
+// placeholder into its queue slot).
+SKIM_DEV void ring_release(const TravArgs &A, FwdRing *R) {
+    const unsigned long long s = *reinterpret_cast<volatile unsigned long long *>(&R->state);
+    if ((s & 0xffffffffull) != 0 || (s >> 32) == kNoTok) return;
+    if (atomicCAS(&R->state, s, kNoTok << 32) != s) return;
+    __threadfence();  // the reservations of the finished items' own pushes come first
+    write_item(A, s >> 32, 0, kNopTag, 1);
+}
+
+// Lane 0 finishes k of the ring's items.
+SKIM_DEV void ring_finish(const TravArgs &A, FwdRing *R, unsigned k) {
+    atomicAdd(&R->state, 0ull - k);
+    if (kFwdParkNs == 0) ring_release(A, R);
+}
+
+// Lane 0 counts tot new ring items; the first of an empty ring takes a token
+// unless the block still holds one.  False when no token can be had (the
+// global queue is full).
+SKIM_DEV bool ring_count(const TravArgs &A, FwdRing *R, unsigned long long tot) {
+    unsigned long long s = *reinterpret_cast<volatile unsigned long long *>(&R->state), tok = kNoTok;
+    for (int k = 0;; k++) {
+        if (k == 4096) {  // contended for too long: the items go to the queue
+            if (tok != kNoTok) write_item(A, tok, 0, kNopTag, 1);
+            return false;
+        }
+        unsigned long long ns;
+        const bool fresh = (s >> 32) == kNoTok;
+        if (fresh) {
+            if (tok == kNoTok) {
+                tok = atomicAdd(&A.ctl->q_tail.v, 1ull);
+                if (tok >= A.qcap) {  // beyond the queue: counted as done at once
+                    atomicAdd(&A.ctl->q_done.v, 1ull);
+                    return false;
+                }
+            }
+            ns = (tok << 32) | tot;
+        } else {
+            ns = s + tot;
+        }
+        const unsigned long long o = atomicCAS(&R->state, s, ns);
+        if (o == s) {
+            if (!fresh && tok != kNoTok) write_item(A, tok, 0, kNopTag, 1);  // a token not needed after all
+            return true;
+        }
+        s = o;
+    }
+}
+
+// Warp-collective: tot ring positions for the warp's new items, all or none;
+// *base = the first.
+SKIM_DEV bool ring_reserve(const TravArgs &A, FwdRing *R, unsigned long long tot, unsigned *base) {
+    int ok = 0;
+    unsigned b = 0;
+    if ((threadIdx.x & 31) == 0 && tot && tot <= kFwdKeep &&
+        ld_vol(&R->tail) - ld_vol(&R->head) + tot <= kFwdKeep && ring_count(A, R, tot)) {
+        unsigned t = ld_vol(&R->tail);
+        for (int k = 0; k < 16; k++) {
+            if (t - ld_vol(&R->head) + tot > kFwdKeep) break;
+            const unsigned o = atomicCAS(&R->tail, t, t + static_cast<unsigned>(tot));
+            if (o == t) {
+                ok = 1;
+                b = t;
+                break;
+            }
+            t = o;
+        }
+        if (!ok) ring_finish(A, R, static_cast<unsigned>(tot));  // no room after all: uncount
+    }
+    *base = __shfl_sync(kFull, b, 0);
+    return __shfl_sync(kFull, ok, 0) != 0;
+}
+
+// Write the item of ring position pos once its slot is free.
+SKIM_DEV void ring_put(const TravArgs &A, FwdRing *R, unsigned pos, uint32_t v, uint32_t w, uint64_t mask) {
+    const unsigned i = pos & (kFwdCap - 1);
+    if (!ring_wait(A, &R->seq[i], pos)) return;
+    const uint64_t lo = (static_cast<uint64_t>(w + 1) << 32) | (v + 1);
+    st_ring_item(&R->it[i], lo, mask);
+    __threadfence_block();
+    *reinterpret_cast<volatile unsigned *>(&R->seq[i]) = pos + 1;
+}
+
+// Warp-collective: the lanes of `freel` take ring items, one each, as many as
+// there are; returns the lanes that took one (an item lost to the wait limit
+// is taken empty).
+SKIM_DEV unsigned ring_take(const TravArgs &A, FwdRing *R, unsigned freel, bool &have, Item &it) {
+    const int lane = threadIdx.x & 31;
+    unsigned n = 0, b = 0;
+    if (lane == 0) {
+        unsigned h = ld_vol(&R->head);
+        const unsigned want = __popc(freel);
+        for (int k = 0; k < 16; k++) {
+            const unsigned avail = ld_vol(&R->tail) - h;
+            const unsigned m = avail < want ? avail : want;
+            if (!m) break;
+            const unsigned o = atomicCAS(&R->head, h, h + m);
+            if (o == h) {
+                n = m;
+                b = h;
+                break;
+            }
+            h = o;
+        }
+    }
+    n = __shfl_sync(kFull, n, 0);
+    if (!n) return 0;
+    b = __shfl_sync(kFull, b, 0);
+    const unsigned r = __popc(freel & lanemask_lt());
+    const bool mine = ((freel >> lane) & 1u) && r < n;
+    if (mine) {
+        const unsigned pos = b + r, i = pos & (kFwdCap - 1);
+        if (ring_wait(A, &R->seq[i], pos + 1)) {
+            uint64_t x = 0, y = 0;
+            ld_ring_item(&R->it[i], &x, &y);
+            __threadfence_block();
+            *reinterpret_cast<volatile unsigned *>(&R->seq[i]) = pos + kFwdCap;
+            it.v = static_cast<uint32_t>(x) - 1;
+            it.w = static_cast<uint32_t>(x >> 32) - 1;
+            it.mask = y;
+            have = true;
+        }
+    }
+    return __ballot_sync(kFull, mine);
+}
+
 // Live in-neighbour row of (u, lane j of word t) in the materialised instances.
 SKIM_DEV uint32_t live_row_len(const TravArgs &A, uint32_t u, uint32_t t, int j) {
     const uint64_t r = static_cast<uint64_t>(u) * A.l + A.lane_inst[static_cast<size_t>(t) * 64 + j];
@@ -316,6 +523,12 @@ struct GlobalSink {
     }
 };
 
+// Where a residual search puts its new items: the block's ring (null: none)
+// while it has room, else the global queue.
+struct FwdSink {
+    FwdRing *ring;
+};
+
 // Warp-collective, materialised reverse searches: lanes with `act` reach node
 // u for lane j of word t (instance inst).  The row bounds of (u, inst) and the
 // pruning word are loaded together, before the visited-table update.
@@ -364,9 +577,11 @@ struct PairPre {
 // erasure of the index entries of pairs (w, i), i in `erase`.  With
 // materialised instances each instance gets row items of its own list of live
 // out-neighbours (none if it is empty).  pre.ok: trav and erase hold at most
-// the bit of pre's instance, whose values are taken from pre.
+// the bit of pre's instance, whose values are taken from pre.  With a ring,
+// the warp's new items go to the ring when they all fit.
 template <bool MAT>
-SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, uint64_t erase, const PairPre &pre) {
+SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, uint64_t erase, const PairPre &pre,
+                       FwdRing *ring = nullptr) {
     uint32_t ni = 0;
     if (MAT) {
         for (uint64_t m = trav; m; m &= m - 1) {
@@ -381,24 +596,42 @@ SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, u
         ni += n_chunks(pre.ok ? pre.sl : A.seg_len[static_cast<uint64_t>(w) * A.l + i]);
     }
     if (!__any_sync(kFull, ni != 0)) return;
-    unsigned long long s = reserve_slots(A, acc, ni);
-    if (ni && spill_if_full(A, s, ni)) {
-        if (trav) atomicOr(reinterpret_cast<unsigned long long *>(&A.pend_trav[w]), trav);
-        if (erase) atomicOr(reinterpret_cast<unsigned long long *>(&A.pend_erase[w]), erase);
-        return;
+    unsigned long long s = 0;
+    bool local = false;
+    if (ring) {
+        unsigned long long tot;
+        const unsigned long long ex = warp_excl_scan(ni, &tot);
+        unsigned base = 0;
+        local = ring_reserve(A, ring, tot, &base);
+        s = base + ex;
     }
+    if (!local) {
+        s = reserve_slots(A, acc, ni);
+        if (ni && spill_if_full(A, s, ni)) {
+            if (trav) atomicOr(reinterpret_cast<unsigned long long *>(&A.pend_trav[w]), trav);
+            if (erase) atomicOr(reinterpret_cast<unsigned long long *>(&A.pend_erase[w]), erase);
+            return;
+        }
+    }
+    auto put = [&](unsigned long long q, uint32_t v, uint32_t iw, uint64_t m) {
+        if (local)
+            ring_put(A, ring, static_cast<unsigned>(q), v, iw, m);
+        else
+            write_item(A, q, v, iw, m);
+    };
     uint32_t c = 0;
     if (MAT) {
         for (uint64_t m = trav; m; m &= m - 1) {
             const int i = __ffsll(m) - 1;
             const uint64_t r = static_cast<uint64_t>(w) * A.l + i;
             const uint64_t b0 = pre.ok ? pre.b0 : A.loff[r], b1 = pre.ok ? pre.b1 : A.loff[r + 1];
-            write_row_items(A, s + c, b0, b1, 0, i, 0);
-            c += n_chunks(static_cast<uint32_t>(b1 - b0));
+            for (uint64_t e = b0; e < b1; e += kChunk, c++)  // row items as write_row_items lays them out
+                put(s + c, static_cast<uint32_t>(e), row_item_w(0, i, 0),
+                    b1 - e < kChunk ? b1 - e : static_cast<uint64_t>(kChunk));
         }
     } else if (trav) {
         uint32_t nc = n_chunks(A.ptr[w + 1] - A.ptr[w], trav);
-        for (; c < nc; c++) write_item(A, s + c, w, c, trav);
+        for (; c < nc; c++) put(s + c, w, c, trav);
     }
     for (uint64_t m = erase; m; m &= m - 1) {
         int i = __ffsll(m) - 1;
@@ -408,7 +641,7 @@ SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, u
         A.seg_len[pair] = 0;  // erase index[w,i]
         uint64_t st = pre.ok ? pre.st : A.seg_start[pair];
         uint32_t ne = n_chunks(len);
-        for (uint32_t e = 0; e < ne; e++, c++) write_item(A, s + c, len, kEraseTag | e, st + 1);
+        for (uint32_t e = 0; e < ne; e++, c++) put(s + c, len, kEraseTag | e, st + 1);
     }
 }
 
@@ -418,7 +651,7 @@ SKIM_DEV void push_fwd(const TravArgs &A, Acc &acc, uint32_t w, uint64_t trav, u
 // that covers it (an index is erased only by the lane whose OR newly covers
 // its pair, so reading it first is safe).
 template <bool MAT>
-SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64_t live) {
+SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64_t live, FwdRing *ring = nullptr) {
     if (!__any_sync(kFull, act && live)) return;
     uint64_t nb = 0;
     PairPre pre;
@@ -448,7 +681,7 @@ SKIM_DEV void emit_fwd(const TravArgs &A, Acc &acc, bool act, uint32_t w, uint64
         int i = __ffsll(m) - 1;
         if (pre.ok ? pre.sl : A.seg_len[static_cast<uint64_t>(w) * A.l + i]) erase |= 1ull << i;
     }
-    push_fwd<MAT>(A, acc, w, nb, erase, pre);
+    push_fwd<MAT>(A, acc, w, nb, erase, pre, ring);
 }
 
 // Process the items held by the lanes with `have`, edges (or index entries)
@@ -601,9 +834,9 @@ SKIM_DEV void emit_step(const TravArgs &A, Acc &acc, SK &sk, const Desc &d, cons
 #pragma unroll
     for (int q = 0; q < kUnroll; q++) {
         uint64_t live = lv[q];
-        if (FWD) {
-            emit_fwd<MAT>(A, acc, live != 0, tg[q], live);
-        } else if (MAT) {
+        if constexpr (FWD) {
+            emit_fwd<MAT>(A, acc, live != 0, tg[q], live, sk.ring);
+        } else if constexpr (MAT) {
             emit_rev_mat(A, acc, sk, live != 0, tg[q], d.w >> kChunkBits, __ffsll(d.mask) - 1, d.inst);
         } else {
             if (live && A.prune) live = prune_full(A, d, tg[q], live);
@@ -1088,19 +1321,30 @@ constexpr unsigned long long kDoneBatch = 64;
 // Reverse searches over materialised rows (MAT) stage their visit records in
 // shared memory and spread the entries of small row items over the warp's
 // lanes, as the per-warp-queue search does (a RingSink whose ring limit is 0
-// puts every row item into the global queue).
+// puts every row item into the global queue).  Residual searches over
+// materialised rows keep items in the block's ring (FwdRing) while it has
+// room; a warp takes ring items into its lanes that hold no queue item.
+struct NoRing {};
 template <bool FWD, bool MAT>
-__global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse(TravArgs A) {
+__global__ void __launch_bounds__(kTravThreads, FWD ? 1 : SKIM_TRAV_MIN_BLOCKS) k_traverse(TravArgs A) {
     constexpr bool kStaged = !FWD && MAT;
+    constexpr bool kLocal = FWD && MAT && kFwdKeep > 0;
     __shared__ uint64_t ginst[64];  // (i + 1) * G for instance i (residual searches)
     __shared__ uint64_t s_rk[kStaged ? kTravThreads / 32 : 1][kStaged ? kRecStage : 1];
     __shared__ uint32_t s_rs[kStaged ? kTravThreads / 32 : 1][kStaged ? kRecStage : 1];
+    __shared__ typename std::conditional<kLocal, FwdRing, NoRing>::type s_ring;
+    FwdRing *ring = nullptr;
+    if constexpr (kLocal) {
+        ring = &s_ring;
+        ring_init(ring);
+    }
     if (threadIdx.x < 64) ginst[threadIdx.x] = kGolden * static_cast<uint64_t>(threadIdx.x + 1);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     DevCtl *C = A.ctl;
     Acc acc;
     GlobalSink gsink;
+    FwdSink fsink{ring};
     const uint32_t wib = kStaged ? threadIdx.x >> 5 : 0;
     RingSink ssink{nullptr, s_rk[wib], s_rs[wib], 0, 0, 0, 0};
     uint64_t t_progress = globaltimer();
@@ -1132,11 +1376,22 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
                 pending = false;
             }
             const unsigned hb = __ballot_sync(kFull, have);
-            if (hb) {
+            unsigned lb = 0;  // lanes holding a ring item
+            if constexpr (kLocal) {
+                if (hb != kFull) lb = ring_take(A, ring, ~hb, have, it);
+            }
+            if (hb | lb) {
                 if constexpr (kStaged)
                     ring_expand(A, acc, ssink, have, it);
+                else if constexpr (FWD)
+                    process_items<FWD, MAT>(A, acc, fsink, have, it, ginst);
                 else
                     process_items<FWD, MAT>(A, acc, gsink, have, it, ginst);
+                if constexpr (kLocal) {
+                    // after the items' own pushes (their reservations are made)
+                    __syncwarp();
+                    if (lb && lane == 0) ring_finish(A, ring, __popc(lb));
+                }
                 // The drain test reads done, then tail, so the slots reserved
                 // while processing must be counted in tail before these items
                 // count as done.  No fence is needed: lane 0 made every
@@ -1193,12 +1448,23 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
                     done = true;
                     break;
                 }
+                if constexpr (kLocal) {
+                    // a block whose ring has stayed empty frees its token
+                    if (lane == 0 && globaltimer() - t_progress > kFwdParkNs) ring_release(A, ring);
+                }
 #ifndef SKIM_SPIN
 #define SKIM_SPIN 0
 #endif
+#ifndef SKIM_FWD_SLEEP
+#define SKIM_FWD_SLEEP 0
+#endif
 #if SKIM_SPIN == 0
-                __nanosleep(backoff);
-                if (backoff < 512) backoff <<= 1;
+                // a residual search's idle warps poll without pausing: it is
+                // the only work on the device and its hops are latency-bound
+                if (!FWD || SKIM_FWD_SLEEP) {
+                    __nanosleep(backoff);
+                    if (backoff < 512) backoff <<= 1;
+                }
 #elif SKIM_SPIN == 2
                 {
                     const long long t0 = clock64();
@@ -1210,6 +1476,38 @@ __global__ void __launch_bounds__(kTravThreads, SKIM_TRAV_MIN_BLOCKS) k_traverse
             if (!__any_sync(kFull, pending)) break;
         }
         if (__any_sync(kFull, empty)) done = true;
+    }
+    if constexpr (kLocal) {
+        // A warp leaves its block's ring empty (the queue ran out of slots,
+        // or drained, in which case the ring is empty already): its items can
+        // be taken by this block's warps only.  Warps still working take the
+        // items they push themselves before they leave.
+        uint64_t t_last = globaltimer();
+        for (;;) {
+            unsigned e = 0;
+            if (lane == 0) e = *reinterpret_cast<volatile unsigned *>(&C->err);
+            if (__shfl_sync(kFull, e, 0) & (kErrRetryable | kErrTimeout)) break;
+            Item it{0, 0, 0};
+            bool have = false;
+            const unsigned lb = ring_take(A, ring, kFull, have, it);
+            if (!lb) {
+                int idle = 0;
+                if (lane == 0) {
+                    idle = ld_vol(&ring->tail) == ld_vol(&ring->head);
+                    if (idle) ring_release(A, ring);
+                }
+                if (__shfl_sync(kFull, idle, 0)) break;
+                if (globaltimer() - t_last > A.timeout_ns) {
+                    if (lane == 0) atomicOr(&C->err, kErrTimeout);
+                    break;
+                }
+                continue;
+            }
+            t_last = globaltimer();
+            process_items<FWD, MAT>(A, acc, fsink, have, it, ginst);
+            __syncwarp();
+            if (lane == 0) ring_finish(A, ring, __popc(lb));
+        }
     }
     if (done_pend && lane == 0) atomicAdd(&C->q_done.v, done_pend);
     if constexpr (kStaged) ssink.flush(A);
