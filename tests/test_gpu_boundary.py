@@ -1,7 +1,7 @@
 """The C ABI's smaller calls on the GPU: the per-node sketch read, the device
-wait limit (made to run out on purpose: the search gives up, returns
-SKIM_ETIMEOUT, and a fresh context then builds correct sketches), and the
-server's host-side wait timeout."""
+wait limit (made to run out on purpose in a build and in SKIM: the search
+gives up, returns SKIM_ETIMEOUT, and a fresh context then builds correct
+sketches), and the server's host-side wait timeout."""
 import numpy as np
 import pytest
 
@@ -71,6 +71,27 @@ def test_wait_limit_runs_out_then_a_fresh_context_is_correct(pkg):
         seeds, cov = sk.greedy(5)
         os_, oc, _, _ = oracle.skim(pb, 5)
         assert np.array_equal(seeds, os_) and np.array_equal(cov, oc)
+
+
+def test_wait_limit_runs_out_during_skim(pkg):
+    """The wait limit bounds SKIM's searches too.  Two seeds taken with the
+    default limit match the oracle; with a 1 ns limit the next seed's search
+    (the residual search of the last seed, finished at the next read-back, or
+    the reverse search of a new batch) gives up, the call reports SKIM_ETIMEOUT
+    and the context refuses further work."""
+    g = synth.random_small_graph(2000, 12000, 9)
+    pb = oracle.Problem(g.n, g.src, g.dst, 8, 8, 0, 0.2, 5, 6, 7)
+    os_, oc, _, _ = oracle.skim(pb, 2)
+    with pkg.Skim(g.n, g.src, g.dst, 8, 8, 0, 0.2, 5, 6, 7) as sk:
+        seeds, cov = sk.greedy(2)
+        assert np.array_equal(seeds, os_) and np.array_equal(cov, oc)
+        sk.set_wait_limit_ns(1)
+        with pytest.raises(pkg.SkimError) as e:
+            sk.greedy(3)
+        assert e.value.code == -4
+        with pytest.raises(pkg.SkimError) as e:
+            sk.greedy(1)
+        assert e.value.code == -5
 
 
 def test_server_wait_times_out_and_server_keeps_serving(pkg):
